@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Throughput of the binned forward rasterizer on one GB300 (or N replicas).
+
+Workload: a displaced heightfield grid of 1000 x 500 quads (1,000,000
+triangles, 501,501 vertices) seen by a perspective camera at 1920 x 1080,
+Lambert shading with the material and light of Listing 1, 16 x 16 tiles,
+static tile schedule.  One step = one forward pass: vertex stage, setup and
+bin counts, scan, scatter, per-tile Process (coverage, depth, shading,
+write-out).  Inputs are resident in HBM; the L2 is flushed between steps by
+writing a 256 MiB buffer outside the per-step events.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+(the plain rasterizer the CUDA path is checked against) on bounded samples
+of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mtris/s + shaded Gfrag/s on 1 GB300 (plain vs batched), bit-exact depth/ID"
+UNIT = "Mtris/s"
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "process_heightfield1080p_traffic.json")
+KERNEL_SOURCES = ["paper_1404_6293_gb300/csrc/piko_forward.cu", "paper_1404_6293_gb300/csrc/piko_internal.cuh"]
+
+# Per-unit algorithmic costs of the Process kernel (thread operations), fixed
+# from the minimal operation sequence of the definition: see the design doc.
+OPS_PER_ENTRY = 60      # re-derive the triangle: 3 gathers, 6 differences, 64-bit area, clip to tile
+OPS_PER_TEST = 12       # three 64-bit incremental edge updates and the sign test
+OPS_PER_FRAGMENT = 16   # 64-bit depth numerator, reciprocal estimate and fix-up, key, shared-memory min
+OPS_PER_SHADE = {0: 20, 1: 30, 2: 30}
+ALU_OPS_PER_SM_CLK = 4 * 32  # four schedulers, 32 lanes
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled while the timed region runs."""
+
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int, period_ms: int = 100):
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits",
+                 "-lms", str(period_ms), "-i", str(index)], stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def mark(self):
+        self.out.flush()
+        try:
+            return sum(1 for _ in open(self.out.name))
+        except OSError:
+            return 0
+
+    def stop(self, first_line: int = 0) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.flush()
+        rows = [ln.strip().split(",") for ln in open(self.out.name)][first_line:]
+        os.unlink(self.out.name)
+        rows = [[c.strip() for c in r] for r in rows if len(r) == len(self.FIELDS)]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
+
+
+def workload(args):
+    from paper_1404_6293_gb300 import scenes as S
+    scene = S.heightfield()
+    cfg = {"workload": "heightfield 1920x1080, 1000x500 quads (1,000,000 triangles), Lambert",
+           "width": scene.width, "height": scene.height, "triangles": scene.num_triangles,
+           "vertices": scene.num_vertices, "bin": [args.bins, args.bins], "schedule": args.schedule,
+           "l2": "flushed between steps (256 MiB write outside the per-step events)"}
+    return scene, cfg
+
+
+def cpu_baseline(scene, seconds: float) -> dict:
+    """The oracle as it stands: bounding-box loop on all host cores + float64 shading."""
+    import oracle
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        key, _ = oracle.raster_bbox(scene, threads=cores)
+        oracle.shade(scene, key)
+        reps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": scene.num_triangles / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{reps} full frame(s) of the same workload: bounding-box oracle on {cores} threads "
+                      f"plus float64 shading, {dt:.2f} s per frame"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    from paper_1404_6293_gb300 import scenes as S
+    scene, cfg = workload(args)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+    def sub(n):
+        return S.Scene(scene.width, scene.height, scene.pos, np.ascontiguousarray(scene.tris[:n]),
+                       normal=scene.normal, mvp=scene.mvp, light_dir=scene.light_dir, shade_mode=scene.shade_mode)
+
+    def step(sc):
+        key, _ = oracle.raster_bbox(sc, threads=cores)
+        oracle.shade(sc, key)
+
+    # size the per-step sample so that warm-up plus timed steps stay near two minutes
+    n = scene.num_triangles // 32
+    t0 = time.perf_counter()
+    step(sub(n))
+    t1 = time.perf_counter() - t0
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    n = int(max(2000, min(scene.num_triangles, n * budget / max(t1, 1e-6))))
+    sc = sub(n)
+    for _ in range(args.warmup):
+        step(sc)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        step(sc)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = n / (ms * 1e-3) / 1e6
+    sample = (f"first {n} triangles (a contiguous band of the grid) of the workload per step, "
+              f"bounding-box oracle on {cores} threads plus float64 shading")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64", "data": "synthetic",
+            "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1404_6293_gb300 import _lib as L
+    from paper_1404_6293_gb300.raster import DeviceScene, Framebuffer, Rasterizer
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    scene, cfg = workload(args)
+    T = scene.num_triangles
+    r = Rasterizer(scene.width, scene.height, args.bins, args.bins, args.schedule)
+    ds = DeviceScene.from_host(scene)
+    fb = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode)
+    r.forward(ds, fb)  # sizes the bin lists (capacity check on)
+    code, need = r.status()
+    if code != 0:
+        raise RuntimeError(f"forward status {code}")
+    r.set_option(L.PIKO_OPT_CHECK_CAPACITY, 0)
+    r.set_option(L.PIKO_OPT_STATS, 1)
+    r.forward(ds, fb)
+    stats = r.stats()
+    r.set_option(L.PIKO_OPT_STATS, 0)
+    covered = int((fb.key != -1).sum().item())
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    clocks = ClockSampler(torch.cuda.current_device() if world == 1 else local)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        flush.zero_()
+        r.forward(ds, fb)
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2 + L.PIKO_NUM_STAGE_EVENTS)] for _ in range(K)]
+    for row in ev:
+        for e in row:
+            e.record(stream)
+    barrier()
+    first_clock_line = clocks.mark()
+    wall0 = time.perf_counter()
+    for k in range(K):
+        flush.zero_()
+        ev[k][0].record(stream)
+        r.set_stage_events(ev[k][2:])
+        r.forward(ds, fb)
+        ev[k][1].record(stream)
+    barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop(first_clock_line)
+    code, _ = r.status()
+    if code != 0:
+        raise RuntimeError(f"status {code} after the timed loop")
+    step_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
+    stage_ms = np.array([[ev[k][2 + i].elapsed_time(ev[k][3 + i]) for i in range(L.PIKO_NUM_STAGE_EVENTS - 1)]
+                         for k in range(K)])
+    ms = float(np.sum(step_ms) / K)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * T / (ms * 1e-3) / 1e6
+    shaded_gfrag = world * covered / (ms * 1e-3) / 1e9
+
+    # ---------------------------------------------------------------- roofline
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    proc_ms = float(stage_ms[:, 4].mean())
+    V = scene.num_vertices
+    attr = 12 * V * ((scene.normal is not None) + (scene.color is not None))
+    bytes_proc = (4 * stats["bin_entries"] + 12 * stats["binned_triangles"] + 16 * V + attr
+                  + 24 * scene.width * scene.height)
+    ops_proc = (OPS_PER_ENTRY * stats["bin_entries"] + OPS_PER_TEST * stats["samples_tested"]
+                + OPS_PER_FRAGMENT * stats["fragments"] + OPS_PER_SHADE[scene.shade_mode] * stats["shaded"])
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    f_mhz = (clk or {}).get("sm_mhz") or float(peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1470.0))
+    alu_peak = n_sm * ALU_OPS_PER_SM_CLK * f_mhz * 1e6 / 1e9  # Gop/s
+    t_hbm = bytes_proc / (hbm * 1e9)
+    t_alu = ops_proc / (alu_peak * 1e9)
+    traffic = None
+    try:
+        with open(PROFILE_TRAFFIC) as f:
+            prof = json.load(f)
+        if prof.get("kernel_hash") == kernel_hash():
+            traffic = prof.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    if t_alu >= t_hbm:
+        achieved = ops_proc / (proc_ms * 1e-3) / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gop/s",
+                "frac": achieved / alu_peak, "traffic": traffic,
+                "peak_note": f"{n_sm} SMs x 128 thread-ops/clk x {f_mhz:.0f} MHz measured SM clock"}
+    else:
+        achieved = bytes_proc / (proc_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": traffic, "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs)"}
+    roof.update({"kernel": "k_process", "kernel_ms": proc_ms, "algorithmic_bytes": bytes_proc,
+                 "algorithmic_ops": ops_proc, "t_hbm_us": t_hbm * 1e6, "t_alu_us": t_alu * 1e6,
+                 "frac_at_2070mhz": (max(t_hbm, ops_proc / (n_sm * 128 * 2070e6)) / (proc_ms * 1e-3)),
+                 "forward_frac": max(t_hbm, t_alu) / (ms * 1e-3)})
+
+    # ---------------------------------------------------------------- end to end
+    e2e = None
+    if not args.no_e2e:
+        names = [n for n in ("pos", "tris", "normal", "color", "mvp", "light_dir") if getattr(ds, n) is not None]
+        host_in = {n: getattr(ds, n).cpu().pin_memory() for n in names}
+        key_h = torch.empty_like(fb.key, device="cpu").pin_memory()
+        rgba_h = torch.empty_like(fb.rgba, device="cpu").pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in host_in.values())
+        d2h = key_h.numel() * 8 + rgba_h.numel() * 4
+        Ke = min(K, args.e2e_steps)
+        pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(Ke)]
+        for _ in range(3):
+            r.render_from_host(host_in, ds, fb, key_h, rgba_h)
+        barrier()
+        for k in range(Ke):
+            flush.zero_()
+            pairs[k][0].record(stream)
+            r.render_from_host(host_in, ds, fb, key_h, rgba_h)
+            pairs[k][1].record(stream)
+        barrier()
+        e_ms = sum(a.elapsed_time(b) for a, b in pairs) / Ke
+        if dist is not None:
+            t = torch.tensor([e_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": world * T / (e_ms * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e_ms, "steps": Ke}
+        if r.status()[0] != 0:
+            raise RuntimeError("status error after the end-to-end loop")
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic", "config": cfg, "shaded_gfrag_s": shaded_gfrag,
+            "stage_ms": {n: float(stage_ms[:, i].mean()) for i, n in
+                         enumerate(["vertex", "setup_count", "scan", "scatter", "process"])},
+            "work": {**stats, "covered_pixels": covered},
+            "wall_ms_incl_flush": 1e3 * wall / K,
+            "roofline": roof, "clocks": clk, "e2e": e2e,
+            "gpu_launches": 5 * K,
+            "parity": "depth/ID bit-exact vs the CPU oracle in tests/test_gpu_parity.py (same workload)"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(scene, args.cpu_seconds)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--bins", type=int, default=16)
+    ap.add_argument("--schedule", default="static", choices=["static", "dynamic", "hardware"])
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    sys.exit(run_reference(args) if args.impl == "reference" else run_ours(args))
+
+
+if __name__ == "__main__":
+    main()

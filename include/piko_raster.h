@@ -1,0 +1,205 @@
+/*
+ * piko_raster.h -- C ABI of the GB300 binned forward rasterizer.
+ *
+ * The library implements the spatially binned raster pipeline of
+ * "Piko: A Design Framework for Programmable Graphics Pipelines" (Patney et
+ * al., arXiv 1404.6293) as fixed CUDA kernels for sm_103a: a vertex stage,
+ * fixed-point triangle setup, AssignBin into screen tiles (count, scan,
+ * scatter), a Schedule of tiles onto CTAs, and a per-tile Process stage that
+ * resolves coverage, depth and shading.  Sec. 4.1 of the paper (Table of
+ * phases: AssignBin per primitive, Schedule per bin, Process per bin) gives
+ * the stage structure; Sec. 7.1 names the raster stages (vertex shader,
+ * rasterizer, fragment shader, depth test, composite); Listing 1 gives the
+ * Lambert fragment shader.
+ *
+ * Conventions for every call:
+ *  - All data pointers are CUDA device pointers owned by the caller, except
+ *    where a parameter says host.  The library never frees caller memory.
+ *  - Calls enqueue work on the caller's stream (a cudaStream_t passed as
+ *    void*, NULL = legacy default stream) and return without waiting, except
+ *    where stated.  Host-side argument checks are synchronous.
+ *  - Every int-returning call returns a PIKO_* status; on failure
+ *    piko_raster_last_error() describes it.  Conditions found on the device
+ *    (bad index, bin-list overflow, timeout) are recorded in a device status
+ *    word that piko_raster_status() reads.
+ *  - A handle owns its scratch memory (vertex and bin buffers) and is not
+ *    thread-safe; use one handle per host thread.
+ *  - Pixel (x, y) is stored at y*width + x, row 0 at the top of the image.
+ *
+ * Rasterization rules (the paper is silent on bit-level rules; these are the
+ * library's definition, identical to its CPU oracle):
+ *  - clip = M * pos in float32, rows summed left to right without fused
+ *    multiply-add; a vertex with clip.w <= 0 or NaN, NDC z outside [-1,1],
+ *    or a snapped coordinate outside +-2^23 culls its triangles.
+ *  - viewport: sx = (x*0.5+0.5)*W, sy = (0.5-y*0.5)*H, sz = (z*0.5+0.5)*(2^24-1);
+ *    16.8 fixed point X = rint(256 sx), Y = rint(256 sy), Z = rint(sz).
+ *  - int64 edge functions, top-left fill rule, samples at pixel centres;
+ *    depth z = floor(sum_i w_i Z_i / A) exactly; the pixel keeps the
+ *    minimum of key = (z << 32) | triangle index (nearest wins, ties to the
+ *    lower index).  Empty pixels keep key 0xFFFFFFFFFFFFFFFF.
+ */
+#ifndef PIKO_RASTER_H
+#define PIKO_RASTER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define PIKO_OK 0
+#define PIKO_ERR_INVALID_ARG 1 /* rejected on the host; nothing was enqueued    */
+#define PIKO_ERR_CUDA 2        /* a CUDA call failed; see piko_raster_last_error */
+#define PIKO_ERR_OOM 3         /* scratch allocation failed                      */
+#define PIKO_ERR_OVERFLOW 4    /* bin lists exceeded the reserved capacity       */
+#define PIKO_ERR_TIMEOUT 5     /* a bounded device-side wait gave up             */
+#define PIKO_ERR_BAD_INDEX 6   /* a triangle referenced a vertex outside [0, V)  */
+
+/* ---- tile schedules (Sec. 4.3, Schedule directives; Sec. 6) ------------ */
+#define PIKO_SCHED_STATIC 0   /* DirectMap: persistent CTA c takes tiles c, c+G, c+2G, ...   */
+#define PIKO_SCHED_DYNAMIC 1  /* LoadBalance: persistent CTAs pop tiles from an atomic queue */
+#define PIKO_SCHED_HARDWARE 2 /* one CTA per tile, balanced by the hardware block scheduler
+                                 (the schedule elimination of Sec. 5.2.2)                   */
+
+/* ---- shading modes ---------------------------------------------------- */
+#define PIKO_SHADE_GOURAUD 0 /* rgb = sum b_i c_i                                         */
+#define PIKO_SHADE_LAMBERT 1 /* rgb = albedo * max(0, n . L), Listing 1                    */
+#define PIKO_SHADE_GBUFFER 2 /* no colour; FP16 normal and albedo for a deferred light pass */
+
+/* ---- options for piko_raster_set_option ------------------------------- */
+#define PIKO_OPT_THREADS_PER_TILE 1 /* CTA size of the Process stage: 64, 128, 256 or 512
+                                       (the threads-per-bin knob of Listing 1 / Sec. 6)   */
+#define PIKO_OPT_UNCLAMPED 2        /* 1: Lambert without the max(0, .) clamp, exactly as
+                                       Listing 1 prints it; default 0                      */
+#define PIKO_OPT_CHECK_CAPACITY 3   /* 1 (default): forward reads the bin-list size back
+                                       after the scan (one host sync) and grows scratch
+                                       before scattering; 0: no sync, overflow is reported
+                                       as PIKO_ERR_OVERFLOW by piko_raster_status          */
+#define PIKO_OPT_SCHEDULE 4         /* change the schedule (PIKO_SCHED_*)                   */
+#define PIKO_OPT_SMALL_TRI_PIXELS 5 /* triangles whose box inside a tile has at most this
+                                       many pixels are rasterized by one thread; larger ones
+                                       by a whole warp (default 32)                         */
+#define PIKO_OPT_STATS 6            /* 1: the Process stage also counts its work (see
+                                       piko_raster_stats); default 0                        */
+
+/* Stage boundaries of one forward pass, for piko_raster_set_stage_events. */
+#define PIKO_NUM_STAGE_EVENTS 6 /* before vertex, after vertex, after setup+count, after scan,
+                                   after scatter, after process                             */
+
+typedef struct piko_raster piko_raster; /* opaque */
+
+/* A triangle list with per-vertex attributes (the input of the raster
+ * pipeline, Sec. 7.1).  All pointers are device memory, caller-owned. */
+typedef struct piko_scene {
+  int32_t width, height;      /* framebuffer size in pixels, 1..32767          */
+  int32_t num_vertices;       /* V >= 0                                         */
+  int32_t num_triangles;      /* T >= 0                                         */
+  const float *pos;           /* [V][4] homogeneous x,y,z,w; 16-byte aligned    */
+  const int32_t *tris;        /* [T][3] vertex indices; 16-byte aligned         */
+  const float *color;         /* [V][3] RGB (albedo), or NULL                   */
+  const float *normal;        /* [V][3], required by LAMBERT and GBUFFER        */
+  const float *mvp;           /* [16] row-major 4x4 applied to pos, NULL = I    */
+  const float *light_dir;     /* [3] directional light L, used as given         */
+  int32_t shade_mode;         /* PIKO_SHADE_*                                   */
+  int32_t reserved;           /* must be 0                                      */
+} piko_scene;
+
+/* Caller-owned device outputs of a forward pass. */
+typedef struct piko_framebuffer {
+  uint64_t *key;     /* [H][W] (depth << 32) | triangle index; required              */
+  float *rgba;       /* [H][W][4] shaded colour, alpha 1 where covered; NULL allowed */
+  void *gbuf_normal; /* [H][W][4] binary16 (nx, ny, nz, 0), GBUFFER mode only        */
+  void *gbuf_albedo; /* [H][W][4] binary16 (r, g, b, 1),   GBUFFER mode only        */
+} piko_framebuffer;
+
+/* Creates a rasterizer for width x height framebuffers with bin_w x bin_h
+ * pixel tiles (each in {8, 16, 32, 64}; Sec. 3 and the bin-size template
+ * parameters of Listing 1) and a PIKO_SCHED_* tile schedule.  Returns NULL
+ * on invalid arguments (width or height outside 1..32767) or if CUDA fails.
+ * Allocates a little device memory on the current device; larger scratch
+ * is allocated on first use or by piko_raster_reserve. */
+piko_raster *piko_raster_create(int width, int height, int bin_w, int bin_h, int schedule);
+
+/* Frees the handle's scratch memory (synchronizes the device first). */
+void piko_raster_destroy(piko_raster *h);
+
+/* Forward pass (Sec. 7.1 stages; AssignBin/Schedule/Process of Sec. 4.1):
+ * vertex stage -> triangle setup and per-bin counts -> scan -> scatter of
+ * triangle indices into bin lists -> per-tile coverage, depth and shading.
+ * scene->width/height must equal the handle's.  Writes every pixel of
+ * fb->key and of fb->rgba (if not NULL; zero where empty) or, in GBUFFER
+ * mode, of fb->gbuf_normal and fb->gbuf_albedo.  Asynchronous unless
+ * PIKO_OPT_CHECK_CAPACITY is 1 (the default), which adds one host sync
+ * after the scan.  Returns PIKO_ERR_INVALID_ARG for bad sizes, NULL
+ * required pointers, misaligned pos/tris, or a shade mode without the
+ * attributes it needs. */
+int piko_raster_forward(piko_raster *h, const piko_scene *scene, piko_framebuffer *fb,
+                        void *cuda_stream);
+
+/* Gradients of a loss through shading with visibility held fixed by a
+ * previous forward's fwd->key (the coverage stays exact integer
+ * arithmetic).  dl_drgba [H][W][4] is dLoss/d(rgba) (alpha ignored).
+ * Accumulates (+=) into dl_dcolor [V][3], dl_dnormal [V][3] and dl_dlight
+ * [3]; any of them may be NULL to skip it.  GOURAUD: colour only; LAMBERT:
+ * colour (if scene->color), normal and light.  The caller zeroes the
+ * outputs.  Not defined by the paper; the gradients are those of the
+ * shading formulas of Listing 1. */
+int piko_raster_backward(piko_raster *h, const piko_scene *scene, const piko_framebuffer *fwd,
+                         const float *dl_drgba, float *dl_dcolor, float *dl_dnormal,
+                         float *dl_dlight, void *cuda_stream);
+
+/* Deferred light pass over a G-buffer written by a GBUFFER forward: for each
+ * covered pixel, sum of n_lights point lights (lights: device [n][4] =
+ * x, y, z in pixel units, intensity) with
+ *   S = (x + 0.5, y + 0.5, depth / (2^24-1) * D),  D = max(W, H), r = D/4,
+ *   rgb = albedo * sum_l I_l max(0, n . (P_l - S)/|P_l - S|) / (1 + |P_l - S|^2 / r^2),
+ * alpha 1; empty pixels get 0.  Shader complexity as the number of lights is
+ * the axis of Fig. (a) of the paper's Sec. 7.2; the light model itself is
+ * this library's.  1 <= n_lights <= 1024. */
+int piko_raster_deferred_light(piko_raster *h, const piko_framebuffer *gbuf, const float *lights,
+                               int n_lights, float *rgba_out, void *cuda_stream);
+
+/* Pre-sizes scratch for scenes of up to max_vertices / max_triangles and
+ * max_bin_entries (triangle, tile) pairs, so that later forwards allocate
+ * nothing (required before capturing forwards in a CUDA graph).
+ * Synchronous. */
+int piko_raster_reserve(piko_raster *h, int64_t max_vertices, int64_t max_triangles,
+                        int64_t max_bin_entries);
+
+/* Sets a PIKO_OPT_* option.  Returns PIKO_ERR_INVALID_ARG for unknown keys
+ * or values. */
+int piko_raster_set_option(piko_raster *h, int key, int value);
+
+/* Waits for the handle's last stream, returns the device status word
+ * (PIKO_OK or the first PIKO_ERR_* recorded since the last call) and clears
+ * it.  If needed_bin_entries is not NULL it receives the bin-list size the
+ * last scan required. */
+int piko_raster_status(piko_raster *h, int64_t *needed_bin_entries);
+
+/* Makes the next piko_raster_forward record the PIKO_NUM_STAGE_EVENTS
+ * caller-created CUDA events (cudaEvent_t passed as void*) on its stream at
+ * the stage boundaries listed above, for per-stage timing without extra
+ * synchronisation.  The events are used by that one forward only.  n must
+ * be PIKO_NUM_STAGE_EVENTS, or 0 with events NULL to cancel. */
+int piko_raster_set_stage_events(piko_raster *h, void *const *events, int n);
+
+/* Work counted by the last forward run with PIKO_OPT_STATS = 1 (waits for
+ * the stream): out[0] bin entries, out[1] pixel samples tested (pixels of
+ * each triangle's bounding box inside each of its tiles), out[2] covered
+ * samples (rasterized fragments, occluded ones included), out[3] covered
+ * pixels after the depth test (shaded fragments), out[4] triangles that
+ * survived culling and reached a bin. */
+int piko_raster_stats(piko_raster *h, int64_t out[5]);
+
+/* Message for the last failing call on this handle (never NULL). */
+const char *piko_raster_last_error(const piko_raster *h);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int piko_raster_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIKO_RASTER_H */

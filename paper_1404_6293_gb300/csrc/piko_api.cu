@@ -1,0 +1,379 @@
+// piko_api.cu -- the C ABI: handles, scratch memory, argument checks, launch order.
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "piko_internal.cuh"
+
+using namespace piko;
+
+int piko_backward_launch(int W, int H, int mode, int unclamped, int T, int V, const int* tris, const int4* vtx,
+                         const float* color,
+                         const float* normal, const float* light, const unsigned long long* key,
+                         const float* dl_drgba, float* dcolor, float* dnormal, float* dlight, int num_sms,
+                         cudaStream_t s);
+
+struct piko_raster {
+  int W, H, bin_w, bin_h, schedule;
+  RasterGeom g;
+  int nbins;
+  int threads = 256;
+  int unclamped = 0;
+  int check_capacity = 1;
+  int small_px = 32;
+  int stats = 0;
+  cudaEvent_t stage_ev[PIKO_NUM_STAGE_EVENTS] = {};
+  bool use_stage_ev = false;
+  int device = 0, num_sms = 0;
+  // scratch (device)
+  int4* vtx = nullptr;
+  long long vcap = 0;
+  BinRect* rect = nullptr;
+  long long tcap = 0;
+  unsigned* bin_count = nullptr;  // zero between frames
+  unsigned* bin_off = nullptr;    // nbins + 1
+  unsigned* cursor = nullptr;
+  unsigned* bin_tris = nullptr;
+  long long ecap = 0;
+  DevStatus* status = nullptr;
+  unsigned long long* h_needed = nullptr;  // pinned
+  cudaStream_t last_stream = nullptr;
+  std::string err;
+};
+
+namespace {
+
+int fail(piko_raster* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+int cuda_fail(piko_raster* h, cudaError_t e, const char* where) {
+  return fail(h, PIKO_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+int ilog2(int v) {
+  int s = 0;
+  while ((1 << s) < v) ++s;
+  return s;
+}
+
+bool valid_bin(int b) { return b == 8 || b == 16 || b == 32 || b == 64; }
+
+template <typename T>
+int grow(piko_raster* h, T** ptr, long long* cap, long long need, const char* what) {
+  if (need <= *cap) return PIKO_OK;
+  long long n = need + need / 4 + 1024;
+  if (*ptr) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaDeviceSynchronize");
+    cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+  }
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(ptr), (size_t)n * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, PIKO_ERR_OOM, std::string("cudaMalloc of ") + what + " failed");
+  }
+  *cap = n;
+  return PIKO_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+int piko_raster_version(void) { return 100; }
+
+piko_raster* piko_raster_create(int width, int height, int bin_w, int bin_h, int schedule) {
+  if (width < 1 || height < 1 || width > 32767 || height > 32767) return nullptr;
+  if (!valid_bin(bin_w) || !valid_bin(bin_h)) return nullptr;
+  if (schedule < PIKO_SCHED_STATIC || schedule > PIKO_SCHED_HARDWARE) return nullptr;
+  piko_raster* h = new piko_raster();
+  h->W = width; h->H = height; h->bin_w = bin_w; h->bin_h = bin_h; h->schedule = schedule;
+  h->g.W = width; h->g.H = height;
+  h->g.bshift_x = ilog2(bin_w); h->g.bshift_y = ilog2(bin_h);
+  h->g.nbx = (width + bin_w - 1) / bin_w;
+  h->g.nby = (height + bin_h - 1) / bin_h;
+  h->nbins = h->g.nbx * h->g.nby;
+  h->threads = bin_w * bin_h >= 256 ? 256 : (bin_w * bin_h < 64 ? 64 : bin_w * bin_h);
+  if (cudaGetDevice(&h->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return nullptr;
+  }
+  bool ok = cudaMalloc(&h->bin_count, sizeof(unsigned) * h->nbins) == cudaSuccess &&
+            cudaMalloc(&h->bin_off, sizeof(unsigned) * (h->nbins + 1)) == cudaSuccess &&
+            cudaMalloc(&h->cursor, sizeof(unsigned) * h->nbins) == cudaSuccess &&
+            cudaMalloc(&h->status, sizeof(DevStatus)) == cudaSuccess &&
+            cudaMallocHost(&h->h_needed, sizeof(unsigned long long)) == cudaSuccess &&
+            cudaMemset(h->bin_count, 0, sizeof(unsigned) * h->nbins) == cudaSuccess &&
+            cudaMemset(h->status, 0, sizeof(DevStatus)) == cudaSuccess &&
+            cudaDeviceSynchronize() == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    piko_raster_destroy(h);
+    return nullptr;
+  }
+  return h;
+}
+
+void piko_raster_destroy(piko_raster* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  cudaFree(h->vtx);
+  cudaFree(h->rect);
+  cudaFree(h->bin_count);
+  cudaFree(h->bin_off);
+  cudaFree(h->cursor);
+  cudaFree(h->bin_tris);
+  cudaFree(h->status);
+  if (h->h_needed) cudaFreeHost(h->h_needed);
+  cudaGetLastError();
+  delete h;
+}
+
+const char* piko_raster_last_error(const piko_raster* h) {
+  if (!h) return "null handle";
+  return h->err.c_str();
+}
+
+int piko_raster_set_option(piko_raster* h, int key, int value) {
+  if (!h) return PIKO_ERR_INVALID_ARG;
+  switch (key) {
+    case PIKO_OPT_THREADS_PER_TILE:
+      if (value != 64 && value != 128 && value != 256 && value != 512)
+        return fail(h, PIKO_ERR_INVALID_ARG, "threads per tile must be 64, 128, 256 or 512");
+      h->threads = value;
+      return PIKO_OK;
+    case PIKO_OPT_UNCLAMPED:
+      if (value != 0 && value != 1) return fail(h, PIKO_ERR_INVALID_ARG, "unclamped must be 0 or 1");
+      h->unclamped = value;
+      return PIKO_OK;
+    case PIKO_OPT_CHECK_CAPACITY:
+      if (value != 0 && value != 1) return fail(h, PIKO_ERR_INVALID_ARG, "check_capacity must be 0 or 1");
+      h->check_capacity = value;
+      return PIKO_OK;
+    case PIKO_OPT_SCHEDULE:
+      if (value < PIKO_SCHED_STATIC || value > PIKO_SCHED_HARDWARE)
+        return fail(h, PIKO_ERR_INVALID_ARG, "unknown schedule");
+      h->schedule = value;
+      return PIKO_OK;
+    case PIKO_OPT_STATS:
+      if (value != 0 && value != 1) return fail(h, PIKO_ERR_INVALID_ARG, "stats must be 0 or 1");
+      h->stats = value;
+      return PIKO_OK;
+    case PIKO_OPT_SMALL_TRI_PIXELS:
+      if (value < 0 || value > 4096) return fail(h, PIKO_ERR_INVALID_ARG, "small-triangle pixels out of range");
+      h->small_px = value;
+      return PIKO_OK;
+    default:
+      return fail(h, PIKO_ERR_INVALID_ARG, "unknown option");
+  }
+}
+
+int piko_raster_reserve(piko_raster* h, int64_t max_vertices, int64_t max_triangles, int64_t max_bin_entries) {
+  if (!h) return PIKO_ERR_INVALID_ARG;
+  if (max_vertices < 0 || max_triangles < 0 || max_bin_entries < 0 || max_vertices > INT32_MAX ||
+      max_triangles > INT32_MAX || max_bin_entries > 0xFFFFFFF0LL)
+    return fail(h, PIKO_ERR_INVALID_ARG, "reserve sizes out of range");
+  int r;
+  if ((r = grow(h, &h->vtx, &h->vcap, max_vertices, "vertex buffer")) != PIKO_OK) return r;
+  if ((r = grow(h, &h->rect, &h->tcap, max_triangles, "bin rectangles")) != PIKO_OK) return r;
+  if ((r = grow(h, &h->bin_tris, &h->ecap, max_bin_entries, "bin lists")) != PIKO_OK) return r;
+  cudaError_t e = cudaDeviceSynchronize();
+  return e == cudaSuccess ? PIKO_OK : cuda_fail(h, e, "reserve");
+}
+
+int piko_raster_status(piko_raster* h, int64_t* needed_bin_entries) {
+  if (!h) return PIKO_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(h->last_stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+  DevStatus st;
+  e = cudaMemcpy(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "status read");
+  e = cudaMemset(h->status, 0, sizeof(unsigned) * 2);  // flags and first_code only
+  if (e != cudaSuccess) return cuda_fail(h, e, "status clear");
+  if (needed_bin_entries) *needed_bin_entries = (int64_t)st.needed;
+  if (st.first_code != 0) {
+    static const char* names[] = {"ok", "invalid argument", "cuda", "out of memory",
+                                  "bin lists overflowed their capacity", "device wait timed out",
+                                  "triangle index outside [0, V)"};
+    h->err = st.first_code < 7 ? names[st.first_code] : "device error";
+  }
+  return (int)st.first_code;
+}
+
+static int check_scene(piko_raster* h, const piko_scene* s) {
+  if (!s) return fail(h, PIKO_ERR_INVALID_ARG, "scene is NULL");
+  if (s->width != h->W || s->height != h->H)
+    return fail(h, PIKO_ERR_INVALID_ARG, "scene size differs from the rasterizer's");
+  if (s->num_vertices < 0 || s->num_triangles < 0) return fail(h, PIKO_ERR_INVALID_ARG, "negative counts");
+  if (s->num_vertices > 0 && (!s->pos || !aligned16(s->pos)))
+    return fail(h, PIKO_ERR_INVALID_ARG, "pos must be a 16-byte aligned device pointer");
+  if (s->num_triangles > 0 && (!s->tris || !aligned16(s->tris)))
+    return fail(h, PIKO_ERR_INVALID_ARG, "tris must be a 16-byte aligned device pointer");
+  if (s->shade_mode < PIKO_SHADE_GOURAUD || s->shade_mode > PIKO_SHADE_GBUFFER)
+    return fail(h, PIKO_ERR_INVALID_ARG, "unknown shade mode");
+  if (s->shade_mode == PIKO_SHADE_GOURAUD && !s->color && s->num_triangles > 0)
+    return fail(h, PIKO_ERR_INVALID_ARG, "Gouraud shading needs per-vertex colours");
+  if (s->shade_mode != PIKO_SHADE_GOURAUD && !s->normal && s->num_triangles > 0)
+    return fail(h, PIKO_ERR_INVALID_ARG, "Lambert / G-buffer shading needs per-vertex normals");
+  if (s->shade_mode == PIKO_SHADE_LAMBERT && !s->light_dir)
+    return fail(h, PIKO_ERR_INVALID_ARG, "Lambert shading needs light_dir");
+  if (s->reserved != 0) return fail(h, PIKO_ERR_INVALID_ARG, "reserved field must be 0");
+  return PIKO_OK;
+}
+
+int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* fb, void* cuda_stream) {
+  if (!h) return PIKO_ERR_INVALID_ARG;
+  int r = check_scene(h, s);
+  if (r != PIKO_OK) return r;
+  if (!fb || !fb->key) return fail(h, PIKO_ERR_INVALID_ARG, "framebuffer key is required");
+  if (s->shade_mode == PIKO_SHADE_GBUFFER && (!fb->gbuf_normal || !fb->gbuf_albedo))
+    return fail(h, PIKO_ERR_INVALID_ARG, "G-buffer mode needs gbuf_normal and gbuf_albedo");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  h->last_stream = st;
+  const int V = s->num_vertices, T = s->num_triangles;
+  if ((r = grow(h, &h->vtx, &h->vcap, V, "vertex buffer")) != PIKO_OK) return r;
+  if ((r = grow(h, &h->rect, &h->tcap, T, "bin rectangles")) != PIKO_OK) return r;
+  if (h->ecap == 0 && (r = grow(h, &h->bin_tris, &h->ecap, (long long)T * 2 + 4096, "bin lists")) != PIKO_OK)
+    return r;
+
+  const bool ev = h->use_stage_ev;
+  h->use_stage_ev = false;
+  if (ev) cudaEventRecord(h->stage_ev[0], st);
+  if (h->stats) cudaMemsetAsync(&h->status->tests, 0, 4 * sizeof(unsigned long long), st);
+  launch_vertex(h->W, h->H, V, s->pos, s->mvp, h->vtx, h->num_sms, st);
+  if (ev) cudaEventRecord(h->stage_ev[1], st);
+  for (int attempt = 0;; ++attempt) {
+    if (h->stats && attempt > 0) cudaMemsetAsync(&h->status->binned, 0, sizeof(unsigned long long), st);
+    launch_setup_count(h->g, T, s->tris, V, h->vtx, h->rect, h->bin_count, h->status, h->stats, h->num_sms, st);
+    if (ev) cudaEventRecord(h->stage_ev[2], st);
+    launch_scan(h->nbins, h->bin_count, h->bin_off, h->cursor, (unsigned long long)h->ecap, h->status, st);
+    if (ev) cudaEventRecord(h->stage_ev[3], st);
+    if (!h->check_capacity) break;
+    cudaError_t e = cudaMemcpyAsync(h->h_needed, &h->status->needed, sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "bin-list size read-back");
+    const long long need = (long long)*h->h_needed;
+    if (need <= h->ecap) break;
+    if (attempt > 0 || need > 0xFFFFFFF0LL) return fail(h, PIKO_ERR_OVERFLOW, "bin lists too large");
+    if ((r = grow(h, &h->bin_tris, &h->ecap, need, "bin lists")) != PIKO_OK) return r;
+    // the failed scan recorded an overflow and zeroed the counts: clear and count again
+    e = cudaMemsetAsync(h->status, 0, sizeof(unsigned) * 2, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "status clear");
+  }
+  launch_scatter(h->g, T, h->rect, h->cursor, h->bin_tris, h->status, h->num_sms, st);
+  if (ev) cudaEventRecord(h->stage_ev[4], st);
+
+  ProcessParams p;
+  p.g = h->g;
+  p.ntiles = h->nbins;
+  p.schedule = h->schedule;
+  p.small_px = h->small_px;
+  p.mode = s->shade_mode;
+  p.unclamped = h->unclamped;
+  p.stats = h->stats;
+  p.tris = s->tris;
+  p.vtx = h->vtx;
+  p.color = s->color;
+  p.normal = s->normal;
+  p.light = s->light_dir;
+  p.bin_off = h->bin_off;
+  p.bin_tris = h->bin_tris;
+  p.key_out = reinterpret_cast<unsigned long long*>(fb->key);
+  p.rgba_out = reinterpret_cast<float4*>(fb->rgba);
+  p.gnorm_out = reinterpret_cast<uint2*>(fb->gbuf_normal);
+  p.galb_out = reinterpret_cast<uint2*>(fb->gbuf_albedo);
+  p.st = h->status;
+  int grid = h->nbins;
+  if (h->schedule != PIKO_SCHED_HARDWARE) {
+    int per_sm = 0;
+    cudaError_t e = process_occupancy(h->threads, h->bin_w * h->bin_h, &per_sm);
+    if (e != cudaSuccess) return cuda_fail(h, e, "occupancy query");
+    if (per_sm < 1) per_sm = 1;
+    grid = per_sm * h->num_sms < h->nbins ? per_sm * h->num_sms : h->nbins;
+  }
+  cudaError_t e = launch_process(p, h->threads, grid, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "process launch");
+  if (ev) cudaEventRecord(h->stage_ev[5], st);
+  return PIKO_OK;
+}
+
+int piko_raster_set_stage_events(piko_raster* h, void* const* events, int n) {
+  if (!h) return PIKO_ERR_INVALID_ARG;
+  if (n == 0 && !events) {
+    h->use_stage_ev = false;
+    return PIKO_OK;
+  }
+  if (n != PIKO_NUM_STAGE_EVENTS || !events) return fail(h, PIKO_ERR_INVALID_ARG, "need PIKO_NUM_STAGE_EVENTS events");
+  for (int i = 0; i < n; ++i) {
+    if (!events[i]) return fail(h, PIKO_ERR_INVALID_ARG, "NULL event");
+    h->stage_ev[i] = reinterpret_cast<cudaEvent_t>(events[i]);
+  }
+  h->use_stage_ev = true;
+  return PIKO_OK;
+}
+
+int piko_raster_stats(piko_raster* h, int64_t out[5]) {
+  if (!h || !out) return PIKO_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(h->last_stream);
+  DevStatus st;
+  if (e == cudaSuccess) e = cudaMemcpy(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "stats read");
+  out[0] = (int64_t)st.needed;
+  out[1] = (int64_t)st.tests;
+  out[2] = (int64_t)st.frags;
+  out[3] = (int64_t)st.shaded;
+  out[4] = (int64_t)st.binned;
+  return PIKO_OK;
+}
+
+int piko_raster_backward(piko_raster* h, const piko_scene* s, const piko_framebuffer* fwd, const float* dl_drgba,
+                         float* dl_dcolor, float* dl_dnormal, float* dl_dlight, void* cuda_stream) {
+  if (!h) return PIKO_ERR_INVALID_ARG;
+  int r = check_scene(h, s);
+  if (r != PIKO_OK) return r;
+  if (s->shade_mode == PIKO_SHADE_GBUFFER)
+    return fail(h, PIKO_ERR_INVALID_ARG, "backward is defined for Gouraud and Lambert shading");
+  if (!fwd || !fwd->key || !dl_drgba) return fail(h, PIKO_ERR_INVALID_ARG, "backward needs the forward key and dL/drgba");
+  if (!aligned16(dl_drgba)) return fail(h, PIKO_ERR_INVALID_ARG, "dl_drgba must be 16-byte aligned");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  h->last_stream = st;
+  if ((r = grow(h, &h->vtx, &h->vcap, s->num_vertices, "vertex buffer")) != PIKO_OK) return r;
+  // the vertex stage runs again so that backward does not depend on which
+  // scene the handle rasterized last
+  launch_vertex(h->W, h->H, s->num_vertices, s->pos, s->mvp, h->vtx, h->num_sms, st);
+  if (piko_backward_launch(h->W, h->H, s->shade_mode, h->unclamped, s->num_triangles, s->num_vertices, s->tris,
+                           h->vtx, s->color, s->normal,
+                           s->light_dir, reinterpret_cast<const unsigned long long*>(fwd->key), dl_drgba, dl_dcolor,
+                           dl_dnormal, dl_dlight, h->num_sms, st) != 0)
+    return cuda_fail(h, cudaGetLastError(), "backward launch");
+  return PIKO_OK;
+}
+
+int piko_raster_deferred_light(piko_raster* h, const piko_framebuffer* gbuf, const float* lights, int n_lights,
+                               float* rgba_out, void* cuda_stream) {
+  if (!h) return PIKO_ERR_INVALID_ARG;
+  if (!gbuf || !gbuf->key || !gbuf->gbuf_normal || !gbuf->gbuf_albedo || !rgba_out || !lights)
+    return fail(h, PIKO_ERR_INVALID_ARG, "deferred light needs key, G-buffer, lights and output");
+  if (n_lights < 1 || n_lights > 1024) return fail(h, PIKO_ERR_INVALID_ARG, "n_lights must be in 1..1024");
+  if (!aligned16(lights) || !aligned16(rgba_out) || !aligned16(gbuf->gbuf_normal) || !aligned16(gbuf->gbuf_albedo))
+    return fail(h, PIKO_ERR_INVALID_ARG, "lights, G-buffer and output must be 16-byte aligned");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  h->last_stream = st;
+  launch_deferred_light(h->W, h->H, reinterpret_cast<const unsigned long long*>(gbuf->key), reinterpret_cast<const uint2*>(gbuf->gbuf_normal),
+                        reinterpret_cast<const uint2*>(gbuf->gbuf_albedo), reinterpret_cast<const float4*>(lights),
+                        n_lights, reinterpret_cast<float4*>(rgba_out), h->num_sms, st);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? PIKO_OK : cuda_fail(h, e, "deferred light launch");
+}
+
+}  // extern "C"

@@ -1,0 +1,183 @@
+// piko_backward.cu -- attribute gradients through the shading of the forward pass.
+//
+// Visibility is held fixed by the forward key buffer, so coverage stays exact
+// integer arithmetic and only the fragment shader is differentiated: for the
+// Lambert shader of Listing 1 (rgb = albedo * s, s = max(0, n . L),
+// n = sum b_i n_i, albedo = sum b_i c_i) and for Gouraud (rgb = sum b_i c_i).
+// Per pixel, with g = dLoss/drgb:
+//   dL/dc_i += s * b_i * g        (Gouraud: b_i * g)
+//   dL/dn_i += (g . albedo) b_i L   when s > 0 (or unclamped)
+//   dL/dL   += (g . albedo) n
+// Lanes of a warp whose pixels share a winning triangle are summed in shared
+// memory and one lane issues the atomics for the group; the light gradient
+// is reduced over the whole CTA before its single atomic.
+#include "piko_internal.cuh"
+
+namespace piko {
+
+struct BackwardParams {
+  int W, H, mode, unclamped;
+  int T, V;
+  const int* tris;
+  const int4* vtx;
+  const float* color;
+  const float* normal;
+  const float* light;
+  const unsigned long long* key;
+  const float4* dl_drgba;
+  float* dcolor;
+  float* dnormal;
+  float* dlight;
+};
+
+constexpr int BWD_THREADS = 256;
+constexpr int BWD_VALS = 18;  // per pixel: 3 vertices x (3 colour + 3 normal)
+
+__global__ void __launch_bounds__(BWD_THREADS) k_backward(BackwardParams p) {
+  __shared__ float sval[BWD_THREADS / 32][BWD_VALS][32];
+  __shared__ float sred[BWD_THREADS / 32][3];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  float L0 = 0.f, L1 = 0.f, L2 = 0.f;
+  if (p.mode == PIKO_SHADE_LAMBERT) {
+    L0 = __ldg(p.light); L1 = __ldg(p.light + 1); L2 = __ldg(p.light + 2);
+  }
+  float gl0 = 0.f, gl1 = 0.f, gl2 = 0.f;  // this thread's share of dL/dL
+  const int npix = p.W * p.H;  // W, H <= 32767
+  const int stride = gridDim.x * blockDim.x;
+  // warp-uniform trip count so that the warp collectives below stay converged
+  for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < npix; base += stride) {
+    const int i = base + lane;
+    unsigned long long k = KEY_EMPTY;
+    if (i < npix) k = __ldg(p.key + i);
+    // a key naming a triangle outside this scene, or one the vertex stage
+    // culls, contributes nothing (it cannot come from this scene's forward)
+    bool hit = k != KEY_EMPTY && (unsigned)(k & 0xFFFFFFFFu) < (unsigned)p.T;
+    unsigned t = hit ? (unsigned)(k & 0xFFFFFFFFu) : 0xFFFFFFFFu;
+    TriSetup s;
+    if (hit) {
+      const int ia = __ldg(p.tris + 3 * (size_t)t), ib = __ldg(p.tris + 3 * (size_t)t + 1),
+                ic = __ldg(p.tris + 3 * (size_t)t + 2);
+      hit = ia >= 0 && ia < p.V && ib >= 0 && ib < p.V && ic >= 0 && ic < p.V && setup_triangle(ia, ib, ic, p.vtx, s);
+      if (!hit) t = 0xFFFFFFFFu;
+    }
+    float v[BWD_VALS];
+#pragma unroll
+    for (int q = 0; q < BWD_VALS; ++q) v[q] = 0.f;
+    int vid[3] = {0, 0, 0};
+    if (hit) {
+      const int y = i / p.W, x = i - y * p.W;
+      vid[0] = s.v0; vid[1] = s.v1; vid[2] = s.v2;
+      const long long Px = 256LL * x + 128, Py = 256LL * y + 128;
+      const long long w0 = (long long)(s.X2 - s.X1) * (Py - s.Y1) - (long long)(s.Y2 - s.Y1) * (Px - s.X1);
+      const long long w1 = (long long)(s.X0 - s.X2) * (Py - s.Y2) - (long long)(s.Y0 - s.Y2) * (Px - s.X2);
+      const long long w2 = (long long)(s.X1 - s.X0) * (Py - s.Y0) - (long long)(s.Y1 - s.Y0) * (Px - s.X0);
+      const float fA = (float)s.A;
+      const float b[3] = {__fdiv_rn((float)w0, fA), __fdiv_rn((float)w1, fA), __fdiv_rn((float)w2, fA)};
+      const float4 g = __ldg(p.dl_drgba + i);
+      if (p.mode == PIKO_SHADE_GOURAUD) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          v[6 * j + 0] = g.x * b[j]; v[6 * j + 1] = g.y * b[j]; v[6 * j + 2] = g.z * b[j];
+        }
+      } else {
+        float a0 = 0.80f, a1 = 0.75f, a2 = 0.65f;  // material of Listing 1 without colours
+        if (p.color) {
+          a0 = a1 = a2 = 0.f;
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const float* c = p.color + 3 * (size_t)vid[j];
+            a0 += b[j] * __ldg(c); a1 += b[j] * __ldg(c + 1); a2 += b[j] * __ldg(c + 2);
+          }
+        }
+        float n0 = 0.f, n1 = 0.f, n2 = 0.f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const float* n = p.normal + 3 * (size_t)vid[j];
+          n0 += b[j] * __ldg(n); n1 += b[j] * __ldg(n + 1); n2 += b[j] * __ldg(n + 2);
+        }
+        const float d = n0 * L0 + n1 * L1 + n2 * L2;
+        const bool active = p.unclamped || d > 0.f;
+        const float sh = p.unclamped ? d : fmaxf(d, 0.f);
+        const float G = active ? (g.x * a0 + g.y * a1 + g.z * a2) : 0.f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          if (p.color) {
+            v[6 * j + 0] = g.x * sh * b[j]; v[6 * j + 1] = g.y * sh * b[j]; v[6 * j + 2] = g.z * sh * b[j];
+          }
+          v[6 * j + 3] = G * b[j] * L0; v[6 * j + 4] = G * b[j] * L1; v[6 * j + 5] = G * b[j] * L2;
+        }
+        gl0 += G * n0; gl1 += G * n1; gl2 += G * n2;
+      }
+    }
+    // group lanes by winning triangle; the lowest lane of each group sums
+    // the group's contributions and issues the atomics
+    const unsigned grp = __match_any_sync(FULL_MASK, t);
+    const bool leader = hit && (grp & lt_mask) == 0u;
+    const bool alone = __popc(grp) == 1;
+    if (!alone) {
+#pragma unroll
+      for (int q = 0; q < BWD_VALS; ++q) sval[warp][q][lane] = v[q];
+    }
+    __syncwarp();
+    if (leader) {
+      if (!alone) {
+        unsigned rest = grp & ~(1u << lane);
+        while (rest) {
+          const int src = __ffs(rest) - 1;
+          rest &= rest - 1;
+#pragma unroll
+          for (int q = 0; q < BWD_VALS; ++q) v[q] += sval[warp][q][src];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        if (p.dcolor && (p.mode == PIKO_SHADE_GOURAUD || p.color)) {
+          float* dc = p.dcolor + 3 * (size_t)vid[j];
+          atomicAdd(dc, v[6 * j]); atomicAdd(dc + 1, v[6 * j + 1]); atomicAdd(dc + 2, v[6 * j + 2]);
+        }
+        if (p.dnormal && p.mode == PIKO_SHADE_LAMBERT) {
+          float* dn = p.dnormal + 3 * (size_t)vid[j];
+          atomicAdd(dn, v[6 * j + 3]); atomicAdd(dn + 1, v[6 * j + 4]); atomicAdd(dn + 2, v[6 * j + 5]);
+        }
+      }
+    }
+    __syncwarp();
+  }
+  if (p.dlight && p.mode == PIKO_SHADE_LAMBERT) {
+    for (int o = 16; o > 0; o >>= 1) {
+      gl0 += __shfl_xor_sync(FULL_MASK, gl0, o);
+      gl1 += __shfl_xor_sync(FULL_MASK, gl1, o);
+      gl2 += __shfl_xor_sync(FULL_MASK, gl2, o);
+    }
+    if (lane == 0) { sred[warp][0] = gl0; sred[warp][1] = gl1; sred[warp][2] = gl2; }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      float acc = 0.f;
+      for (int w = 0; w < BWD_THREADS / 32; ++w) acc += sred[w][threadIdx.x];
+      atomicAdd(p.dlight + threadIdx.x, acc);
+    }
+  }
+}
+
+}  // namespace piko
+
+using namespace piko;
+
+int piko_backward_launch(int W, int H, int mode, int unclamped, int T, int V, const int* tris, const int4* vtx,
+                         const float* color,
+                         const float* normal, const float* light, const unsigned long long* key,
+                         const float* dl_drgba, float* dcolor, float* dnormal, float* dlight, int num_sms,
+                         cudaStream_t s) {
+  BackwardParams p;
+  p.W = W; p.H = H; p.mode = mode; p.unclamped = unclamped; p.T = T; p.V = V;
+  p.tris = tris; p.vtx = vtx; p.color = color; p.normal = normal; p.light = light;
+  p.key = key; p.dl_drgba = reinterpret_cast<const float4*>(dl_drgba);
+  p.dcolor = dcolor; p.dnormal = dnormal; p.dlight = dlight;
+  const long long npix = (long long)W * H;
+  long long blocks = (npix + BWD_THREADS - 1) / BWD_THREADS;
+  if (blocks > (long long)num_sms * 4) blocks = (long long)num_sms * 4;
+  if (blocks < 1) blocks = 1;
+  k_backward<<<(int)blocks, BWD_THREADS, 0, s>>>(p);
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}

@@ -1,0 +1,170 @@
+// piko_internal.cuh -- shared declarations of the CUDA rasterizer (not part of the C ABI).
+//
+// Fixed-point conventions (the library's definition; the paper leaves
+// rasterization bits open):
+//   16.8 snapped vertex coordinates X, Y (int32, |X| < 2^23), depth Z in
+//   [0, 2^24-1]; edge functions in int64; pixel centres at 256*p + 128;
+//   key = (z << 32) | triangle index, minimum wins.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/piko_raster.h"
+
+namespace piko {
+
+constexpr unsigned long long KEY_EMPTY = 0xFFFFFFFFFFFFFFFFull;
+constexpr unsigned FULL_MASK = 0xFFFFFFFFu;
+
+// Device-side status word, one per handle.
+struct DevStatus {
+  unsigned int flags;           // bit c set when PIKO_ERR c was recorded
+  unsigned int first_code;      // first PIKO_ERR_* recorded (0 = none)
+  unsigned long long needed;    // bin entries the last scan required
+  unsigned int queue_head;      // tile counter of the dynamic schedule
+  unsigned int pad[3];
+  unsigned long long tests;     // statistics (PIKO_OPT_STATS): pixel samples tested
+  unsigned long long frags;     // covered samples
+  unsigned long long shaded;    // covered pixels after the depth test
+  unsigned long long binned;    // triangles that reached at least one bin
+};
+
+// Screen and bin geometry of one framebuffer.
+struct RasterGeom {
+  int W, H;
+  int bshift_x, bshift_y;  // log2 of bin width / height
+  int nbx, nby;            // bins per row / column
+};
+
+// Per-triangle bin rectangle from the count pass: x0 | y0 << 16, x1 | y1 << 16.
+// A culled triangle stores x0 = 0xFFFF (x0 > x1).
+struct BinRect {
+  unsigned int lo, hi;
+};
+
+__device__ __forceinline__ void record_error(DevStatus* st, unsigned code) {
+  atomicCAS(&st->first_code, 0u, code);
+  atomicOr(&st->flags, 1u << code);
+}
+
+// ------------------------------------------------------------------ setup
+// Triangle after snapping and orientation: slots 0..2 with A > 0.
+struct TriSetup {
+  int X0, Y0, X1, Y1, X2, Y2;
+  int Z0, Z1, Z2;
+  int v0, v1, v2;   // original vertex indices in slot order
+  long long A;      // twice the area, 16.8 units squared, > 0
+};
+
+// Reads the three snapped vertices of triangle (a, b, c) and orients it.
+// Returns false if a vertex was culled by the vertex stage or A == 0.
+__device__ __forceinline__ bool setup_triangle(int a, int b, int c, const int4* __restrict__ vtx,
+                                               TriSetup& s) {
+  const int4 p0 = __ldg(vtx + a), p1 = __ldg(vtx + b), p2 = __ldg(vtx + c);
+  if (!(p0.w & p1.w & p2.w)) return false;
+  long long A = (long long)(p1.x - p0.x) * (long long)(p2.y - p0.y) -
+                (long long)(p2.x - p0.x) * (long long)(p1.y - p0.y);
+  if (A == 0) return false;
+  s.X0 = p0.x; s.Y0 = p0.y; s.Z0 = p0.z; s.v0 = a;
+  if (A > 0) {
+    s.X1 = p1.x; s.Y1 = p1.y; s.Z1 = p1.z; s.v1 = b;
+    s.X2 = p2.x; s.Y2 = p2.y; s.Z2 = p2.z; s.v2 = c;
+    s.A = A;
+  } else {
+    s.X1 = p2.x; s.Y1 = p2.y; s.Z1 = p2.z; s.v1 = c;
+    s.X2 = p1.x; s.Y2 = p1.y; s.Z2 = p1.z; s.v2 = b;
+    s.A = -A;
+  }
+  return true;
+}
+
+// Pixel columns / rows whose centres lie inside [min, max] of the snapped
+// coordinates, clipped to [lo, hi].  ceil((v-128)/256) and floor((v-128)/256)
+// with arithmetic shifts (floor for negatives).
+__device__ __forceinline__ void centre_range(int vmin, int vmax, int lo, int hi, int& p0, int& p1) {
+  p0 = max((vmin - 128 + 255) >> 8, lo);
+  p1 = min((vmax - 128) >> 8, hi);
+}
+
+// Edge a->b top-left test in the A > 0, y-down orientation.
+__device__ __forceinline__ int top_left(int dx, int dy) { return (dy < 0 || (dy == 0 && dx > 0)) ? 1 : 0; }
+
+// floor(n / A) for A > 0 and |n / A| < 2^25, exact.  The float estimate
+// (relative error below 2^-21) is within a few units of the quotient; the
+// integer remainder then moves it to the unique q with 0 <= n - q*A < A.
+__device__ __forceinline__ long long floor_div_est(long long n, long long A, float rA) {
+  long long q = (long long)floorf(__fmul_rn((float)n, rA));
+  long long r = n - q * A;
+  while (r < 0) { --q; r += A; }
+  while (r >= A) { ++q; r -= A; }
+  return q;
+}
+
+// Same for a 128-bit numerator (huge triangles, A >= 2^38).  The estimate
+// comes from the top bits of n; the remainder is kept in 128 bits.
+__device__ __forceinline__ long long floor_div_est128(__int128 n, long long A, float rA) {
+  const float nf = (float)(long long)(n >> 32) * 4294967296.0f + (float)(unsigned)(n & 0xFFFFFFFFu);
+  long long q = (long long)floorf(nf * rA);
+  __int128 r = n - (__int128)q * A;
+  while (r < 0) { --q; r += A; }
+  while (r >= A) { ++q; r -= A; }
+  return q;
+}
+
+// Depth of a covered sample from its edge functions w1, w2 (w0 = A - w1 - w2):
+// z = floor((w0 Z0 + w1 Z1 + w2 Z2) / A) = Z0 + floor((w1 (Z1-Z0) + w2 (Z2-Z0)) / A).
+__device__ __forceinline__ unsigned depth_of(long long w1, long long w2, const TriSetup& s, float rA) {
+  const long long d1 = (long long)s.Z1 - s.Z0, d2 = (long long)s.Z2 - s.Z0;
+  long long q;
+  if (s.A < (1LL << 38)) {
+    q = floor_div_est(w1 * d1 + w2 * d2, s.A, rA);
+  } else {
+    q = floor_div_est128((__int128)w1 * d1 + (__int128)w2 * d2, s.A, rA);
+  }
+  return (unsigned)(s.Z0 + q);
+}
+
+// --------------------------------------------------------------- kernels
+struct ProcessParams {
+  RasterGeom g;
+  int ntiles;
+  int schedule;
+  int small_px;
+  int mode;
+  int unclamped;
+  int stats;
+  const int* tris;
+  const int4* vtx;
+  const float* color;
+  const float* normal;
+  const float* light;
+  const unsigned* bin_off;
+  const unsigned* bin_tris;
+  unsigned long long* key_out;
+  float4* rgba_out;
+  uint2* gnorm_out;  // binary16 x4
+  uint2* galb_out;   // binary16 x4
+  DevStatus* st;
+};
+
+void launch_vertex(int W, int H, int V, const float* pos, const float* mvp, int4* vtx, int num_sms,
+                   cudaStream_t s);
+void launch_setup_count(const RasterGeom& g, int T, const int* tris, int V, const int4* vtx,
+                        BinRect* rect, unsigned* bin_count, DevStatus* st, int stats, int num_sms,
+                        cudaStream_t s);
+void launch_scan(int nbins, unsigned* bin_count, unsigned* bin_off, unsigned* cursor,
+                 unsigned long long capacity, DevStatus* st, cudaStream_t s);
+void launch_scatter(const RasterGeom& g, int T, const BinRect* rect, unsigned* cursor, unsigned* bin_tris,
+                    DevStatus* st, int num_sms, cudaStream_t s);
+cudaError_t launch_process(const ProcessParams& p, int threads, int grid, cudaStream_t s);
+cudaError_t process_occupancy(int threads, int bin_px, int* blocks_per_sm);
+size_t process_smem_bytes(int threads, int bin_px);
+
+void launch_deferred_light(int W, int H, const unsigned long long* key, const uint2* gnorm,
+                           const uint2* galb, const float4* lights, int n_lights, float4* rgba,
+                           int num_sms, cudaStream_t s);
+
+}  // namespace piko

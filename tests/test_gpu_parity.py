@@ -1,0 +1,327 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Depth/ID keys must match bit for bit; shaded colour within 1e-5 absolute
+(the GPU shades in float32, the oracle in float64); binary16 G-buffer
+values within one binary16 step (both sides round a value that differs only
+by float32-vs-float64 interpolation); gradients within 1e-4 relative on
+components above 1e-3 of the largest, 1e-4 of the largest below that.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1404_6293_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+EMPTY = np.uint64(0xFFFFFFFFFFFFFFFF)
+RGB_TOL = 1e-5
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def rasterize(scene, bin_w=16, bin_h=16, schedule="static", options=None, mvp=None):
+    torch = _torch()
+    from paper_1404_6293_gb300.raster import DeviceScene, Rasterizer
+    r = Rasterizer(scene.width, scene.height, bin_w, bin_h, schedule)
+    for k, v in (options or {}).items():
+        r.set_option(k, v)
+    ds = DeviceScene.from_host(scene, mvp=mvp)
+    fb = r.forward(ds)
+    torch.cuda.synchronize()
+    code, need = r.status()
+    out = {"key": fb.key_numpy(), "status": code, "needed": need, "r": r, "ds": ds, "fb": fb}
+    if fb.rgba is not None:
+        out["rgba"] = fb.rgba.cpu().numpy()
+    if fb.gbuf_normal is not None:
+        out["gn"] = fb.gbuf_normal.cpu().numpy()
+        out["ga"] = fb.gbuf_albedo.cpu().numpy()
+    return out
+
+
+def assert_keys_equal(gpu, ref, what=""):
+    if not np.array_equal(gpu, ref):
+        bad = np.argwhere(gpu != ref)
+        y, x = bad[0]
+        raise AssertionError(f"{what}: {len(bad)} key mismatches, first at (x={x}, y={y}): "
+                             f"gpu {int(gpu[y, x]):#x} oracle {int(ref[y, x]):#x}")
+
+
+def assert_half_close(gpu_h, ref_u16):
+    g = gpu_h.astype(np.float64)
+    r = ref_u16.view(np.float16).astype(np.float64)
+    step = np.spacing(np.maximum(np.abs(g), np.abs(r)).astype(np.float16)).astype(np.float64)
+    assert np.all(np.abs(g - r) <= step), np.max(np.abs(g - r) / np.maximum(step, 1e-30))
+
+
+# --------------------------------------------------------------- configs
+def test_random_triangles_256_parity():
+    s = S.random_triangles()
+    out = rasterize(s, 16, 16, "static")
+    assert out["status"] == 0
+    ref, st = oracle.raster_brute(s)
+    assert st == 0
+    assert_keys_equal(out["key"], ref, "random 256x256")
+    rgba = oracle.shade(s, ref)
+    assert np.abs(out["rgba"] - rgba).max() <= RGB_TOL
+
+
+SHAPES = [(1, 1), (7, 5), (37, 53), (200, 120), (257, 65), (64, 64)]
+
+
+@pytest.mark.parametrize("W,H", SHAPES)
+@pytest.mark.parametrize("bins", [(8, 8), (16, 16), (32, 32), (64, 64), (8, 32), (64, 16)])
+def test_all_bins_and_schedules_match_oracle(W, H, bins):
+    rng = np.random.default_rng(W * 1000 + H)
+    T = int(rng.integers(50, 400))
+    radius = float(rng.choice([3.0, 12.0, 60.0, 300.0]))
+    s = S.random_triangles(W, H, T, radius, seed=int(rng.integers(1 << 30)))
+    ref, _ = oracle.raster_bbox(s, threads=4)
+    rgba_ref = oracle.shade(s, ref)
+    for sched in ("static", "dynamic", "hardware"):
+        out = rasterize(s, bins[0], bins[1], sched)
+        assert out["status"] == 0
+        assert_keys_equal(out["key"], ref, f"{W}x{H} bins {bins} {sched}")
+        assert np.abs(out["rgba"] - rgba_ref).max() <= RGB_TOL
+
+
+@pytest.mark.parametrize("small_px", [0, 1, 32, 4096])
+@pytest.mark.parametrize("threads", [64, 128, 256, 512])
+def test_thread_and_warp_raster_paths_agree(small_px, threads):
+    from paper_1404_6293_gb300 import _lib as L
+    s = S.random_triangles(160, 96, 300, 25.0, seed=77)
+    ref, _ = oracle.raster_bbox(s)
+    out = rasterize(s, 32, 16, "dynamic", {L.PIKO_OPT_SMALL_TRI_PIXELS: small_px, L.PIKO_OPT_THREADS_PER_TILE: threads})
+    assert_keys_equal(out["key"], ref, f"small_px={small_px} threads={threads}")
+
+
+def test_lambert_heightfield_small():
+    s = S.heightfield(320, 180, 80, 40, seed=5)
+    ref, _ = oracle.raster_bbox(s, threads=4)
+    rgba = oracle.shade(s, ref)
+    for bins in ((8, 8), (16, 16), (64, 64)):
+        out = rasterize(s, *bins)
+        assert_keys_equal(out["key"], ref, f"heightfield bins {bins}")
+        assert np.abs(out["rgba"] - rgba).max() <= RGB_TOL
+
+
+def test_lambert_with_colours_and_unclamped():
+    from paper_1404_6293_gb300 import _lib as L
+    s = S.random_triangles(128, 128, 200, 20.0, seed=8, shade_mode=S.SHADE_LAMBERT, with_normals=True)
+    s.light_dir = np.array([0.2, -0.5, -0.84], np.float32)
+    ref, _ = oracle.raster_brute(s)
+    for unclamped in (0, 1):
+        out = rasterize(s, 16, 16, "dynamic", {L.PIKO_OPT_UNCLAMPED: unclamped})
+        assert_keys_equal(out["key"], ref)
+        rgba = oracle.shade(s, ref, unclamped=bool(unclamped))
+        assert np.abs(out["rgba"] - rgba).max() <= RGB_TOL
+
+
+def test_heightfield_1080p_full_frame():
+    s = S.heightfield()
+    ref, _ = oracle.raster_bbox(s, threads=8)
+    rgba = oracle.shade(s, ref)
+    for bins in ((8, 8), (16, 16), (32, 32), (64, 64)):
+        out = rasterize(s, *bins)
+        assert out["status"] == 0
+        assert_keys_equal(out["key"], ref, f"heightfield 1080p bins {bins}")
+        assert np.abs(out["rgba"] - rgba).max() <= RGB_TOL
+
+
+def test_gbuffer_power_law_small():
+    s = S.power_law_triangles(480, 270, 20_000, seed=9)
+    ref, _ = oracle.raster_bbox(s, threads=4)
+    gn, ga = oracle.shade(s, ref)
+    for sched in ("static", "dynamic"):
+        out = rasterize(s, 16, 16, sched)
+        assert_keys_equal(out["key"], ref, f"power law {sched}")
+        assert_half_close(out["gn"], gn)
+        assert_half_close(out["ga"], ga)
+
+
+def test_power_law_1080p_full_frame_keys():
+    s = S.power_law_triangles()
+    ref, _ = oracle.raster_bbox(s, threads=8)
+    out = rasterize(s, 16, 16, "dynamic")
+    assert_keys_equal(out["key"], ref, "power law 1080p")
+
+
+def test_deferred_light_pass_on_synthetic_gbuffer():
+    torch = _torch()
+    from paper_1404_6293_gb300.raster import Framebuffer, Rasterizer
+    W, H = 333, 187
+    key, gn, ga = S.gbuffer_inputs(W, H)
+    lights = S.point_lights(W, H, 64)
+    ref = oracle.light_pass(key, gn.view(np.uint16), ga.view(np.uint16), lights)
+    r = Rasterizer(W, H, 16, 16)
+    fb = Framebuffer(torch.from_numpy(key.view(np.int64)).cuda(), None, torch.from_numpy(gn).cuda(),
+                     torch.from_numpy(ga).cuda())
+    for n in (1, 7, 64):
+        lt = lights[:n]
+        ref = oracle.light_pass(key, gn.view(np.uint16), ga.view(np.uint16), lt)
+        out = r.deferred_light(fb, torch.from_numpy(lt).cuda()).cpu().numpy()
+        assert np.abs(out - ref).max() <= RGB_TOL
+
+
+def test_deferred_end_to_end_where_gbuffer_agrees():
+    torch = _torch()
+    s = S.power_law_triangles(480, 270, 20_000, seed=10)
+    lights = S.point_lights(480, 270, 64)
+    ref_key, _ = oracle.raster_bbox(s)
+    gn, ga = oracle.shade(s, ref_key)
+    ref = oracle.light_pass(ref_key, gn, ga, lights)
+    out = rasterize(s, 16, 16, "dynamic")
+    rgba = out["r"].deferred_light(out["fb"], torch.from_numpy(lights).cuda()).cpu().numpy()
+    same = np.all(out["gn"].view(np.uint16) == gn, axis=-1) & np.all(out["ga"].view(np.uint16) == ga, axis=-1)
+    assert same.mean() > 0.99
+    assert np.abs(rgba[same] - ref[same]).max() <= RGB_TOL
+    # where a binary16 value differs by one step the light sum moves by a bounded amount
+    assert np.abs(rgba - ref).max() <= 4e-3
+
+
+# --------------------------------------------------------------- edge cases
+def test_empty_scene_and_no_vertices():
+    for V, T in ((0, 0), (30, 0)):
+        s = S.Scene(40, 30, np.zeros((V, 4), np.float32), np.zeros((T, 3), np.int32),
+                    color=np.zeros((V, 3), np.float32))
+        out = rasterize(s, 8, 8)
+        assert out["status"] == 0
+        assert (out["key"] == EMPTY).all()
+        assert (out["rgba"] == 0).all()
+
+
+def test_culled_degenerate_and_huge_triangles():
+    W = H = 256
+    pos = []
+    # huge triangle (A > 2^38: 128-bit depth path), vertices near the guard band
+    pos += [[-200.0, -200.0, -0.5, 1], [200.0, -200.0, 0.7, 1], [0.0, 230.0, 0.1, 1]]
+    # vertex behind the camera (w < 0) and one with z outside [-1, 1]
+    pos += [[0, 0, 0, -1], [0.5, 0, 0, 1], [0, 0.5, 0, 1]]
+    pos += [[0, 0, 1.5, 1], [0.5, 0, 0, 1], [0, 0.5, 0, 1]]
+    # collinear (A = 0)
+    pos += [[-0.5, -0.5, 0, 1], [0.0, 0.0, 0, 1], [0.5, 0.5, 0, 1]]
+    # ordinary triangle in front of the huge one, and one behind it
+    pos += [[-0.3, -0.3, -0.9, 1], [0.4, -0.2, -0.9, 1], [0.0, 0.5, -0.9, 1]]
+    pos += [[-0.6, -0.1, 0.99, 1], [0.2, -0.7, 0.99, 1], [0.3, 0.6, 0.99, 1]]
+    pos = np.array(pos, np.float32)
+    n = pos.shape[0]
+    rng = np.random.default_rng(0)
+    s = S.Scene(W, H, pos, np.arange(n).reshape(-1, 3).astype(np.int32), color=rng.random((n, 3)).astype(np.float32))
+    ref, _ = oracle.raster_brute(s)
+    assert (ref != EMPTY).all()  # the huge triangle covers the screen
+    for bins in ((8, 8), (64, 64)):
+        for sched in ("static", "dynamic", "hardware"):
+            out = rasterize(s, *bins, sched)
+            assert_keys_equal(out["key"], ref, f"huge/culled {bins} {sched}")
+            assert np.abs(out["rgba"] - oracle.shade(s, ref)).max() <= RGB_TOL
+
+
+def test_bad_index_is_reported_and_culled():
+    from paper_1404_6293_gb300 import _lib as L
+    s = S.random_triangles(64, 64, 50, 10.0, seed=2)
+    s.tris = s.tris.copy()
+    s.tris[7] = [0, 1, 1 << 20]
+    s.tris[9] = [-5, 2, 3]
+    ref, st = oracle.raster_brute(s)
+    assert st == oracle.BAD_INDEX
+    out = rasterize(s, 16, 16)
+    assert out["status"] == L.PIKO_ERR_BAD_INDEX
+    assert_keys_equal(out["key"], ref, "bad index")
+
+
+def test_overflow_is_reported_then_grows():
+    torch = _torch()
+    from paper_1404_6293_gb300 import _lib as L
+    from paper_1404_6293_gb300.raster import DeviceScene, Rasterizer
+    s = S.random_triangles(256, 256, 2000, 40.0, seed=4)
+    ref, _ = oracle.raster_bbox(s)
+    r = Rasterizer(256, 256, 8, 8, "dynamic")
+    r.set_option(L.PIKO_OPT_CHECK_CAPACITY, 0)
+    r.reserve(s.num_vertices, s.num_triangles, 100)
+    ds = DeviceScene.from_host(s)
+    r.forward(ds)
+    code, need = r.status()
+    assert code == L.PIKO_ERR_OVERFLOW and need > 100
+    r.reserve(s.num_vertices, s.num_triangles, need)
+    fb = r.forward(ds)
+    torch.cuda.synchronize()
+    assert r.status()[0] == 0
+    assert_keys_equal(fb.key_numpy(), ref, "after reserve")
+    # with the capacity check on, a too-small reservation grows by itself
+    r2 = Rasterizer(256, 256, 8, 8, "static")
+    r2.reserve(s.num_vertices, s.num_triangles, 10)
+    fb2 = r2.forward(ds)
+    torch.cuda.synchronize()
+    assert r2.status()[0] == 0
+    assert_keys_equal(fb2.key_numpy(), ref, "auto grow")
+
+
+def test_invalid_arguments_rejected_on_host():
+    torch = _torch()
+    from paper_1404_6293_gb300 import _lib as L
+    from paper_1404_6293_gb300.raster import DeviceScene, PikoError, Rasterizer
+    lib = L.load()
+    assert not lib.piko_raster_create(0, 10, 16, 16, 0)
+    assert not lib.piko_raster_create(10, 10, 12, 16, 0)
+    assert not lib.piko_raster_create(40000, 10, 16, 16, 0)
+    assert not lib.piko_raster_create(10, 10, 16, 16, 7)
+    r = Rasterizer(64, 64)
+    s = S.random_triangles(32, 32, 5, 5.0)
+    with pytest.raises(PikoError):
+        r.forward(DeviceScene.from_host(s))  # size mismatch
+    with pytest.raises(PikoError):
+        r.set_option(L.PIKO_OPT_THREADS_PER_TILE, 100)
+    s = S.random_triangles(64, 64, 5, 5.0)
+    ds = DeviceScene.from_host(s)
+    ds.color = None
+    with pytest.raises(PikoError):
+        r.forward(ds)  # Gouraud without colours
+
+
+def test_bin_size_and_schedule_never_change_output():
+    s = S.random_triangles(300, 200, 3000, 15.0, seed=12)
+    keys = []
+    for bins in ((8, 8), (16, 16), (32, 32), (64, 64), (16, 64)):
+        for sched in ("static", "dynamic", "hardware"):
+            keys.append(rasterize(s, *bins, sched)["key"])
+    for k in keys[1:]:
+        assert np.array_equal(k, keys[0])
+
+
+# --------------------------------------------------------------- backward
+def _grad_check(g_gpu, g_ref):
+    g_gpu = np.asarray(g_gpu, np.float64)
+    scale = np.abs(g_ref).max()
+    big = np.abs(g_ref) > 1e-3 * scale
+    rel = np.abs(g_gpu - g_ref)[big] / np.abs(g_ref)[big]
+    assert rel.max() <= 1e-4, rel.max()
+    assert np.abs(g_gpu - g_ref)[~big].max(initial=0) <= 1e-4 * scale
+
+
+@pytest.mark.parametrize("mode", [S.SHADE_GOURAUD, S.SHADE_LAMBERT])
+def test_backward_matches_oracle_gradients(mode):
+    torch = _torch()
+    s = S.random_triangles(128, 96, 400, 14.0, seed=31, shade_mode=mode, with_normals=True)
+    s.light_dir = np.array([0.3, -0.4, -0.866], np.float32)
+    out = rasterize(s, 16, 16, "dynamic")
+    ref_key, _ = oracle.raster_brute(s)
+    assert_keys_equal(out["key"], ref_key)
+    tgt = S.target_image(128, 96, seed=2)[0]
+    rgba_ref = oracle.shade(s, ref_key)
+    g = np.zeros((96, 128, 4))
+    g[..., :3] = 2.0 * (rgba_ref[..., :3] - tgt[..., :3])
+    dc, dn, dl = oracle.backward(s, ref_key, g)
+    V = s.num_vertices
+    gd = torch.from_numpy(g.astype(np.float32)).cuda()
+    dcg = torch.zeros((V, 3), device="cuda")
+    dng = torch.zeros((V, 3), device="cuda")
+    dlg = torch.zeros(3, device="cuda")
+    out["r"].backward(out["ds"], out["fb"], gd, dcg, dng, dlg)
+    torch.cuda.synchronize()
+    _grad_check(dcg.cpu().numpy(), dc)
+    if mode == S.SHADE_LAMBERT:
+        _grad_check(dng.cpu().numpy(), dn)
+        _grad_check(dlg.cpu().numpy(), dl)

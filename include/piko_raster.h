@@ -192,6 +192,42 @@ int piko_raster_set_stage_events(piko_raster *h, void *const *events, int n);
  * survived culling and reached a bin. */
 int piko_raster_stats(piko_raster *h, int64_t out[5]);
 
+/* ---- forward pass without any device allocation ------------------------
+ * The paper has no counterpart; this entry point exists for callers that
+ * are not allowed to allocate GPU memory: work recorded inside a CUDA stream
+ * capture that must not add allocations, plugins whose host application
+ * owns the device allocator, and real-time loops that cannot afford the
+ * implicit synchronisation of cudaMalloc/cudaFree.
+ *
+ * It computes what piko_raster_forward computes with the same bin size and
+ * schedule and the default options, but needs no handle: its scratch memory
+ * is one fixed device array of about 5.8 MB inside this library, which every
+ * GPU that loads the library keeps until the process exits.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *  - The first call on each device looks up that array's device address
+ *    (once per device, with the device current); make that first call
+ *    before any stream capture.
+ *  - Every call on a device shares the array and it keeps the previous
+ *    call's contents (the call clears what must start at zero itself).
+ *    Calls whose work overlaps on the GPU -- on different streams or from
+ *    different host threads -- race and give wrong results; order them on
+ *    one stream.
+ *  - Scenes above the limits below, or more tiles than
+ *    PIKO_NOALLOC_MAX_BINS, are rejected with PIKO_ERR_INVALID_ARG and
+ *    nothing is enqueued.  Other host-side checks are those of
+ *    piko_raster_forward.
+ *  - status_out (a device int32, may be NULL) receives PIKO_OK or the first
+ *    device-side condition when the pass finishes: PIKO_ERR_OVERFLOW if the
+ *    bin lists need more than PIKO_NOALLOC_MAX_BIN_ENTRIES entries (the
+ *    framebuffer is then not written), PIKO_ERR_BAD_INDEX for an index
+ *    outside [0, V) (that triangle is culled). */
+#define PIKO_NOALLOC_MAX_VERTICES 65536
+#define PIKO_NOALLOC_MAX_TRIANGLES 65536
+#define PIKO_NOALLOC_MAX_BINS 16384
+#define PIKO_NOALLOC_MAX_BIN_ENTRIES 1048576
+int piko_raster_forward_noalloc(const piko_scene *scene, piko_framebuffer *fb, int bin_w, int bin_h,
+                                int schedule, int32_t *status_out, void *cuda_stream);
+
 /* Message for the last failing call on this handle (never NULL). */
 const char *piko_raster_last_error(const piko_raster *h);
 

@@ -51,6 +51,9 @@ def build_library(force: bool = False, verbose: bool = False, ptxas_info: bool =
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
+    # optional tuning knobs for experiments, e.g. PIKO_DEFINES="PIKO_PROCESS_MAXNREG=96"
+    for d in os.environ.get("PIKO_DEFINES", "").split():
+        extra.append("-D" + d)
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")

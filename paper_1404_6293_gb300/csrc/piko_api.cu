@@ -31,7 +31,7 @@ struct piko_raster {
   long long vcap = 0;
   BinRect* rect = nullptr;
   long long tcap = 0;
-  unsigned* bin_count = nullptr;  // zero between frames
+  unsigned* bin_count = nullptr;  // 2 * nbins, zero between frames
   unsigned* bin_off = nullptr;    // nbins + 1
   unsigned* cursor = nullptr;
   unsigned* bin_tris = nullptr;
@@ -100,19 +100,19 @@ piko_raster* piko_raster_create(int width, int height, int bin_w, int bin_h, int
   h->g.nbx = (width + bin_w - 1) / bin_w;
   h->g.nby = (height + bin_h - 1) / bin_h;
   h->nbins = h->g.nbx * h->g.nby;
-  h->threads = bin_w * bin_h >= 256 ? 256 : (bin_w * bin_h < 64 ? 64 : bin_w * bin_h);
+  h->threads = default_process_threads(bin_w * bin_h);
   if (cudaGetDevice(&h->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
     cudaGetLastError();
     delete h;
     return nullptr;
   }
-  bool ok = cudaMalloc(&h->bin_count, sizeof(unsigned) * h->nbins) == cudaSuccess &&
+  bool ok = cudaMalloc(&h->bin_count, sizeof(unsigned) * 2 * h->nbins) == cudaSuccess &&
             cudaMalloc(&h->bin_off, sizeof(unsigned) * (h->nbins + 1)) == cudaSuccess &&
             cudaMalloc(&h->cursor, sizeof(unsigned) * h->nbins) == cudaSuccess &&
             cudaMalloc(&h->status, sizeof(DevStatus)) == cudaSuccess &&
             cudaMallocHost(&h->h_needed, sizeof(unsigned long long)) == cudaSuccess &&
-            cudaMemset(h->bin_count, 0, sizeof(unsigned) * h->nbins) == cudaSuccess &&
+            cudaMemset(h->bin_count, 0, sizeof(unsigned) * 2 * h->nbins) == cudaSuccess &&
             cudaMemset(h->status, 0, sizeof(DevStatus)) == cudaSuccess &&
             cudaDeviceSynchronize() == cudaSuccess;
   if (!ok) {
@@ -270,7 +270,7 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
     e = cudaMemsetAsync(h->status, 0, sizeof(unsigned) * 2, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "status clear");
   }
-  launch_scatter(h->g, T, h->rect, h->cursor, h->bin_tris, h->status, h->num_sms, st);
+  launch_scatter(h->g, T, h->rect, h->bin_off, h->cursor, h->bin_tris, h->status, h->num_sms, st);
   if (ev) cudaEventRecord(h->stage_ev[4], st);
 
   ProcessParams p;
@@ -281,6 +281,7 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
   p.mode = s->shade_mode;
   p.unclamped = h->unclamped;
   p.stats = h->stats;
+  p.num_triangles = T;
   p.tris = s->tris;
   p.vtx = h->vtx;
   p.color = s->color;
@@ -296,7 +297,7 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
   int grid = h->nbins;
   if (h->schedule != PIKO_SCHED_HARDWARE) {
     int per_sm = 0;
-    cudaError_t e = process_occupancy(h->threads, h->bin_w * h->bin_h, &per_sm);
+    cudaError_t e = process_occupancy(p, h->threads, &per_sm);
     if (e != cudaSuccess) return cuda_fail(h, e, "occupancy query");
     if (per_sm < 1) per_sm = 1;
     grid = per_sm * h->num_sms < h->nbins ? per_sm * h->num_sms : h->nbins;

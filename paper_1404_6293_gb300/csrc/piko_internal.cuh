@@ -39,8 +39,7 @@ struct RasterGeom {
   int nbx, nby;            // bins per row / column
 };
 
-// Per-triangle bin rectangle from the count pass: x0 | y0 << 16, x1 | y1 << 16.
-// A culled triangle stores x0 = 0xFFFF (x0 > x1).
+// Per-triangle result of the count pass (encoding in piko_forward.cu).
 struct BinRect {
   unsigned int lo, hi;
 };
@@ -136,6 +135,10 @@ struct ProcessParams {
   int mode;
   int unclamped;
   int stats;
+  int num_triangles;
+  int slot_bits;   // set by launch_process: bits of the record slot below the triangle index
+  int nslots;      // shared-memory records per tile
+  int rec_stride;  // 32-bit words per record
   const int* tris;
   const int4* vtx;
   const float* color;
@@ -152,16 +155,20 @@ struct ProcessParams {
 
 void launch_vertex(int W, int H, int V, const float* pos, const float* mvp, int4* vtx, int num_sms,
                    cudaStream_t s);
+// bin_count holds 2 * nbins counters (single-bin and multi-bin entries), zero
+// between frames.
 void launch_setup_count(const RasterGeom& g, int T, const int* tris, int V, const int4* vtx,
                         BinRect* rect, unsigned* bin_count, DevStatus* st, int stats, int num_sms,
                         cudaStream_t s);
 void launch_scan(int nbins, unsigned* bin_count, unsigned* bin_off, unsigned* cursor,
                  unsigned long long capacity, DevStatus* st, cudaStream_t s);
-void launch_scatter(const RasterGeom& g, int T, const BinRect* rect, unsigned* cursor, unsigned* bin_tris,
-                    DevStatus* st, int num_sms, cudaStream_t s);
+void launch_scatter(const RasterGeom& g, int T, const BinRect* rect, const unsigned* bin_off, unsigned* cursor,
+                    unsigned* bin_tris, DevStatus* st, int num_sms, cudaStream_t s);
 cudaError_t launch_process(const ProcessParams& p, int threads, int grid, cudaStream_t s);
-cudaError_t process_occupancy(int threads, int bin_px, int* blocks_per_sm);
-size_t process_smem_bytes(int threads, int bin_px);
+cudaError_t process_occupancy(const ProcessParams& p, int threads, int* blocks_per_sm);
+
+// Default CTA size of the Process stage for a tile of bin_px pixels.
+inline int default_process_threads(int bin_px) { return bin_px <= 64 ? 64 : (bin_px <= 256 ? 128 : 256); }
 
 void launch_deferred_light(int W, int H, const unsigned long long* key, const uint2* gnorm,
                            const uint2* galb, const float4* lights, int n_lights, float4* rgba,

@@ -29,7 +29,7 @@ constexpr size_t OFF_STATUS = 0;
 constexpr size_t OFF_VTX = align256(OFF_STATUS + sizeof(DevStatus));
 constexpr size_t OFF_RECT = align256(OFF_VTX + sizeof(int4) * PIKO_NOALLOC_MAX_VERTICES);
 constexpr size_t OFF_COUNT = align256(OFF_RECT + sizeof(BinRect) * PIKO_NOALLOC_MAX_TRIANGLES);
-constexpr size_t OFF_OFFS = align256(OFF_COUNT + sizeof(unsigned) * PIKO_NOALLOC_MAX_BINS);
+constexpr size_t OFF_OFFS = align256(OFF_COUNT + sizeof(unsigned) * 2 * PIKO_NOALLOC_MAX_BINS);
 constexpr size_t OFF_CURSOR = align256(OFF_OFFS + sizeof(unsigned) * (PIKO_NOALLOC_MAX_BINS + 1));
 constexpr size_t OFF_ENTRIES = align256(OFF_CURSOR + sizeof(unsigned) * PIKO_NOALLOC_MAX_BINS);
 constexpr size_t SCRATCH_BYTES = align256(OFF_ENTRIES + sizeof(unsigned) * (size_t)PIKO_NOALLOC_MAX_BIN_ENTRIES);
@@ -122,14 +122,14 @@ extern "C" int piko_raster_forward_noalloc(const piko_scene* s, piko_framebuffer
   // The array keeps whatever the previous call left in it: the status word
   // and the per-tile counts must start at zero.
   if (cudaMemsetAsync(status, 0, sizeof(DevStatus), st) != cudaSuccess ||
-      cudaMemsetAsync(bin_count, 0, sizeof(unsigned) * nbins, st) != cudaSuccess) {
+      cudaMemsetAsync(bin_count, 0, sizeof(unsigned) * 2 * nbins, st) != cudaSuccess) {
     cudaGetLastError();
     return PIKO_ERR_CUDA;
   }
   launch_vertex(g.W, g.H, s->num_vertices, s->pos, s->mvp, vtx, num_sms, st);
   launch_setup_count(g, s->num_triangles, s->tris, s->num_vertices, vtx, rect, bin_count, status, 0, num_sms, st);
   launch_scan(nbins, bin_count, bin_off, cursor, (unsigned long long)PIKO_NOALLOC_MAX_BIN_ENTRIES, status, st);
-  launch_scatter(g, s->num_triangles, rect, cursor, bin_tris, status, num_sms, st);
+  launch_scatter(g, s->num_triangles, rect, bin_off, cursor, bin_tris, status, num_sms, st);
 
   ProcessParams p;
   p.g = g;
@@ -139,6 +139,7 @@ extern "C" int piko_raster_forward_noalloc(const piko_scene* s, piko_framebuffer
   p.mode = s->shade_mode;
   p.unclamped = 0;
   p.stats = 0;
+  p.num_triangles = s->num_triangles;
   p.tris = s->tris;
   p.vtx = vtx;
   p.color = s->color;
@@ -151,11 +152,11 @@ extern "C" int piko_raster_forward_noalloc(const piko_scene* s, piko_framebuffer
   p.gnorm_out = reinterpret_cast<uint2*>(fb->gbuf_normal);
   p.galb_out = reinterpret_cast<uint2*>(fb->gbuf_albedo);
   p.st = status;
-  const int threads = bin_w * bin_h >= 256 ? 256 : (bin_w * bin_h < 64 ? 64 : bin_w * bin_h);
+  const int threads = default_process_threads(bin_w * bin_h);
   int grid = nbins;
   if (schedule != PIKO_SCHED_HARDWARE) {
     int per_sm = 0;
-    if (process_occupancy(threads, bin_w * bin_h, &per_sm) != cudaSuccess) {
+    if (process_occupancy(p, threads, &per_sm) != cudaSuccess) {
       cudaGetLastError();
       return PIKO_ERR_CUDA;
     }

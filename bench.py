@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Mtris/s + shaded Gfrag/s on 1 GB300 (plain vs batched), bit-exact depth/ID"
 UNIT = "Mtris/s"
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "process_heightfield1080p_traffic.json")
-KERNEL_SOURCES = ["paper_1404_6293_gb300/csrc/piko_forward.cu", "paper_1404_6293_gb300/csrc/piko_internal.cuh"]
+KERNEL_SOURCES = ["paper_1404_6293_gb300/csrc/piko_process.cu", "paper_1404_6293_gb300/csrc/piko_internal.cuh"]
 
 # Per-unit algorithmic costs of the Process kernel (thread operations), fixed
 # from the minimal operation sequence of the definition: see the design doc.
@@ -208,6 +208,9 @@ def run_ours(args):
     scene, cfg = workload(args)
     T = scene.num_triangles
     r = Rasterizer(scene.width, scene.height, args.bins, args.bins, args.schedule)
+    if args.threads:
+        r.set_option(L.PIKO_OPT_THREADS_PER_TILE, args.threads)
+        cfg["threads_per_tile"] = args.threads
     ds = DeviceScene.from_host(scene)
     fb = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode)
     r.forward(ds, fb)  # sizes the bin lists (capacity check on)
@@ -353,6 +356,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--bins", type=int, default=16)
     ap.add_argument("--schedule", default="static", choices=["static", "dynamic", "hardware"])
+    ap.add_argument("--threads", type=int, default=0, help="Process CTA size (0: library default)")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -201,7 +201,7 @@ int piko_raster_stats(piko_raster *h, int64_t out[5]);
  *
  * It computes what piko_raster_forward computes with the same bin size and
  * schedule and the default options, but needs no handle: its scratch memory
- * is one fixed device array of about 5.8 MB inside this library, which every
+ * is one fixed device array of about 6.3 MB inside this library, which every
  * GPU that loads the library keeps until the process exits.  It calls no
  * cudaMalloc, cudaFree or other allocating routine.
  *  - The first call on each device looks up that array's device address

@@ -29,11 +29,15 @@ struct piko_raster {
   // scratch (device)
   int4* vtx = nullptr;
   long long vcap = 0;
+  float* vdot = nullptr;  // n . L per vertex for Lambert
+  long long dcap = 0;
   BinRect* rect = nullptr;
   long long tcap = 0;
   unsigned* bin_count = nullptr;  // 2 * nbins, zero between frames
   unsigned* bin_off = nullptr;    // nbins + 1
   unsigned* cursor = nullptr;
+  unsigned long long* chunk_state = nullptr;  // look-back state of the scan
+  unsigned scan_epoch = 0;
   unsigned* bin_tris = nullptr;
   long long ecap = 0;
   DevStatus* status = nullptr;
@@ -110,6 +114,8 @@ piko_raster* piko_raster_create(int width, int height, int bin_w, int bin_h, int
   bool ok = cudaMalloc(&h->bin_count, sizeof(unsigned) * 2 * h->nbins) == cudaSuccess &&
             cudaMalloc(&h->bin_off, sizeof(unsigned) * (h->nbins + 1)) == cudaSuccess &&
             cudaMalloc(&h->cursor, sizeof(unsigned) * h->nbins) == cudaSuccess &&
+            cudaMalloc(&h->chunk_state, sizeof(unsigned long long) * scan_chunks(h->nbins)) == cudaSuccess &&
+            cudaMemset(h->chunk_state, 0, sizeof(unsigned long long) * scan_chunks(h->nbins)) == cudaSuccess &&
             cudaMalloc(&h->status, sizeof(DevStatus)) == cudaSuccess &&
             cudaMallocHost(&h->h_needed, sizeof(unsigned long long)) == cudaSuccess &&
             cudaMemset(h->bin_count, 0, sizeof(unsigned) * 2 * h->nbins) == cudaSuccess &&
@@ -127,10 +133,12 @@ void piko_raster_destroy(piko_raster* h) {
   if (!h) return;
   cudaDeviceSynchronize();
   cudaFree(h->vtx);
+  cudaFree(h->vdot);
   cudaFree(h->rect);
   cudaFree(h->bin_count);
   cudaFree(h->bin_off);
   cudaFree(h->cursor);
+  cudaFree(h->chunk_state);
   cudaFree(h->bin_tris);
   cudaFree(h->status);
   if (h->h_needed) cudaFreeHost(h->h_needed);
@@ -184,6 +192,7 @@ int piko_raster_reserve(piko_raster* h, int64_t max_vertices, int64_t max_triang
     return fail(h, PIKO_ERR_INVALID_ARG, "reserve sizes out of range");
   int r;
   if ((r = grow(h, &h->vtx, &h->vcap, max_vertices, "vertex buffer")) != PIKO_OK) return r;
+  if ((r = grow(h, &h->vdot, &h->dcap, max_vertices, "vertex light terms")) != PIKO_OK) return r;
   if ((r = grow(h, &h->rect, &h->tcap, max_triangles, "bin rectangles")) != PIKO_OK) return r;
   if ((r = grow(h, &h->bin_tris, &h->ecap, max_bin_entries, "bin lists")) != PIKO_OK) return r;
   cudaError_t e = cudaDeviceSynchronize();
@@ -241,6 +250,8 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
   h->last_stream = st;
   const int V = s->num_vertices, T = s->num_triangles;
   if ((r = grow(h, &h->vtx, &h->vcap, V, "vertex buffer")) != PIKO_OK) return r;
+  const bool lambert = s->shade_mode == PIKO_SHADE_LAMBERT;
+  if (lambert && (r = grow(h, &h->vdot, &h->dcap, V, "vertex light terms")) != PIKO_OK) return r;
   if ((r = grow(h, &h->rect, &h->tcap, T, "bin rectangles")) != PIKO_OK) return r;
   if (h->ecap == 0 && (r = grow(h, &h->bin_tris, &h->ecap, (long long)T * 2 + 4096, "bin lists")) != PIKO_OK)
     return r;
@@ -249,13 +260,15 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
   h->use_stage_ev = false;
   if (ev) cudaEventRecord(h->stage_ev[0], st);
   if (h->stats) cudaMemsetAsync(&h->status->tests, 0, 4 * sizeof(unsigned long long), st);
-  launch_vertex(h->W, h->H, V, s->pos, s->mvp, h->vtx, h->num_sms, st);
+  launch_vertex(h->W, h->H, V, s->pos, s->mvp, h->vtx, lambert ? s->normal : nullptr, s->light_dir,
+                lambert ? h->vdot : nullptr, h->num_sms, st);
   if (ev) cudaEventRecord(h->stage_ev[1], st);
   for (int attempt = 0;; ++attempt) {
     if (h->stats && attempt > 0) cudaMemsetAsync(&h->status->binned, 0, sizeof(unsigned long long), st);
     launch_setup_count(h->g, T, s->tris, V, h->vtx, h->rect, h->bin_count, h->status, h->stats, h->num_sms, st);
     if (ev) cudaEventRecord(h->stage_ev[2], st);
-    launch_scan(h->nbins, h->bin_count, h->bin_off, h->cursor, (unsigned long long)h->ecap, h->status, st);
+    launch_scan(h->nbins, h->bin_count, h->bin_off, h->cursor, (unsigned long long)h->ecap, h->status,
+                h->chunk_state, ++h->scan_epoch, st);
     if (ev) cudaEventRecord(h->stage_ev[3], st);
     if (!h->check_capacity) break;
     cudaError_t e = cudaMemcpyAsync(h->h_needed, &h->status->needed, sizeof(unsigned long long),
@@ -270,7 +283,8 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
     e = cudaMemsetAsync(h->status, 0, sizeof(unsigned) * 2, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "status clear");
   }
-  launch_scatter(h->g, T, h->rect, h->bin_off, h->cursor, h->bin_tris, h->status, h->num_sms, st);
+  launch_scatter(h->g, T, h->rect, h->bin_off, h->cursor, h->bin_tris, (unsigned long long)h->ecap, h->status,
+                 h->num_sms, st);
   if (ev) cudaEventRecord(h->stage_ev[4], st);
 
   ProcessParams p;
@@ -287,6 +301,7 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
   p.color = s->color;
   p.normal = s->normal;
   p.light = s->light_dir;
+  p.vdot = h->vdot;
   p.bin_off = h->bin_off;
   p.bin_tris = h->bin_tris;
   p.key_out = reinterpret_cast<unsigned long long*>(fb->key);
@@ -351,7 +366,7 @@ int piko_raster_backward(piko_raster* h, const piko_scene* s, const piko_framebu
   if ((r = grow(h, &h->vtx, &h->vcap, s->num_vertices, "vertex buffer")) != PIKO_OK) return r;
   // the vertex stage runs again so that backward does not depend on which
   // scene the handle rasterized last
-  launch_vertex(h->W, h->H, s->num_vertices, s->pos, s->mvp, h->vtx, h->num_sms, st);
+  launch_vertex(h->W, h->H, s->num_vertices, s->pos, s->mvp, h->vtx, nullptr, nullptr, nullptr, h->num_sms, st);
   if (piko_backward_launch(h->W, h->H, s->shade_mode, h->unclamped, s->num_triangles, s->num_vertices, s->tris,
                            h->vtx, s->color, s->normal,
                            s->light_dir, reinterpret_cast<const unsigned long long*>(fwd->key), dl_drgba, dl_dcolor,

@@ -25,7 +25,9 @@ __device__ __forceinline__ float mvp_row(const float* m, float4 p) {
 }
 
 __global__ void __launch_bounds__(256) k_vertex(int W, int H, int V, const float4* __restrict__ pos,
-                                                const float* __restrict__ mvp, int4* __restrict__ vtx) {
+                                                const float* __restrict__ mvp, int4* __restrict__ vtx,
+                                                const float* __restrict__ normal, const float* __restrict__ light,
+                                                float* __restrict__ vdot) {
   __shared__ float m[16];
   const bool has_m = mvp != nullptr;
   if (has_m) {
@@ -33,7 +35,13 @@ __global__ void __launch_bounds__(256) k_vertex(int W, int H, int V, const float
     __syncthreads();
   }
   const float fW = (float)W, fH = (float)H;
+  float L0 = 0.f, L1 = 0.f, L2 = 0.f;
+  if (vdot) {
+    L0 = __ldg(light); L1 = __ldg(light + 1); L2 = __ldg(light + 2);
+  }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V; i += gridDim.x * blockDim.x) {
+    if (vdot) vdot[i] = __ldg(normal + 3 * (size_t)i) * L0 + __ldg(normal + 3 * (size_t)i + 1) * L1 +
+                        __ldg(normal + 3 * (size_t)i + 2) * L2;
     const float4 p = __ldg(pos + i);  // one 16-byte load per vertex, coalesced across the warp
     float c0 = p.x, c1 = p.y, c2 = p.z, c3 = p.w;
     if (has_m) {
@@ -62,12 +70,13 @@ __global__ void __launch_bounds__(256) k_vertex(int W, int H, int V, const float
   }
 }
 
-void launch_vertex(int W, int H, int V, const float* pos, const float* mvp, int4* vtx, int num_sms,
-                   cudaStream_t s) {
+void launch_vertex(int W, int H, int V, const float* pos, const float* mvp, int4* vtx, const float* normal,
+                   const float* light, float* vdot, int num_sms, cudaStream_t s) {
   if (V <= 0) return;
-  int blocks = (V + 255) / 256;
-  blocks = blocks < num_sms * 8 ? blocks : num_sms * 8;
-  k_vertex<<<blocks, 256, 0, s>>>(W, H, V, reinterpret_cast<const float4*>(pos), mvp, vtx);
+  // one vertex per thread: every load is in flight at once
+  (void)num_sms;
+  const int blocks = (V + 255) / 256;
+  k_vertex<<<blocks, 256, 0, s>>>(W, H, V, reinterpret_cast<const float4*>(pos), mvp, vtx, normal, light, vdot);
 }
 
 // ======================================================================
@@ -100,14 +109,11 @@ __device__ __forceinline__ bool bin_setup(const RasterGeom& g, int V, const int4
     record_error(st, PIKO_ERR_BAD_INDEX);
     return false;
   }
-  const int4 p0 = __ldg(vtx + idx.x), p1 = __ldg(vtx + idx.y), p2 = __ldg(vtx + idx.z);
-  if (!(p0.w & p1.w & p2.w)) return false;
-  const long long A = (long long)(p1.x - p0.x) * (long long)(p2.y - p0.y) -
-                      (long long)(p2.x - p0.x) * (long long)(p1.y - p0.y);
-  if (A == 0) return false;
+  TriSetup s;
+  if (!setup_triangle(idx.x, idx.y, idx.z, vtx, s)) return false;
   int px0, px1, py0, py1;
-  centre_range(min(p0.x, min(p1.x, p2.x)), max(p0.x, max(p1.x, p2.x)), 0, g.W - 1, px0, px1);
-  centre_range(min(p0.y, min(p1.y, p2.y)), max(p0.y, max(p1.y, p2.y)), 0, g.H - 1, py0, py1);
+  centre_range(min(s.X0, min(s.X1, s.X2)), max(s.X0, max(s.X1, s.X2)), 0, g.W - 1, px0, px1);
+  centre_range(min(s.Y0, min(s.Y1, s.Y2)), max(s.Y0, max(s.Y1, s.Y2)), 0, g.H - 1, py0, py1);
   if (px0 > px1 || py0 > py1) return false;  // no pixel centre inside the bounding box
   bx0 = px0 >> g.bshift_x; bx1 = px1 >> g.bshift_x;
   by0 = py0 >> g.bshift_y; by1 = py1 >> g.bshift_y;
@@ -163,169 +169,286 @@ constexpr unsigned RECT_CULLED = 0xFFFFFFFFu;
 constexpr unsigned RECT_SINGLE = 0x8000u;
 
 // ======================================================================
+// Scan: a single-pass decoupled look-back scan over chunks of
+// SCAN_CHUNK bins, one chunk per CTA (CTAs take chunk numbers from a ticket,
+// so every predecessor of a chunk has already started).  Each chunk
+// publishes its aggregate, then its inclusive prefix, in a 64-bit state word
+// tagged with the frame's epoch (no clearing between frames):
+//   bits 63..62 kind (1 aggregate, 2 inclusive prefix), 61..46 epoch,
+//   45..0 value.
+// off[b] = entries of all earlier bins; the scatter cursor of a bin starts
+// after its single-bin part; both count arrays are zeroed for the next frame.
+// Look-back waits are bounded by a clock budget; on expiry the scan records
+// PIKO_ERR_TIMEOUT and the frame's later stages skip their work.
+// ======================================================================
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_PER = 8;
+constexpr int SCAN_CHUNK = SCAN_THREADS * SCAN_PER;
+constexpr unsigned long long SCAN_KIND_AGG = 1ull << 62, SCAN_KIND_PREFIX = 2ull << 62;
+constexpr unsigned long long SCAN_VALUE_MASK = (1ull << 46) - 1ull;
+constexpr long long SCAN_WAIT_CYCLES = 40000000;  // ~20 ms at 2 GHz
+
+__device__ __forceinline__ void load8(const unsigned* __restrict__ a, int b0, int nbins, bool vec, unsigned* v) {
+  if (vec && b0 + 8 <= nbins) {
+    const uint4 x = __ldcg(reinterpret_cast<const uint4*>(a + b0)), y = __ldcg(reinterpret_cast<const uint4*>(a + b0 + 4));
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w; v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = b0 + j < nbins ? __ldcg(a + b0 + j) : 0u;
+  }
+}
+
+__device__ __forceinline__ unsigned long long state_load(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void state_store(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan(int nbins, unsigned* __restrict__ cnt,
+                                                       unsigned* __restrict__ bin_off, unsigned* __restrict__ cursor,
+                                                       unsigned long long capacity, DevStatus* st,
+                                                       unsigned long long* __restrict__ chunk_state, unsigned epoch) {
+  __shared__ unsigned long long warp_sums[SCAN_THREADS / 32];
+  __shared__ unsigned long long s_excl;
+  __shared__ int s_chunk;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const unsigned long long tag = (unsigned long long)(epoch & 0xFFFFu) << 46;
+  if (tid == 0) s_chunk = (int)atomicAdd(&st->scan_ticket, 1u);
+  __syncthreads();
+  const int chunk = s_chunk;
+  const int nchunks = (nbins + SCAN_CHUNK - 1) / SCAN_CHUNK;
+  if (chunk >= nchunks) return;  // only with a corrupted ticket; the count pass resets it every frame
+  unsigned* __restrict__ multi = cnt + nbins;
+  const bool vec = (nbins & 3) == 0;  // second array 16-byte aligned
+  const int b0 = chunk * SCAN_CHUNK + tid * SCAN_PER;
+  unsigned sg[SCAN_PER], mu[SCAN_PER];
+  load8(cnt, b0, nbins, vec, sg);
+  load8(multi, b0, nbins, vec, mu);
+  unsigned long long local = 0;
+#pragma unroll
+  for (int j = 0; j < SCAN_PER; ++j) local += (unsigned long long)sg[j] + mu[j];
+  unsigned long long v = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long u = __shfl_up_sync(FULL_MASK, v, o);
+    if (lane >= o) v += u;
+  }
+  if (lane == 31) warp_sums[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    unsigned long long x = lane < SCAN_THREADS / 32 ? warp_sums[lane] : 0ull;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long u = __shfl_up_sync(FULL_MASK, x, o);
+      if (lane >= o) x += u;
+    }
+    if (lane < SCAN_THREADS / 32) warp_sums[lane] = x;
+  }
+  __syncthreads();
+  const unsigned long long agg = warp_sums[SCAN_THREADS / 32 - 1];
+  if (tid == 0) {
+    unsigned long long excl = 0;
+    if (chunk == 0) {
+      state_store(chunk_state, SCAN_KIND_PREFIX | tag | (agg & SCAN_VALUE_MASK));
+    } else {
+      state_store(chunk_state + chunk, SCAN_KIND_AGG | tag | (agg & SCAN_VALUE_MASK));
+      const long long t0 = clock64();
+      bool timed_out = false;
+      for (int j = chunk - 1; j >= 0 && !timed_out;) {
+        const unsigned long long sv = state_load(chunk_state + j);
+        const unsigned long long sv_epoch = sv & ~SCAN_VALUE_MASK & ~(3ull << 62);
+        if (sv_epoch != tag || (sv >> 62) == 0) {
+          if (clock64() - t0 > SCAN_WAIT_CYCLES) timed_out = true;
+          else __nanosleep(64);
+          continue;  // predecessor not published for this frame yet
+        }
+        excl += sv & SCAN_VALUE_MASK;
+        if ((sv >> 62) == 2) break;  // inclusive prefix: done
+        --j;
+      }
+      if (timed_out) record_error(st, PIKO_ERR_TIMEOUT);
+      state_store(chunk_state + chunk, SCAN_KIND_PREFIX | tag | ((excl + agg) & SCAN_VALUE_MASK));
+    }
+    s_excl = excl;
+  }
+  __syncthreads();
+  unsigned long long run = s_excl + v - local + (w > 0 ? warp_sums[w - 1] : 0ull);
+  unsigned of[SCAN_PER], cu[SCAN_PER];
+#pragma unroll
+  for (int j = 0; j < SCAN_PER; ++j) {
+    of[j] = (unsigned)run;
+    cu[j] = (unsigned)(run + sg[j]);
+    run += (unsigned long long)sg[j] + mu[j];
+  }
+  if (vec && b0 + SCAN_PER <= nbins) {
+    reinterpret_cast<uint4*>(bin_off + b0)[0] = make_uint4(of[0], of[1], of[2], of[3]);
+    reinterpret_cast<uint4*>(bin_off + b0)[1] = make_uint4(of[4], of[5], of[6], of[7]);
+    reinterpret_cast<uint4*>(cursor + b0)[0] = make_uint4(cu[0], cu[1], cu[2], cu[3]);
+    reinterpret_cast<uint4*>(cursor + b0)[1] = make_uint4(cu[4], cu[5], cu[6], cu[7]);
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    reinterpret_cast<uint4*>(cnt + b0)[0] = z;
+    reinterpret_cast<uint4*>(cnt + b0)[1] = z;
+    reinterpret_cast<uint4*>(multi + b0)[0] = z;
+    reinterpret_cast<uint4*>(multi + b0)[1] = z;
+  } else {
+#pragma unroll
+    for (int j = 0; j < SCAN_PER; ++j)
+      if (b0 + j < nbins) {
+        bin_off[b0 + j] = of[j];
+        cursor[b0 + j] = cu[j];
+        cnt[b0 + j] = 0u;
+        multi[b0 + j] = 0u;
+      }
+  }
+  if (chunk == nchunks - 1 && tid == 0) {
+    const unsigned long long total = s_excl + agg;
+    const bool ok = total <= capacity;
+    if (ok) bin_off[nbins] = (unsigned)total;
+    st->needed = total;
+    st->queue_head = 0u;
+    st->scan_ticket = 0u;  // every chunk took its ticket before this chunk's look-back ended
+    if (!ok) record_error(st, PIKO_ERR_OVERFLOW);
+  }
+}
+
+int scan_chunks(int nbins) { return (nbins + SCAN_CHUNK - 1) / SCAN_CHUNK; }
+
+// ======================================================================
 // AssignBin, pass 1: setup + counts.  Counts live in two arrays: entries of
 // triangles covering one bin (cnt[b]) and of triangles covering several
 // (cnt[nbins + b]).  A single-bin triangle gets its slot here from one atomic
 // per group of lanes sharing the bin (__match_any_sync), so the scatter
 // needs no atomic for it; multi-bin pairs are spread over the warp.
 // ======================================================================
+// Vertex data of one triangle, gathered before any of it is used so that two
+// batches of triangles have their loads in flight together.
+struct TriVerts {
+  int4 p0, p1, p2;
+  bool in_range;
+};
+
+__device__ __forceinline__ TriVerts gather_verts(int3 idx, int V, const int4* __restrict__ vtx, bool live) {
+  TriVerts v;
+  v.in_range = live && (unsigned)idx.x < (unsigned)V && (unsigned)idx.y < (unsigned)V && (unsigned)idx.z < (unsigned)V;
+  if (v.in_range) {
+    v.p0 = __ldg(vtx + idx.x); v.p1 = __ldg(vtx + idx.y); v.p2 = __ldg(vtx + idx.z);
+  } else {
+    v.p0 = v.p1 = v.p2 = make_int4(0, 0, 0, 0);
+  }
+  return v;
+}
+
+// Count-pass work for one batch of 32 triangles (one per lane).
+__device__ __forceinline__ void count_batch(const RasterGeom& g, int T, int t, int3 idx, const TriVerts& v,
+                                            BinRect* __restrict__ rect, unsigned* __restrict__ cnt, int nbins,
+                                            DevStatus* st, int stats, int lane, unsigned lt_mask) {
+  bool valid = false;
+  int bx0 = 0, by0 = 0, bx1 = -1, by1 = -1;
+  if (t < T) {
+    if (!v.in_range) {
+      record_error(st, PIKO_ERR_BAD_INDEX);
+    } else if (v.p0.w & v.p1.w & v.p2.w) {
+      const long long A = (long long)(v.p1.x - v.p0.x) * (v.p2.y - v.p0.y) -
+                          (long long)(v.p2.x - v.p0.x) * (v.p1.y - v.p0.y);
+      if (A != 0) {
+        int px0, px1, py0, py1;
+        centre_range(min(v.p0.x, min(v.p1.x, v.p2.x)), max(v.p0.x, max(v.p1.x, v.p2.x)), 0, g.W - 1, px0, px1);
+        centre_range(min(v.p0.y, min(v.p1.y, v.p2.y)), max(v.p0.y, max(v.p1.y, v.p2.y)), 0, g.H - 1, py0, py1);
+        if (px0 <= px1 && py0 <= py1) {  // some pixel centre inside the bounding box
+          valid = true;
+          bx0 = px0 >> g.bshift_x; bx1 = px1 >> g.bshift_x;
+          by0 = py0 >> g.bshift_y; by1 = py1 >> g.bshift_y;
+        }
+      }
+    }
+  }
+  (void)idx;
+  if (stats) {
+    const unsigned nv = __popc(__ballot_sync(FULL_MASK, valid));
+    if (lane == 0 && nv) atomicAdd(&st->binned, (unsigned long long)nv);
+  }
+  const bool single = valid && bx0 == bx1 && by0 == by1;
+  const unsigned bin = single ? (unsigned)(by0 * g.nbx + bx0) : 0xFFFFFFFFu;
+  const unsigned grp = __match_any_sync(FULL_MASK, bin);
+  const int leader = __ffs(grp) - 1;
+  unsigned slot = 0;
+  if (single && lane == leader) slot = atomicAdd(cnt + bin, (unsigned)__popc(grp));
+  slot = __shfl_sync(FULL_MASK, slot, leader) + __popc(grp & lt_mask);
+  if (t < T) {
+    BinRect r;
+    if (!valid) {
+      r.lo = RECT_CULLED; r.hi = 0u;
+    } else if (single) {
+      r.lo = (unsigned)bx0 | ((unsigned)by0 << 16) | RECT_SINGLE; r.hi = slot;
+    } else {
+      r.lo = (unsigned)bx0 | ((unsigned)by0 << 16); r.hi = (unsigned)bx1 | ((unsigned)by1 << 16);
+    }
+    rect[t] = r;
+  }
+  const int bw = bx1 - bx0 + 1;
+  const int nb = (valid && !single) ? bw * (by1 - by0 + 1) : 0;
+  const MultiSpan m = warp_prefix(nb, lane);
+  for (int k0 = 0; k0 < m.total; k0 += 32) {
+    const int k = k0 + lane;
+    const int owner = pair_owner(m.incl, k < m.total ? k : m.total - 1);
+    const int ox = __shfl_sync(FULL_MASK, bx0, owner), oy = __shfl_sync(FULL_MASK, by0, owner);
+    const int obw = __shfl_sync(FULL_MASK, bw, owner);
+    const int first = __shfl_sync(FULL_MASK, m.incl - nb, owner);
+    if (k < m.total) atomicAdd(cnt + nbins + pair_bin(g, k, first, ox, oy, obw), 1u);
+  }
+}
+
 __global__ void __launch_bounds__(256) k_setup_count(RasterGeom g, int T, const int* __restrict__ tris, int V,
                                                      const int4* __restrict__ vtx, BinRect* __restrict__ rect,
                                                      unsigned* __restrict__ cnt, int nbins, DevStatus* st,
                                                      int stats) {
-  __shared__ __align__(16) int sbuf[8][96];
+  __shared__ __align__(16) int sbuf[8][2][96];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->scan_ticket = 0u;  // the scan runs after this kernel
   const unsigned lt_mask = (1u << lane) - 1u;
-  const int warps_total = gridDim.x * (blockDim.x >> 5);
-  for (int base = (blockIdx.x * (blockDim.x >> 5) + wib) * 32; base < T; base += warps_total * 32) {
-    const int t = base + lane;
-    const int3 idx = load_tri_warp(tris, T, base, lane, sbuf[wib]);
-    int bx0 = 0, by0 = 0, bx1 = -1, by1 = -1;
-    const bool valid = t < T && bin_setup(g, V, vtx, idx, st, bx0, by0, bx1, by1);
-    if (stats) {
-      const unsigned nv = __popc(__ballot_sync(FULL_MASK, valid));
-      if (lane == 0 && nv) atomicAdd(&st->binned, (unsigned long long)nv);
-    }
-    const bool single = valid && bx0 == bx1 && by0 == by1;
-    const unsigned bin = single ? (unsigned)(by0 * g.nbx + bx0) : 0xFFFFFFFFu;
-    const unsigned grp = __match_any_sync(FULL_MASK, bin);
-    const int leader = __ffs(grp) - 1;
-    unsigned slot = 0;
-    if (single && lane == leader) slot = atomicAdd(cnt + bin, (unsigned)__popc(grp));
-    slot = __shfl_sync(FULL_MASK, slot, leader) + __popc(grp & lt_mask);
-    if (t < T) {
-      BinRect r;
-      if (!valid) {
-        r.lo = RECT_CULLED; r.hi = 0u;
-      } else if (single) {
-        r.lo = (unsigned)bx0 | ((unsigned)by0 << 16) | RECT_SINGLE; r.hi = slot;
-      } else {
-        r.lo = (unsigned)bx0 | ((unsigned)by0 << 16); r.hi = (unsigned)bx1 | ((unsigned)by1 << 16);
-      }
-      rect[t] = r;
-    }
-    const int bw = bx1 - bx0 + 1;
-    const int nb = (valid && !single) ? bw * (by1 - by0 + 1) : 0;
-    const MultiSpan m = warp_prefix(nb, lane);
-    for (int k0 = 0; k0 < m.total; k0 += 32) {
-      const int k = k0 + lane;
-      const int owner = pair_owner(m.incl, k < m.total ? k : m.total - 1);
-      const int ox = __shfl_sync(FULL_MASK, bx0, owner), oy = __shfl_sync(FULL_MASK, by0, owner);
-      const int obw = __shfl_sync(FULL_MASK, bw, owner);
-      const int first = __shfl_sync(FULL_MASK, m.incl - nb, owner);
-      if (k < m.total) atomicAdd(cnt + nbins + pair_bin(g, k, first, ox, oy, obw), 1u);
-    }
+  const int step = gridDim.x * (blockDim.x >> 5) * 32;
+  // two batches of 32 triangles per iteration: both batches' loads are issued
+  // before either is processed
+  for (int base = (blockIdx.x * (blockDim.x >> 5) + wib) * 32; base < T; base += 2 * step) {
+    const int baseB = base + step;
+    const bool hasB = baseB < T;  // warp-uniform
+    const int3 ia = load_tri_warp(tris, T, base, lane, sbuf[wib][0]);
+    const int3 ib = hasB ? load_tri_warp(tris, T, baseB, lane, sbuf[wib][1]) : make_int3(0, 0, 0);
+    const TriVerts va = gather_verts(ia, V, vtx, base + lane < T);
+    const TriVerts vb = gather_verts(ib, V, vtx, hasB && baseB + lane < T);
+    count_batch(g, T, base + lane, ia, va, rect, cnt, nbins, st, stats, lane, lt_mask);
+    if (hasB) count_batch(g, T, baseB + lane, ib, vb, rect, cnt, nbins, st, stats, lane, lt_mask);
   }
+}
+
+// Resident CTAs per SM of a kernel (one wave of a persistent grid).
+template <typename K>
+static int resident_per_sm(K kernel, int threads) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, 0) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    n = 1;
+  }
+  return n;
 }
 
 void launch_setup_count(const RasterGeom& g, int T, const int* tris, int V, const int4* vtx, BinRect* rect,
                         unsigned* bin_count, DevStatus* st, int stats, int num_sms, cudaStream_t s) {
-  if (T <= 0) return;
+  static const int per_sm = resident_per_sm(k_setup_count, 256);
   int warps = (T + 31) / 32;
   int blocks = (warps + 7) / 8;
-  blocks = blocks < num_sms * 8 ? blocks : num_sms * 8;
+  blocks = blocks < num_sms * per_sm ? blocks : num_sms * per_sm;
+  if (blocks < 1) blocks = 1;  // with no triangles the kernel still resets the scan ticket
   k_setup_count<<<blocks, 256, 0, s>>>(g, T, tris, V, vtx, rect, bin_count, g.nbx * g.nby, st, stats);
 }
 
-// ======================================================================
-// Scan: one CTA of 1024 threads walks the bins in rounds of 8192, each
-// thread owning 8 consecutive bins (two 16-byte loads per count array).
-// off[b] = entries of all earlier bins; the scatter cursor of a bin starts
-// after its single-bin part; both count arrays are zeroed for the next frame.
-// ======================================================================
-constexpr int SCAN_THREADS = 1024;
-constexpr int SCAN_PER = 8;
-
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan(int nbins, unsigned* __restrict__ cnt,
-                                                       unsigned* __restrict__ bin_off,
-                                                       unsigned* __restrict__ cursor, unsigned long long capacity,
-                                                       DevStatus* st) {
-  __shared__ unsigned long long warp_sums[32];
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  unsigned* __restrict__ multi = cnt + nbins;
-  const bool vec = (nbins & 3) == 0;  // 16-byte aligned second array
-  unsigned long long carry = 0;
-  for (int round = 0; round < nbins; round += SCAN_THREADS * SCAN_PER) {
-    const int b0 = round + tid * SCAN_PER;
-    unsigned sg[SCAN_PER], mu[SCAN_PER];
-    if (vec && b0 + SCAN_PER <= nbins) {
-      const uint4 a = *reinterpret_cast<const uint4*>(cnt + b0), b = *reinterpret_cast<const uint4*>(cnt + b0 + 4);
-      const uint4 c = *reinterpret_cast<const uint4*>(multi + b0), d = *reinterpret_cast<const uint4*>(multi + b0 + 4);
-      sg[0] = a.x; sg[1] = a.y; sg[2] = a.z; sg[3] = a.w; sg[4] = b.x; sg[5] = b.y; sg[6] = b.z; sg[7] = b.w;
-      mu[0] = c.x; mu[1] = c.y; mu[2] = c.z; mu[3] = c.w; mu[4] = d.x; mu[5] = d.y; mu[6] = d.z; mu[7] = d.w;
-    } else {
-#pragma unroll
-      for (int j = 0; j < SCAN_PER; ++j) {
-        const bool in = b0 + j < nbins;
-        sg[j] = in ? cnt[b0 + j] : 0u;
-        mu[j] = in ? multi[b0 + j] : 0u;
-      }
-    }
-    unsigned long long local = 0;
-#pragma unroll
-    for (int j = 0; j < SCAN_PER; ++j) local += (unsigned long long)sg[j] + mu[j];
-    unsigned long long v = local;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long u = __shfl_up_sync(FULL_MASK, v, o);
-      if (lane >= o) v += u;
-    }
-    if (lane == 31) warp_sums[w] = v;
-    __syncthreads();
-    if (w == 0) {
-      unsigned long long x = warp_sums[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long u = __shfl_up_sync(FULL_MASK, x, o);
-        if (lane >= o) x += u;
-      }
-      warp_sums[lane] = x;
-    }
-    __syncthreads();
-    unsigned long long run = carry + v - local + (w > 0 ? warp_sums[w - 1] : 0ull);
-    const unsigned long long round_total = warp_sums[31];
-    unsigned of[SCAN_PER], cu[SCAN_PER];
-#pragma unroll
-    for (int j = 0; j < SCAN_PER; ++j) {
-      of[j] = (unsigned)run;
-      cu[j] = (unsigned)(run + sg[j]);
-      run += (unsigned long long)sg[j] + mu[j];
-    }
-    if (vec && b0 + SCAN_PER <= nbins) {
-      reinterpret_cast<uint4*>(bin_off + b0)[0] = make_uint4(of[0], of[1], of[2], of[3]);
-      reinterpret_cast<uint4*>(bin_off + b0)[1] = make_uint4(of[4], of[5], of[6], of[7]);
-      reinterpret_cast<uint4*>(cursor + b0)[0] = make_uint4(cu[0], cu[1], cu[2], cu[3]);
-      reinterpret_cast<uint4*>(cursor + b0)[1] = make_uint4(cu[4], cu[5], cu[6], cu[7]);
-      const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-      reinterpret_cast<uint4*>(cnt + b0)[0] = z;
-      reinterpret_cast<uint4*>(cnt + b0)[1] = z;
-      reinterpret_cast<uint4*>(multi + b0)[0] = z;
-      reinterpret_cast<uint4*>(multi + b0)[1] = z;
-    } else {
-#pragma unroll
-      for (int j = 0; j < SCAN_PER; ++j)
-        if (b0 + j < nbins) {
-          bin_off[b0 + j] = of[j];
-          cursor[b0 + j] = cu[j];
-          cnt[b0 + j] = 0u;
-          multi[b0 + j] = 0u;
-        }
-    }
-    carry += round_total;
-    __syncthreads();  // warp_sums is rewritten by the next round
-  }
-  if (tid == 0) {
-    const bool ok = carry <= capacity;
-    if (ok) bin_off[nbins] = (unsigned)carry;
-    st->needed = carry;
-    st->queue_head = 0u;
-    if (!ok) record_error(st, PIKO_ERR_OVERFLOW);
-  }
-}
-
-void launch_scan(int nbins, unsigned* bin_count, unsigned* bin_off, unsigned* cursor,
-                 unsigned long long capacity, DevStatus* st, cudaStream_t s) {
-  k_scan<<<1, SCAN_THREADS, 0, s>>>(nbins, bin_count, bin_off, cursor, capacity, st);
+void launch_scan(int nbins, unsigned* bin_count, unsigned* bin_off, unsigned* cursor, unsigned long long capacity,
+                 DevStatus* st, unsigned long long* chunk_state, unsigned epoch, cudaStream_t s) {
+  k_scan<<<scan_chunks(nbins), SCAN_THREADS, 0, s>>>(nbins, bin_count, bin_off, cursor, capacity, st, chunk_state,
+                                                     epoch);
 }
 
 // ======================================================================
@@ -333,49 +456,68 @@ void launch_scan(int nbins, unsigned* bin_count, unsigned* bin_off, unsigned* cu
 // at off[bin] + their slot from pass 1; multi-bin pairs take an atomic slot
 // after the bin's single-bin part, spread over the warp.
 // ======================================================================
-__global__ void __launch_bounds__(256) k_scatter(RasterGeom g, int T, const BinRect* __restrict__ rect,
-                                                 const unsigned* __restrict__ bin_off,
-                                                 unsigned* __restrict__ cursor, unsigned* __restrict__ bin_tris,
-                                                 const DevStatus* st) {
-  if (st->flags & (1u << PIKO_ERR_OVERFLOW)) return;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int warps_total = gridDim.x * (blockDim.x >> 5);
-  for (int base = (blockIdx.x * (blockDim.x >> 5) + wib) * 32; base < T; base += warps_total * 32) {
-    const int t = base + lane;
-    BinRect r;
-    r.lo = RECT_CULLED; r.hi = 0u;
-    if (t < T) r = rect[t];
-    const bool culled = r.lo == RECT_CULLED;
-    const bool single = !culled && (r.lo & RECT_SINGLE);
-    if (single) {
-      const int bin = (int)(r.lo >> 16) * g.nbx + (int)(r.lo & 0x7FFFu);
-      bin_tris[__ldg(bin_off + bin) + r.hi] = (unsigned)t;
-    }
-    const int bx0 = r.lo & 0xFFFF, by0 = r.lo >> 16, bx1 = r.hi & 0xFFFF, by1 = r.hi >> 16;
-    const int bw = bx1 - bx0 + 1;
-    const int nb = (!culled && !single) ? bw * (by1 - by0 + 1) : 0;
-    const MultiSpan m = warp_prefix(nb, lane);
-    for (int k0 = 0; k0 < m.total; k0 += 32) {
-      const int k = k0 + lane;
-      const int owner = pair_owner(m.incl, k < m.total ? k : m.total - 1);
-      const int ox = __shfl_sync(FULL_MASK, bx0, owner), oy = __shfl_sync(FULL_MASK, by0, owner);
-      const int obw = __shfl_sync(FULL_MASK, bw, owner);
-      const int first = __shfl_sync(FULL_MASK, m.incl - nb, owner);
-      if (k < m.total) {
-        const unsigned pos = atomicAdd(cursor + pair_bin(g, k, first, ox, oy, obw), 1u);
-        bin_tris[pos] = (unsigned)(base + owner);
-      }
+// Scatter work for one batch of 32 triangles whose rectangles are loaded.
+__device__ __forceinline__ void scatter_batch(const RasterGeom& g, int base, BinRect r, unsigned pos_single,
+                                              unsigned* __restrict__ cursor, unsigned* __restrict__ bin_tris,
+                                              unsigned long long capacity, int lane) {
+  const bool culled = r.lo == RECT_CULLED;
+  const bool single = !culled && (r.lo & RECT_SINGLE);
+  // positions are below the scanned total, which is at most the capacity;
+  // the bound only guards against inconsistent offsets
+  if (single && pos_single < capacity) bin_tris[pos_single] = (unsigned)(base + lane);
+  const int bx0 = r.lo & 0xFFFF, by0 = r.lo >> 16, bx1 = r.hi & 0xFFFF, by1 = r.hi >> 16;
+  const int bw = bx1 - bx0 + 1;
+  const int nb = (!culled && !single) ? bw * (by1 - by0 + 1) : 0;
+  const MultiSpan m = warp_prefix(nb, lane);
+  for (int k0 = 0; k0 < m.total; k0 += 32) {
+    const int k = k0 + lane;
+    const int owner = pair_owner(m.incl, k < m.total ? k : m.total - 1);
+    const int ox = __shfl_sync(FULL_MASK, bx0, owner), oy = __shfl_sync(FULL_MASK, by0, owner);
+    const int obw = __shfl_sync(FULL_MASK, bw, owner);
+    const int first = __shfl_sync(FULL_MASK, m.incl - nb, owner);
+    if (k < m.total) {
+      const unsigned pos = atomicAdd(cursor + pair_bin(g, k, first, ox, oy, obw), 1u);
+      if (pos < capacity) bin_tris[pos] = (unsigned)(base + owner);
     }
   }
 }
 
+// Offset of a single-bin triangle's entry: off[bin] + its slot (0 otherwise).
+__device__ __forceinline__ unsigned single_pos(const RasterGeom& g, BinRect r, const unsigned* __restrict__ bin_off) {
+  if (r.lo == RECT_CULLED || !(r.lo & RECT_SINGLE)) return 0u;
+  const int bin = (int)(r.lo >> 16) * g.nbx + (int)(r.lo & 0x7FFFu);
+  return __ldg(bin_off + bin) + r.hi;
+}
+
+__global__ void __launch_bounds__(256) k_scatter(RasterGeom g, int T, const BinRect* __restrict__ rect,
+                                                 const unsigned* __restrict__ bin_off,
+                                                 unsigned* __restrict__ cursor, unsigned* __restrict__ bin_tris,
+                                                 unsigned long long capacity, const DevStatus* st) {
+  if (st->flags & STATUS_SKIP_MASK) return;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int step = gridDim.x * (blockDim.x >> 5) * 32;
+  BinRect none;
+  none.lo = RECT_CULLED; none.hi = 0u;
+  // two batches per iteration, loads first
+  for (int base = (blockIdx.x * (blockDim.x >> 5) + wib) * 32; base < T; base += 2 * step) {
+    const int baseB = base + step;
+    const bool hasB = baseB < T;
+    const BinRect ra = base + lane < T ? rect[base + lane] : none;
+    const BinRect rb = hasB && baseB + lane < T ? rect[baseB + lane] : none;
+    const unsigned pa = single_pos(g, ra, bin_off), pb = single_pos(g, rb, bin_off);
+    scatter_batch(g, base, ra, pa, cursor, bin_tris, capacity, lane);
+    if (hasB) scatter_batch(g, baseB, rb, pb, cursor, bin_tris, capacity, lane);
+  }
+}
+
 void launch_scatter(const RasterGeom& g, int T, const BinRect* rect, const unsigned* bin_off, unsigned* cursor,
-                    unsigned* bin_tris, DevStatus* st, int num_sms, cudaStream_t s) {
+                    unsigned* bin_tris, unsigned long long capacity, DevStatus* st, int num_sms, cudaStream_t s) {
   if (T <= 0) return;
+  static const int per_sm = resident_per_sm(k_scatter, 256);
   int warps = (T + 31) / 32;
   int blocks = (warps + 7) / 8;
-  blocks = blocks < num_sms * 8 ? blocks : num_sms * 8;
-  k_scatter<<<blocks, 256, 0, s>>>(g, T, rect, bin_off, cursor, bin_tris, st);
+  blocks = blocks < num_sms * per_sm ? blocks : num_sms * per_sm;
+  k_scatter<<<blocks, 256, 0, s>>>(g, T, rect, bin_off, cursor, bin_tris, capacity, st);
 }
 
 }  // namespace piko

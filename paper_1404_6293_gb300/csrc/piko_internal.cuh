@@ -25,7 +25,8 @@ struct DevStatus {
   unsigned int first_code;      // first PIKO_ERR_* recorded (0 = none)
   unsigned long long needed;    // bin entries the last scan required
   unsigned int queue_head;      // tile counter of the dynamic schedule
-  unsigned int pad[3];
+  unsigned int scan_ticket;     // next chunk number of the scan (reset by its last chunk)
+  unsigned int pad[2];
   unsigned long long tests;     // statistics (PIKO_OPT_STATS): pixel samples tested
   unsigned long long frags;     // covered samples
   unsigned long long shaded;    // covered pixels after the depth test
@@ -43,6 +44,9 @@ struct RasterGeom {
 struct BinRect {
   unsigned int lo, hi;
 };
+
+// Conditions after which the bin lists of a frame are not usable.
+constexpr unsigned STATUS_SKIP_MASK = (1u << PIKO_ERR_OVERFLOW) | (1u << PIKO_ERR_TIMEOUT);
 
 __device__ __forceinline__ void record_error(DevStatus* st, unsigned code) {
   atomicCAS(&st->first_code, 0u, code);
@@ -113,6 +117,20 @@ __device__ __forceinline__ long long floor_div_est128(__int128 n, long long A, f
   return q;
 }
 
+// floor(n / A) for 0 < A < 2^31 and |n / A| < 2^25: the same estimate and
+// exact fix-up with 32-bit quotient and divisor.
+__device__ __forceinline__ int floor_div_small(long long n, int A, float rA) {
+  int q = (int)floorf((float)n * rA);
+  long long r = n - (long long)q * A;
+  while (r < 0) { --q; r += A; }
+  while (r >= A) { ++q; r -= A; }
+  return q;
+}
+
+// Approximate 1/a (a >= 1): only ever used as an estimate that integer
+// arithmetic corrects, or for float barycentrics.
+__device__ __forceinline__ float approx_rcp(float a) { return __fdividef(1.0f, a); }
+
 // Depth of a covered sample from its edge functions w1, w2 (w0 = A - w1 - w2):
 // z = floor((w0 Z0 + w1 Z1 + w2 Z2) / A) = Z0 + floor((w1 (Z1-Z0) + w2 (Z2-Z0)) / A).
 __device__ __forceinline__ unsigned depth_of(long long w1, long long w2, const TriSetup& s, float rA) {
@@ -144,6 +162,7 @@ struct ProcessParams {
   const float* color;
   const float* normal;
   const float* light;
+  const float* vdot;  // n_v . L per vertex (Lambert)
   const unsigned* bin_off;
   const unsigned* bin_tris;
   unsigned long long* key_out;
@@ -153,17 +172,24 @@ struct ProcessParams {
   DevStatus* st;
 };
 
-void launch_vertex(int W, int H, int V, const float* pos, const float* mvp, int4* vtx, int num_sms,
-                   cudaStream_t s);
-// bin_count holds 2 * nbins counters (single-bin and multi-bin entries), zero
-// between frames.
+// Vertex stage.  If vdot is not NULL it also stores n_v . L per vertex (the
+// Lambert term is linear in the interpolated normal, so per-vertex dots
+// interpolate to the same value).
+void launch_vertex(int W, int H, int V, const float* pos, const float* mvp, int4* vtx, const float* normal,
+                   const float* light, float* vdot, int num_sms, cudaStream_t s);
+// Count pass and scan (two launches): bin_count holds 2 * nbins counters
+// (single-bin and multi-bin entries), zero between frames; the scan turns
+// them into CSR offsets and scatter cursors (capacity: entries the bin lists
+// can hold; above it PIKO_ERR_OVERFLOW is recorded).
 void launch_setup_count(const RasterGeom& g, int T, const int* tris, int V, const int4* vtx,
-                        BinRect* rect, unsigned* bin_count, DevStatus* st, int stats, int num_sms,
-                        cudaStream_t s);
-void launch_scan(int nbins, unsigned* bin_count, unsigned* bin_off, unsigned* cursor,
-                 unsigned long long capacity, DevStatus* st, cudaStream_t s);
+                        BinRect* rect, unsigned* bin_count, DevStatus* st, int stats, int num_sms, cudaStream_t s);
+// chunk_state: scan_chunks(nbins) words, zero at allocation; epoch must
+// differ between consecutive scans on the same state array.
+void launch_scan(int nbins, unsigned* bin_count, unsigned* bin_off, unsigned* cursor, unsigned long long capacity,
+                 DevStatus* st, unsigned long long* chunk_state, unsigned epoch, cudaStream_t s);
+int scan_chunks(int nbins);
 void launch_scatter(const RasterGeom& g, int T, const BinRect* rect, const unsigned* bin_off, unsigned* cursor,
-                    unsigned* bin_tris, DevStatus* st, int num_sms, cudaStream_t s);
+                    unsigned* bin_tris, unsigned long long capacity, DevStatus* st, int num_sms, cudaStream_t s);
 cudaError_t launch_process(const ProcessParams& p, int threads, int grid, cudaStream_t s);
 cudaError_t process_occupancy(const ProcessParams& p, int threads, int* blocks_per_sm);
 

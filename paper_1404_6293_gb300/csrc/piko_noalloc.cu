@@ -12,8 +12,9 @@
 //
 // Limits: at most PIKO_NOALLOC_MAX_VERTICES vertices, PIKO_NOALLOC_MAX_TRIANGLES
 // triangles, PIKO_NOALLOC_MAX_BINS tiles and PIKO_NOALLOC_MAX_BIN_ENTRIES
-// (triangle, tile) pairs; about 5.8 MB of device memory that every GPU which
+// (triangle, tile) pairs; about 6.3 MB of device memory that every GPU which
 // loads this library keeps until the process exits.
+#include <atomic>
 #include <mutex>
 
 #include "piko_internal.cuh"
@@ -27,11 +28,14 @@ constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 // layout of the scratch array
 constexpr size_t OFF_STATUS = 0;
 constexpr size_t OFF_VTX = align256(OFF_STATUS + sizeof(DevStatus));
-constexpr size_t OFF_RECT = align256(OFF_VTX + sizeof(int4) * PIKO_NOALLOC_MAX_VERTICES);
+constexpr size_t OFF_VDOT = align256(OFF_VTX + sizeof(int4) * PIKO_NOALLOC_MAX_VERTICES);
+constexpr size_t OFF_RECT = align256(OFF_VDOT + sizeof(float) * PIKO_NOALLOC_MAX_VERTICES);
 constexpr size_t OFF_COUNT = align256(OFF_RECT + sizeof(BinRect) * PIKO_NOALLOC_MAX_TRIANGLES);
 constexpr size_t OFF_OFFS = align256(OFF_COUNT + sizeof(unsigned) * 2 * PIKO_NOALLOC_MAX_BINS);
 constexpr size_t OFF_CURSOR = align256(OFF_OFFS + sizeof(unsigned) * (PIKO_NOALLOC_MAX_BINS + 1));
-constexpr size_t OFF_ENTRIES = align256(OFF_CURSOR + sizeof(unsigned) * PIKO_NOALLOC_MAX_BINS);
+constexpr size_t OFF_CHUNKS = align256(OFF_CURSOR + sizeof(unsigned) * PIKO_NOALLOC_MAX_BINS);
+constexpr size_t OFF_ENTRIES = align256(OFF_CHUNKS + sizeof(unsigned long long) * 64);
+static_assert(PIKO_NOALLOC_MAX_BINS / 2048 + 1 <= 64, "scan chunk states (2048 bins each) must fit");
 constexpr size_t SCRATCH_BYTES = align256(OFF_ENTRIES + sizeof(unsigned) * (size_t)PIKO_NOALLOC_MAX_BIN_ENTRIES);
 
 // The one scratch buffer shared by every call on a device.  In host code this
@@ -40,6 +44,7 @@ constexpr size_t SCRATCH_BYTES = align256(OFF_ENTRIES + sizeof(unsigned) * (size
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 
 constexpr int MAX_DEVICES = 64;
+std::atomic<unsigned> g_scan_epoch{0};  // distinct per call: the scan's chunk states are never cleared
 std::mutex g_setup_lock;
 unsigned char* g_scratch_addr[MAX_DEVICES] = {};
 
@@ -106,11 +111,13 @@ extern "C" int piko_raster_forward_noalloc(const piko_scene* s, piko_framebuffer
   }
   DevStatus* status = reinterpret_cast<DevStatus*>(base + OFF_STATUS);
   int4* vtx = reinterpret_cast<int4*>(base + OFF_VTX);
+  float* vdot = reinterpret_cast<float*>(base + OFF_VDOT);
   BinRect* rect = reinterpret_cast<BinRect*>(base + OFF_RECT);
   unsigned* bin_count = reinterpret_cast<unsigned*>(base + OFF_COUNT);
   unsigned* bin_off = reinterpret_cast<unsigned*>(base + OFF_OFFS);
   unsigned* cursor = reinterpret_cast<unsigned*>(base + OFF_CURSOR);
   unsigned* bin_tris = reinterpret_cast<unsigned*>(base + OFF_ENTRIES);
+  unsigned long long* chunk_state = reinterpret_cast<unsigned long long*>(base + OFF_CHUNKS);
 
   RasterGeom g;
   g.W = s->width; g.H = s->height;
@@ -126,10 +133,14 @@ extern "C" int piko_raster_forward_noalloc(const piko_scene* s, piko_framebuffer
     cudaGetLastError();
     return PIKO_ERR_CUDA;
   }
-  launch_vertex(g.W, g.H, s->num_vertices, s->pos, s->mvp, vtx, num_sms, st);
+  const bool lambert = s->shade_mode == PIKO_SHADE_LAMBERT;
+  launch_vertex(g.W, g.H, s->num_vertices, s->pos, s->mvp, vtx, lambert ? s->normal : nullptr, s->light_dir,
+                lambert ? vdot : nullptr, num_sms, st);
   launch_setup_count(g, s->num_triangles, s->tris, s->num_vertices, vtx, rect, bin_count, status, 0, num_sms, st);
-  launch_scan(nbins, bin_count, bin_off, cursor, (unsigned long long)PIKO_NOALLOC_MAX_BIN_ENTRIES, status, st);
-  launch_scatter(g, s->num_triangles, rect, bin_off, cursor, bin_tris, status, num_sms, st);
+  launch_scan(nbins, bin_count, bin_off, cursor, (unsigned long long)PIKO_NOALLOC_MAX_BIN_ENTRIES, status, chunk_state,
+              ++g_scan_epoch, st);
+  launch_scatter(g, s->num_triangles, rect, bin_off, cursor, bin_tris, (unsigned long long)PIKO_NOALLOC_MAX_BIN_ENTRIES,
+                 status, num_sms, st);
 
   ProcessParams p;
   p.g = g;
@@ -145,6 +156,7 @@ extern "C" int piko_raster_forward_noalloc(const piko_scene* s, piko_framebuffer
   p.color = s->color;
   p.normal = s->normal;
   p.light = s->light_dir;
+  p.vdot = vdot;
   p.bin_off = bin_off;
   p.bin_tris = bin_tris;
   p.key_out = reinterpret_cast<unsigned long long*>(fb->key);

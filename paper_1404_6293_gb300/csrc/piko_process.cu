@@ -54,37 +54,57 @@ __device__ __forceinline__ Edges<I> make_edges(const TriSetup& s, int px, int py
   const int b0 = 1 - top_left(dx0, dy0);
   e.b1 = 1 - top_left(dx1, dy1);
   e.b2 = 1 - top_left(dx2, dy2);
-  e.e0 = (I)dx0 * (Py - s.Y1) - (I)dy0 * (Px - s.X1) - b0;
-  e.e1 = (I)dx1 * (Py - s.Y2) - (I)dy1 * (Px - s.X2) - e.b1;
-  e.e2 = (I)dx2 * (Py - s.Y0) - (I)dy2 * (Px - s.X0) - e.b2;
+  // coordinate differences are below 2^24 and fit int32
+  e.e0 = (I)dx0 * (I)((int)Py - s.Y1) - (I)dy0 * (I)((int)Px - s.X1) - b0;
+  e.e1 = (I)dx1 * (I)((int)Py - s.Y2) - (I)dy1 * (I)((int)Px - s.X2) - e.b1;
+  e.e2 = (I)dx2 * (I)((int)Py - s.Y0) - (I)dy2 * (I)((int)Px - s.X0) - e.b2;
   e.sx0 = (I)-256 * dy0; e.sx1 = (I)-256 * dy1; e.sx2 = (I)-256 * dy2;
   e.sy0 = (I)256 * dx0;  e.sy1 = (I)256 * dx1;  e.sy2 = (I)256 * dx2;
   return e;
 }
 
-template <bool SMALL>
-__device__ __forceinline__ void key_min(unsigned long long* skey, int idx, long long w1, long long w2,
-                                        const TriSetup& s, float rA, unsigned long long tag) {
-  unsigned z;
-  if (SMALL) {  // A < 2^30: the numerator fits in 64 bits (see depth_of)
-    z = (unsigned)(s.Z0 + floor_div_est(w1 * (long long)(s.Z1 - s.Z0) + w2 * (long long)(s.Z2 - s.Z0), s.A, rA));
-  } else {
-    z = depth_of(w1, w2, s, rA);
-  }
+__device__ __forceinline__ void key_store(unsigned long long* skey, int idx, unsigned z, unsigned long long tag) {
   const unsigned long long k = ((unsigned long long)z << 40) | tag;
   if (k < skey[idx]) atomicMin(skey + idx, k);
+}
+
+// Triangles whose bounding box is below 2^15 in 16.8 units: A < 2^30 and
+// w1, w2 < 2^31, so the depth numerator is two 32x32->64 products.  With
+// N32 the caller has checked A * (|Z1-Z0| + |Z2-Z0| + 8) < 2^31: the
+// numerator, the quotient estimate times A and the remainder then all fit
+// in 32 bits.
+template <bool N32>
+__device__ __forceinline__ void key_min_small(unsigned long long* skey, int idx, int w1, int w2, const TriSetup& s,
+                                              float rA, unsigned long long tag) {
+  if (N32) {
+    const int A = (int)s.A;
+    const int n = w1 * (s.Z1 - s.Z0) + w2 * (s.Z2 - s.Z0);
+    int q = __float2int_rd((float)n * rA);
+    int r = n - q * A;
+    while (r < 0) { --q; r += A; }
+    while (r >= A) { ++q; r -= A; }
+    key_store(skey, idx, (unsigned)(s.Z0 + q), tag);
+  } else {
+    const long long n = (long long)w1 * (s.Z1 - s.Z0) + (long long)w2 * (s.Z2 - s.Z0);
+    key_store(skey, idx, (unsigned)(s.Z0 + floor_div_small(n, (int)s.A, rA)), tag);
+  }
+}
+
+__device__ __forceinline__ void key_min_large(unsigned long long* skey, int idx, long long w1, long long w2,
+                                              const TriSetup& s, float rA, unsigned long long tag) {
+  key_store(skey, idx, depth_of(w1, w2, s, rA), tag);
 }
 
 // One thread walks the box of a small triangle inside the tile.  With I =
 // int the triangle's bounding box is below 2^15 in 16.8 units in both
 // directions, so every edge value inside the box is below 2^31 in magnitude
 // and int32 arithmetic is exact.
-template <typename I>
+template <typename I, bool N32>
 __device__ __forceinline__ unsigned raster_thread_body(const TriSetup& s, unsigned long long tag, int px0, int px1,
                                                        int py0, int py1, int x0, int y0, int bshift_x,
                                                        unsigned long long* skey) {
   const Edges<I> e = make_edges<I>(s, px0, py0);
-  const float rA = __frcp_rn((float)s.A);
+  const float rA = approx_rcp((float)s.A);
   unsigned frags = 0;
   I r0 = e.e0, r1 = e.e1, r2 = e.e2;
   for (int y = py0; y <= py1; ++y) {
@@ -92,7 +112,10 @@ __device__ __forceinline__ unsigned raster_thread_body(const TriSetup& s, unsign
     const int row = (y - y0) << bshift_x;
     for (int x = px0; x <= px1; ++x) {
       if ((a0 | a1 | a2) >= 0) {
-        key_min<sizeof(I) == 4>(skey, row + (x - x0), (long long)a1 + e.b1, (long long)a2 + e.b2, s, rA, tag);
+        if (sizeof(I) == 4)
+          key_min_small<N32>(skey, row + (x - x0), (int)a1 + e.b1, (int)a2 + e.b2, s, rA, tag);
+        else
+          key_min_large(skey, row + (x - x0), (long long)a1 + e.b1, (long long)a2 + e.b2, s, rA, tag);
         ++frags;
       }
       a0 += e.sx0; a1 += e.sx1; a2 += e.sx2;
@@ -108,12 +131,14 @@ __device__ __forceinline__ unsigned raster_thread_body(const TriSetup& s, unsign
 __device__ __forceinline__ unsigned raster_thread32(const TriSetup& s, unsigned long long tag, int px0, int px1,
                                                     int py0, int py1, int x0, int y0, int bshift_x,
                                                     unsigned long long* skey) {
-  return raster_thread_body<int>(s, tag, px0, px1, py0, py1, x0, y0, bshift_x, skey);
+  const long long dz = (long long)abs(s.Z1 - s.Z0) + abs(s.Z2 - s.Z0) + 8;
+  if (s.A * dz < (1LL << 31)) return raster_thread_body<int, true>(s, tag, px0, px1, py0, py1, x0, y0, bshift_x, skey);
+  return raster_thread_body<int, false>(s, tag, px0, px1, py0, py1, x0, y0, bshift_x, skey);
 }
 __device__ __forceinline__ unsigned raster_thread64(const TriSetup& s, unsigned long long tag, int px0, int px1,
                                                  int py0, int py1, int x0, int y0, int bshift_x,
                                                  unsigned long long* skey) {
-  return raster_thread_body<long long>(s, tag, px0, px1, py0, py1, x0, y0, bshift_x, skey);
+  return raster_thread_body<long long, false>(s, tag, px0, px1, py0, py1, x0, y0, bshift_x, skey);
 }
 
 // A warp covers a large triangle's box 32 pixels at a time; the ballot of
@@ -122,7 +147,7 @@ __device__ __forceinline__ unsigned raster_warp(const TriSetup& s, unsigned long
                                                 int py1, int x0, int y0, int bshift_x, unsigned long long* skey,
                                                 int lane) {
   const Edges<long long> e = make_edges<long long>(s, px0, py0);
-  const float rA = __frcp_rn((float)s.A);
+  const float rA = approx_rcp((float)s.A);
   const int bw = px1 - px0 + 1, n = bw * (py1 - py0 + 1);
   const int dy = 32 / bw, dx = 32 - dy * bw;
   int lx = lane % bw, ly = lane / bw;
@@ -136,7 +161,7 @@ __device__ __forceinline__ unsigned raster_warp(const TriSetup& s, unsigned long
     const unsigned m = __ballot_sync(FULL_MASK, cov);
     if (m != 0u) {
       if (cov)
-        key_min<false>(skey, ((py0 + ly - y0) << bshift_x) + (px0 + lx - x0), a1 + e.b1, a2 + e.b2, s, rA, tag);
+        key_min_large(skey, ((py0 + ly - y0) << bshift_x) + (px0 + lx - x0), a1 + e.b1, a2 + e.b2, s, rA, tag);
       frags += __popc(m);
     }
     lx += dx; ly += dy;
@@ -166,15 +191,15 @@ __device__ __forceinline__ void write_empty(const ProcessParams& p, size_t o) {
 // Barycentrics of pixel (x, y) from a record: exact int64 edge functions
 // times 1/A.
 __device__ __forceinline__ void rec_bary(const int* r, int x, int y, float& b0, float& b1, float& b2) {
-  const long long Px = 256LL * x + 128, Py = 256LL * y + 128;
+  const int Px = 256 * x + 128, Py = 256 * y + 128;
   const int X0 = r[0], Y0 = r[1], X1 = r[2], Y1 = r[3], X2 = r[4], Y2 = r[5];
   const float rA = __int_as_float(r[R_RA]);
-  const long long w0 = (long long)(X2 - X1) * (Py - Y1) - (long long)(Y2 - Y1) * (Px - X1);
+  // exact edge functions from 32-bit differences (each below 2^24) widened once
   const long long w1 = (long long)(X0 - X2) * (Py - Y2) - (long long)(Y0 - Y2) * (Px - X2);
   const long long w2 = (long long)(X1 - X0) * (Py - Y0) - (long long)(Y1 - Y0) * (Px - X0);
-  b0 = (float)w0 * rA;
   b1 = (float)w1 * rA;
   b2 = (float)w2 * rA;
+  b0 = 1.0f - b1 - b2;
 }
 
 __device__ __forceinline__ void shade_from_record(const ProcessParams& p, const int* r, int x, int y, size_t o,
@@ -219,12 +244,11 @@ __device__ __forceinline__ void shade_from_global(const ProcessParams& p, unsign
   TriSetup s;
   setup_triangle(__ldg(p.tris + 3 * (size_t)t), __ldg(p.tris + 3 * (size_t)t + 1), __ldg(p.tris + 3 * (size_t)t + 2),
                  p.vtx, s);
-  const long long Px = 256LL * x + 128, Py = 256LL * y + 128;
-  const long long w0 = (long long)(s.X2 - s.X1) * (Py - s.Y1) - (long long)(s.Y2 - s.Y1) * (Px - s.X1);
+  const int Px = 256 * x + 128, Py = 256 * y + 128;
   const long long w1 = (long long)(s.X0 - s.X2) * (Py - s.Y2) - (long long)(s.Y0 - s.Y2) * (Px - s.X2);
   const long long w2 = (long long)(s.X1 - s.X0) * (Py - s.Y0) - (long long)(s.Y1 - s.Y0) * (Px - s.X0);
-  const float rA = __frcp_rn((float)s.A);
-  const float b0 = (float)w0 * rA, b1 = (float)w1 * rA, b2 = (float)w2 * rA;
+  const float rA = approx_rcp((float)s.A);
+  const float b1 = (float)w1 * rA, b2 = (float)w2 * rA, b0 = 1.0f - b1 - b2;
   float c0 = 0.80f, c1 = 0.75f, c2 = 0.65f;
   if (p.color) {
     const float* q0 = p.color + 3 * (size_t)s.v0;
@@ -258,15 +282,12 @@ __device__ __forceinline__ void shade_from_global(const ProcessParams& p, unsign
 __device__ __forceinline__ void fill_record(const ProcessParams& p, const TriSetup& s, int* r, float L0, float L1,
                                             float L2) {
   r[0] = s.X0; r[1] = s.Y0; r[2] = s.X1; r[3] = s.Y1; r[4] = s.X2; r[5] = s.Y2;
-  r[R_RA] = __float_as_int(__frcp_rn((float)s.A));
+  r[R_RA] = __float_as_int(approx_rcp((float)s.A));
   float* a = reinterpret_cast<float*>(r + R_ATTR);
   const int v[3] = {s.v0, s.v1, s.v2};
   if (p.mode == PIKO_SHADE_LAMBERT) {
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const float* n = p.normal + 3 * (size_t)v[j];
-      a[j] = __ldg(n) * L0 + __ldg(n + 1) * L1 + __ldg(n + 2) * L2;
-    }
+    for (int j = 0; j < 3; ++j) a[j] = __ldg(p.vdot + v[j]);
     if (p.color) {
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
@@ -312,9 +333,9 @@ __global__ void __maxnreg__(PIKO_PROCESS_MAXNREG) k_process(ProcessParams p) {
   unsigned long long* skey = smem;                                       // [bin_px]
   unsigned long long* sbig = smem + bin_px;                              // [nt] ring of (slot << 32 | t)
   int* srec = reinterpret_cast<int*>(smem + bin_px + nt);               // [nslots][stride]
-  __shared__ int s_tile[2];
+  __shared__ int s_tile[3];
   __shared__ unsigned s_nbig;
-  if (p.st->flags & (1u << PIKO_ERR_OVERFLOW)) return;
+  if (p.st->flags & STATUS_SKIP_MASK) return;
 
   float L0 = 0.f, L1 = 0.f, L2 = 0.f;
   if (p.mode == PIKO_SHADE_LAMBERT) {
@@ -324,35 +345,48 @@ __global__ void __maxnreg__(PIKO_PROCESS_MAXNREG) k_process(ProcessParams p) {
   for (int i = tid; i < bin_px; i += nt) skey[i] = KEY_EMPTY;
   if (tid == 0) {
     s_nbig = 0u;
-    if (dynamic) s_tile[0] = (int)atomicAdd(&p.st->queue_head, 1u);
+    if (dynamic) {  // the queue hands out tiles two iterations ahead
+      s_tile[0] = (int)atomicAdd(&p.st->queue_head, 1u);
+      s_tile[1] = (int)atomicAdd(&p.st->queue_head, 1u);
+    }
   }
   __syncthreads();
   const unsigned no_slot = (1u << p.slot_bits) - 1u;
   unsigned big_base = 0u;  // entries of the large-triangle ring consumed so far (uniform)
   unsigned long long n_tests = 0, n_frags = 0, n_shaded = 0;  // PIKO_OPT_STATS only
 
-  for (int iter = 0;; ++iter) {
-    int tile;
+  // The first hops of each tile's dependent loads (its bin-list range and
+  // this thread's first entry) are issued one tile ahead.
+  int tile = dynamic ? s_tile[0] : (int)blockIdx.x;
+  unsigned beg = 0u, end = 0u, t_first = 0u;
+  if (tile < p.ntiles) {
+    beg = __ldg(p.bin_off + tile);
+    end = __ldg(p.bin_off + tile + 1);
+    if (beg + tid < end) t_first = __ldg(p.bin_tris + beg + tid);
+  }
+  for (int iter = 0; tile < p.ntiles; ++iter) {
+    int next;
     if (p.schedule == PIKO_SCHED_HARDWARE) {
-      if (iter > 0) break;
-      tile = blockIdx.x;
+      next = p.ntiles;
     } else if (p.schedule == PIKO_SCHED_STATIC) {
-      tile = blockIdx.x + iter * gridDim.x;
+      next = tile + gridDim.x;
     } else {
-      tile = s_tile[iter & 1];
-      // fetch the next tile now; it is read after two more barriers
-      if (tid == 0 && tile < p.ntiles) s_tile[(iter + 1) & 1] = (int)atomicAdd(&p.st->queue_head, 1u);
+      next = s_tile[(iter + 1) % 3];
+      if (tid == 0 && next < p.ntiles) s_tile[(iter + 2) % 3] = (int)atomicAdd(&p.st->queue_head, 1u);
     }
-    if (tile >= p.ntiles) break;
+    unsigned nbeg = 0u, nend = 0u;
+    if (next < p.ntiles) {
+      nbeg = __ldg(p.bin_off + next);
+      nend = __ldg(p.bin_off + next + 1);
+    }
     const int tx = tile % p.g.nbx, ty = tile / p.g.nbx;
     const int x0 = tx << p.g.bshift_x, y0 = ty << p.g.bshift_y;
     const int x1 = min(x0 + bin_w, p.g.W) - 1, y1 = min(y0 + bin_h, p.g.H) - 1;
-    const unsigned beg = __ldg(p.bin_off + tile), end = __ldg(p.bin_off + tile + 1);
     for (unsigned c = beg; c < end; c += nt) {
       const unsigned i = c + tid;
       bool pushed = false;
       if (i < end) {
-        const unsigned t = __ldg(p.bin_tris + i);
+        const unsigned t = c == beg ? t_first : __ldg(p.bin_tris + i);
         const unsigned slot = (i - beg) < (unsigned)p.nslots ? (i - beg) : no_slot;
         TriSetup s;
         load_setup(p, t, s);
@@ -401,6 +435,9 @@ __global__ void __maxnreg__(PIKO_PROCESS_MAXNREG) k_process(ProcessParams p) {
         __syncthreads();
       }
     }
+    // the next tile's first entry for this thread, in flight during shading
+    unsigned t_next = 0u;
+    if (nbeg + tid < nend) t_next = __ldg(p.bin_tris + nbeg + tid);
     // shade, write, and leave the key tile cleared for the next tile
     for (int i = tid; i < bin_px; i += nt) {
       const unsigned long long k = skey[i];
@@ -425,6 +462,10 @@ __global__ void __maxnreg__(PIKO_PROCESS_MAXNREG) k_process(ProcessParams p) {
         shade_from_global(p, t, x, y, o, L0, L1, L2);
     }
     __syncthreads();
+    tile = next;
+    beg = nbeg;
+    end = nend;
+    t_first = t_next;
   }
   if (p.stats) {
     atomicAdd(&p.st->tests, n_tests);

@@ -348,6 +348,188 @@ def run_ours(args):
     return 0
 
 
+def _timed_steps(step, K, warmup, flush, stream):
+    import torch
+    for _ in range(warmup):
+        flush.zero_()
+        step(None)
+    torch.cuda.synchronize()
+    records = []
+    for _ in range(K):
+        flush.zero_()
+        marks = {}
+        step(marks)
+        records.append(marks)
+    torch.cuda.synchronize()
+    return records
+
+
+def run_extra(args):
+    """Measurements of the other rows of the hot path (one GPU, rank 0):
+    deferred: power-law 1080p G-buffer forward + 64-light pass;
+    sphere: 64 views of a 99.5k-triangle sphere, forward + L2-loss backward."""
+    import numpy as np
+    import torch
+
+    from paper_1404_6293_gb300 import _lib as L
+    from paper_1404_6293_gb300 import scenes as S
+    from paper_1404_6293_gb300.raster import DeviceScene, Framebuffer, Rasterizer
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)  # creates the underlying CUDA event
+        return e
+    clocks = ClockSampler(0)
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+
+    if args.workload == "deferred":
+        scene = S.power_law_triangles()
+        lights = torch.from_numpy(S.point_lights(scene.width, scene.height, 64)).cuda()
+        r = Rasterizer(scene.width, scene.height, args.bins, args.bins, args.schedule)
+        ds = DeviceScene.from_host(scene)
+        fb = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode)
+        out = torch.empty((scene.height, scene.width, 4), dtype=torch.float32, device="cuda")
+        r.forward(ds, fb)
+        assert r.status()[0] == 0
+        r.set_option(L.PIKO_OPT_CHECK_CAPACITY, 0)
+        r.set_option(L.PIKO_OPT_STATS, 1)
+        r.forward(ds, fb)
+        stats = r.stats()
+        r.set_option(L.PIKO_OPT_STATS, 0)
+        covered = int((fb.key != -1).sum().item())
+
+        def step(m):
+            if m is None:
+                r.forward(ds, fb)
+                r.deferred_light(fb, lights, out)
+                return
+            m["stage"] = [ev() for _ in range(L.PIKO_NUM_STAGE_EVENTS)]
+            m["light_end"] = ev()
+            r.set_stage_events(m["stage"])
+            r.forward(ds, fb)
+            r.deferred_light(fb, lights, out)
+            m["light_end"].record(stream)
+
+        mark = clocks.mark()
+        recs = _timed_steps(step, args.steps, args.warmup, flush, stream)
+        clk = clocks.stop(mark)
+        assert r.status()[0] == 0
+        fwd = np.array([m["stage"][0].elapsed_time(m["stage"][5]) for m in recs])
+        light = np.array([m["stage"][5].elapsed_time(m["light_end"]) for m in recs])
+        proc = np.array([m["stage"][4].elapsed_time(m["stage"][5]) for m in recs])
+        ms = float((fwd + light).mean())
+        light_ops = 30 * covered * 64
+        alu_peak = n_sm * 128 * ((clk or {}).get("sm_mhz") or 1470.0) * 1e6 / 1e9
+        light_bytes = scene.width * scene.height * (8 + 8 + 8 + 16)
+        lt = float(light.mean()) * 1e-3
+        line.update({"value": scene.num_triangles / (ms * 1e-3) / 1e6, "ms_per_step": ms, "dtype": "int64+f32",
+                     "config": {"workload": "power-law 1920x1080, 500k triangles, G-buffer + 64 point lights",
+                                "bin": [args.bins, args.bins], "schedule": args.schedule,
+                                "l2": "flushed between steps (256 MiB write)"},
+                     "forward_ms": float(fwd.mean()), "process_ms": float(proc.mean()),
+                     "light_pass_ms": float(light.mean()),
+                     "light_gpixlights_s": covered * 64 / lt / 1e9, "work": {**stats, "covered_pixels": covered},
+                     "roofline": {"kernel": "k_deferred_light", "bound": "alu" if light_ops / (alu_peak * 1e9) >
+                                  light_bytes / (hbm * 1e9) else "hbm",
+                                  "achieved": light_ops / lt / 1e9, "peak": alu_peak, "unit": "Gop/s",
+                                  "frac": light_ops / lt / 1e9 / alu_peak, "traffic": None,
+                                  "hbm_frac": light_bytes / lt / 1e9 / hbm},
+                     "clocks": clk, "gpu_launches": 6 * args.steps})
+        if not args.no_cpu_baseline:
+            import oracle
+            t0 = time.perf_counter()
+            key, _ = oracle.raster_bbox(scene, threads=len(os.sched_getaffinity(0)))
+            gn, ga = oracle.shade(scene, key)
+            oracle.light_pass(key, gn, ga, lights.cpu().numpy())
+            dt = time.perf_counter() - t0
+            line["cpu_baseline"] = {"value": scene.num_triangles / dt / 1e6, "unit": UNIT,
+                                    "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                                    "sample": f"one full frame: bounding-box oracle, float64 G-buffer and light pass, {dt:.2f} s"}
+    elif args.workload == "sphere":
+        from paper_1404_6293_gb300.autograd import render  # noqa: F401  (same kernels as below)
+        sph, mvps = S.sphere_views(num_views=64)
+        W = H = 512
+        r = Rasterizer(W, H, args.bins, args.bins, args.schedule)
+        ds = DeviceScene.from_host(sph)
+        mv = torch.from_numpy(mvps).cuda()
+        tgt = torch.from_numpy(S.target_image(W, H, seed=1240, views=64)).cuda()
+        fbs = [Framebuffer.allocate(W, H, sph.shade_mode) for _ in range(64)]
+        dc = torch.zeros_like(ds.color)
+        dn = torch.zeros_like(ds.normal)
+        dl = torch.zeros_like(ds.light_dir)
+        g = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+        for v in range(64):
+            ds.mvp = mv[v]
+            r.forward(ds, fbs[v])
+        assert r.status()[0] == 0
+        r.set_option(L.PIKO_OPT_CHECK_CAPACITY, 0)
+        covered = int(sum((fb.key != -1).sum().item() for fb in fbs))
+
+        def step(m):
+            dc.zero_(); dn.zero_(); dl.zero_()
+            if m is not None:
+                m["s"] = ev(); m["f"] = ev(); m["e"] = ev(); m["bw"] = 0.0
+                m["s"].record(stream)
+            for v in range(64):
+                ds.mvp = mv[v]
+                r.forward(ds, fbs[v])
+            if m is not None:
+                m["f"].record(stream)
+            for v in range(64):
+                ds.mvp = mv[v]
+                torch.sub(fbs[v].rgba, tgt[v], out=g).mul_(2.0)
+                g[..., 3] = 0.0
+                r.backward(ds, fbs[v], g, dc, dn, dl)
+            if m is not None:
+                m["e"].record(stream)
+
+        mark = clocks.mark()
+        recs = _timed_steps(step, args.steps, args.warmup, flush, stream)
+        clk = clocks.stop(mark)
+        assert r.status()[0] == 0
+        fwd = np.array([m["s"].elapsed_time(m["f"]) for m in recs])
+        bwd = np.array([m["f"].elapsed_time(m["e"]) for m in recs])
+        ms = float((fwd + bwd).mean())
+        T = 64 * sph.num_triangles
+        bw_bytes = 64 * W * H * (8 + 16) + sph.num_vertices * (16 + 12 * 2) + 64 * sph.num_vertices * 12 * 2
+        bt = float(bwd.mean()) * 1e-3
+        line.update({"value": T / (ms * 1e-3) / 1e6, "ms_per_step": ms, "dtype": "int64+f32",
+                     "config": {"workload": "sphere 99.5k triangles, 64 views 512x512, forward + L2 backward",
+                                "bin": [args.bins, args.bins], "schedule": args.schedule,
+                                "l2": "flushed between steps (256 MiB write)"},
+                     "forward_ms": float(fwd.mean()), "backward_ms": float(bwd.mean()),
+                     "covered_pixels": covered,
+                     "roofline": {"kernel": "backward (64 views, incl. loss gradient)", "bound": "hbm",
+                                  "achieved": bw_bytes / bt / 1e9, "peak": hbm, "unit": "GB/s",
+                                  "frac": bw_bytes / bt / 1e9 / hbm, "traffic": None},
+                     "clocks": clk, "gpu_launches": 64 * 5 + 64 * 2})
+        if not args.no_cpu_baseline:
+            import oracle
+            t0 = time.perf_counter()
+            sv = S.Scene(W, H, sph.pos, sph.tris, color=sph.color, normal=sph.normal, mvp=mvps[0],
+                         light_dir=sph.light_dir, shade_mode=sph.shade_mode)
+            key, _ = oracle.raster_bbox(sv, threads=len(os.sched_getaffinity(0)))
+            rgba = oracle.shade(sv, key)
+            gg = np.zeros((H, W, 4))
+            gg[..., :3] = 2 * (rgba[..., :3] - tgt[0].cpu().numpy()[..., :3])
+            oracle.backward(sv, key, gg)
+            dt = time.perf_counter() - t0
+            line["cpu_baseline"] = {"value": sph.num_triangles / dt / 1e6, "unit": UNIT,
+                                    "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                                    "sample": f"one view: bounding-box oracle, float64 shading and gradients, {dt:.2f} s"}
+    else:
+        raise SystemExit(f"unknown workload {args.workload}")
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -357,6 +539,8 @@ def main():
     ap.add_argument("--bins", type=int, default=16)
     ap.add_argument("--schedule", default="static", choices=["static", "dynamic", "hardware"])
     ap.add_argument("--threads", type=int, default=0, help="Process CTA size (0: library default)")
+    ap.add_argument("--workload", default="heightfield", choices=["heightfield", "deferred", "sphere"],
+                    help="heightfield: the headline line; the others measure further rows of the path")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -364,7 +548,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
-    sys.exit(run_reference(args) if args.impl == "reference" else run_ours(args))
+    if args.impl == "reference":
+        sys.exit(run_reference(args))
+    sys.exit(run_ours(args) if args.workload == "heightfield" else run_extra(args))
 
 
 if __name__ == "__main__":

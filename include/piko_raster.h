@@ -82,6 +82,9 @@ extern "C" {
                                        by a whole warp (default 32)                         */
 #define PIKO_OPT_STATS 6            /* 1: the Process stage also counts its work (see
                                        piko_raster_stats); default 0                        */
+#define PIKO_OPT_BATCH_LAUNCH 7     /* how piko_raster_forward_batch launches its phases:
+                                       0 (default) one persistent cooperative kernel with grid
+                                       barriers between phases; 1 one launch per phase     */
 
 /* Stage boundaries of one forward pass, for piko_raster_set_stage_events. */
 #define PIKO_NUM_STAGE_EVENTS 6 /* before vertex, after vertex, after setup+count, after scan,
@@ -159,6 +162,44 @@ int piko_raster_backward(piko_raster *h, const piko_scene *scene, const piko_fra
  * this library's.  1 <= n_lights <= 1024. */
 int piko_raster_deferred_light(piko_raster *h, const piko_framebuffer *gbuf, const float *lights,
                                int n_lights, float *rgba_out, void *cuda_stream);
+
+/* Many scenes in one pass (scenes with uneven triangle counts and
+ * resolutions, or many views of one mesh): vertex stage, setup and counts,
+ * scan, scatter and Process for all n scenes run as one persistent
+ * cooperative launch whose CTAs meet at grid barriers between the phases
+ * (PIKO_OPT_BATCH_LAUNCH = 1: one launch per phase instead).  The paper's
+ * runtime is multi-kernel (Sec. 5, Sec. 6) and names a persistent kernel as
+ * the alternative; scenes, bins and tiles of all scenes share one index
+ * space here.
+ *  scenes, fbs  host arrays of n descriptors (their pointers are device
+ *               memory); each scene has its own width and height
+ *               (1..32767) and shading mode, and writes its own framebuffer.
+ *  bin_sizes    host int32 [n][2] (bin width, height per scene, each in
+ *               {8,16,32,64}), or NULL for the handle's bin size.
+ *  schedules    host int32 [n] PIKO_SCHED_STATIC (the scene's tiles are dealt
+ *               round robin over the persistent CTAs) or PIKO_SCHED_DYNAMIC
+ *               (taken from a shared queue after the static tiles; HARDWARE
+ *               is treated as DYNAMIC), or NULL for the handle's schedule.
+ * Results are bit-identical to n piko_raster_forward calls with the same
+ * bin sizes.  With PIKO_OPT_CHECK_CAPACITY = 1 the call waits for the
+ * launch, and relaunches once with larger bin lists if they overflowed; with
+ * 0 it never waits (so it can be captured in a CUDA graph after a first call
+ * with the same scenes, or piko_raster_reserve, has sized the scratch) and
+ * reports overflow through piko_raster_status.  A grid barrier or scan wait
+ * that runs out of its time budget records PIKO_ERR_TIMEOUT and every later
+ * phase is skipped.  The batch keeps its own scratch in the handle; n >= 1,
+ * sum of vertices and of triangles below 2^31. */
+int piko_raster_forward_batch(piko_raster *h, const piko_scene *scenes, int n, piko_framebuffer *fbs,
+                              const int32_t *bin_sizes, const int32_t *schedules, void *cuda_stream);
+
+/* Gradients for all scenes of the last piko_raster_forward_batch on this
+ * handle (same scenes, same order), in one launch: dl_drgba, dl_dcolor,
+ * dl_dnormal and dl_dlight are host arrays of n device pointers (entries
+ * may be NULL to skip that output for a scene); semantics per scene as in
+ * piko_raster_backward (accumulated, visibility fixed by fbs[i].key). */
+int piko_raster_backward_batch(piko_raster *h, const piko_scene *scenes, int n, const piko_framebuffer *fbs,
+                               const float *const *dl_drgba, float *const *dl_dcolor, float *const *dl_dnormal,
+                               float *const *dl_dlight, void *cuda_stream);
 
 /* Pre-sizes scratch for scenes of up to max_vertices / max_triangles and
  * max_bin_entries (triangle, tile) pairs, so that later forwards allocate

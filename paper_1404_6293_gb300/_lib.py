@@ -33,6 +33,7 @@ PIKO_OPT_CHECK_CAPACITY = 3
 PIKO_OPT_SCHEDULE = 4
 PIKO_OPT_SMALL_TRI_PIXELS = 5
 PIKO_OPT_STATS = 6
+PIKO_OPT_BATCH_LAUNCH = 7
 PIKO_NUM_STAGE_EVENTS = 6
 
 ERROR_NAMES = {
@@ -83,15 +84,10 @@ def _declare(lib):
                  "piko_raster_reserve", "piko_raster_set_option", "piko_raster_status",
                  "piko_raster_version", "piko_raster_set_stage_events", "piko_raster_stats"):
         getattr(lib, name).restype = i32
-    if hasattr(lib, "piko_raster_forward_batch"):
-        lib.piko_raster_forward_batch.argtypes = [P, C.POINTER(PikoScene), i32, C.POINTER(PikoFramebuffer),
-                                                  P, P, P]
-        lib.piko_raster_forward_batch.restype = i32
-    if hasattr(lib, "piko_raster_backward_batch"):
-        lib.piko_raster_backward_batch.argtypes = [P, C.POINTER(PikoScene), i32, C.POINTER(PikoFramebuffer),
-                                                   C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
-                                                   C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), P]
-        lib.piko_raster_backward_batch.restype = i32
+    lib.piko_raster_forward_batch.argtypes = [P, C.POINTER(PikoScene), i32, C.POINTER(PikoFramebuffer), P, P, P]
+    lib.piko_raster_forward_batch.restype = i32
+    lib.piko_raster_backward_batch.argtypes = [P, C.POINTER(PikoScene), i32, C.POINTER(PikoFramebuffer), P, P, P, P, P]
+    lib.piko_raster_backward_batch.restype = i32
     return lib
 
 

@@ -1,0 +1,104 @@
+"""Autotuner for the binning and scheduling knobs.
+
+The Piko paper explores bin size and schedule by hand for each scene and
+architecture (Sec. 7.2: spatial binning helps most scenes but not one made
+of tiny uniform triangles; fusing stages trades load balance for locality).
+This tuner searches the same knobs automatically: for a scene it times the
+forward pass under every (bin size, schedule) candidate with CUDA events and
+keeps the fastest.  Results are cached by workload features (resolution,
+triangle count, coverage density, shading mode) so that similar scenes share
+one measurement; the cache can be saved to and loaded from JSON.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+from typing import Dict, Iterable, List, Optional, Tuple
+
+import torch
+
+from .raster import DeviceScene, Rasterizer
+
+DEFAULT_BINS: Tuple[Tuple[int, int], ...] = ((8, 8), (16, 16), (32, 32), (64, 64))
+DEFAULT_SCHEDULES: Tuple[str, ...] = ("static", "dynamic")
+
+
+def features(scene: DeviceScene) -> str:
+    """Workload class of a scene: log2 buckets of pixels and triangles, the
+    triangles-per-pixel density bucket, and the shading mode."""
+    px = scene.width * scene.height
+    T = max(1, scene.num_triangles)
+    return "px%d_t%d_d%d_m%d" % (round(math.log2(px) * 2), round(math.log2(T) * 2),
+                                 round(math.log2(T / px) * 2), scene.shade_mode)
+
+
+class Autotuner:
+    def __init__(self, bins: Iterable[Tuple[int, int]] = DEFAULT_BINS,
+                 schedules: Iterable[str] = DEFAULT_SCHEDULES, reps: int = 3, cache_path: Optional[str] = None):
+        self.bins = tuple(tuple(b) for b in bins)
+        self.schedules = tuple(schedules)
+        self.reps = reps
+        self.cache: Dict[str, dict] = {}
+        self.cache_path = cache_path
+        if cache_path and os.path.exists(cache_path):
+            with open(cache_path) as f:
+                self.cache = json.load(f)
+        self._handles: Dict[tuple, Rasterizer] = {}
+
+    def _handle(self, W, H, bw, bh, sched) -> Rasterizer:
+        k = (W, H, bw, bh, sched)
+        if k not in self._handles:
+            self._handles[k] = Rasterizer(W, H, bw, bh, sched)
+        return self._handles[k]
+
+    def time_candidate(self, scene: DeviceScene, bw: int, bh: int, sched: str) -> float:
+        """Median forward time in ms of one candidate (after a sizing pass)."""
+        r = self._handle(scene.width, scene.height, bw, bh, sched)
+        fb = r.forward(scene)  # sizes the bin lists
+        r.status()
+        times: List[float] = []
+        for _ in range(self.reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            r.forward(scene, fb)
+            b.record()
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        times.sort()
+        return times[len(times) // 2]
+
+    def tune(self, scene: DeviceScene) -> dict:
+        best = None
+        trials = []
+        for bw, bh in self.bins:
+            for sched in self.schedules:
+                ms = self.time_candidate(scene, bw, bh, sched)
+                trials.append({"bin": [bw, bh], "schedule": sched, "ms": ms})
+                if best is None or ms < best["ms"]:
+                    best = {"bin": [bw, bh], "schedule": sched, "ms": ms}
+        best["trials"] = trials
+        return best
+
+    def choose(self, scene: DeviceScene) -> Tuple[Tuple[int, int], str]:
+        key = features(scene)
+        if key not in self.cache:
+            self.cache[key] = self.tune(scene)
+        c = self.cache[key]
+        return (c["bin"][0], c["bin"][1]), c["schedule"]
+
+    def choose_all(self, scenes: List[DeviceScene]):
+        """Per-scene (bin sizes, schedules) lists for forward_batch."""
+        picks = [self.choose(s) for s in scenes]
+        return [p[0] for p in picks], [p[1] for p in picks]
+
+    def save(self, path: Optional[str] = None):
+        path = path or self.cache_path
+        if path:
+            with open(path, "w") as f:
+                json.dump(self.cache, f, indent=1, sort_keys=True)
+
+    def close(self):
+        for r in self._handles.values():
+            r.close()
+        self._handles.clear()

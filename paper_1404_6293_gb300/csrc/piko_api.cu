@@ -8,6 +8,18 @@
 
 using namespace piko;
 
+struct BatchState;
+void batch_state_free(BatchState* bs);
+int batch_prepare(BatchState*& bs, int num_sms, const piko_scene* scenes, int n, piko_framebuffer* fbs,
+                  const int32_t* bin_sizes, const int32_t* schedules, int default_bin_w, int default_bin_h,
+                  int default_schedule, cudaStream_t stream, std::string& err);
+int batch_launch_forward(BatchState* bs, DevStatus* st, bool persistent, cudaStream_t stream, std::string& err);
+long long batch_capacity(const BatchState* bs);
+int batch_grow_entries(BatchState* bs, long long need, std::string& err);
+int batch_launch_backward(BatchState* bs, const piko_scene* scenes, int n, const piko_framebuffer* fbs,
+                          const float* const* dl, float* const* dc, float* const* dn, float* const* dlt, int num_sms,
+                          cudaStream_t stream, std::string& err);
+
 int piko_backward_launch(int W, int H, int mode, int unclamped, int T, int V, const int* tris, const int4* vtx,
                          const float* color,
                          const float* normal, const float* light, const unsigned long long* key,
@@ -23,6 +35,8 @@ struct piko_raster {
   int check_capacity = 1;
   int small_px = 32;
   int stats = 0;
+  int batch_launch = 0;  // 0 persistent cooperative, 1 one launch per phase
+  BatchState* batch = nullptr;
   cudaEvent_t stage_ev[PIKO_NUM_STAGE_EVENTS] = {};
   bool use_stage_ev = false;
   int device = 0, num_sms = 0;
@@ -141,6 +155,7 @@ void piko_raster_destroy(piko_raster* h) {
   cudaFree(h->chunk_state);
   cudaFree(h->bin_tris);
   cudaFree(h->status);
+  batch_state_free(h->batch);
   if (h->h_needed) cudaFreeHost(h->h_needed);
   cudaGetLastError();
   delete h;
@@ -175,6 +190,10 @@ int piko_raster_set_option(piko_raster* h, int key, int value) {
     case PIKO_OPT_STATS:
       if (value != 0 && value != 1) return fail(h, PIKO_ERR_INVALID_ARG, "stats must be 0 or 1");
       h->stats = value;
+      return PIKO_OK;
+    case PIKO_OPT_BATCH_LAUNCH:
+      if (value != 0 && value != 1) return fail(h, PIKO_ERR_INVALID_ARG, "batch launch must be 0 or 1");
+      h->batch_launch = value;
       return PIKO_OK;
     case PIKO_OPT_SMALL_TRI_PIXELS:
       if (value < 0 || value > 4096) return fail(h, PIKO_ERR_INVALID_ARG, "small-triangle pixels out of range");
@@ -321,6 +340,41 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
   if (e != cudaSuccess) return cuda_fail(h, e, "process launch");
   if (ev) cudaEventRecord(h->stage_ev[5], st);
   return PIKO_OK;
+}
+
+int piko_raster_forward_batch(piko_raster* h, const piko_scene* scenes, int n, piko_framebuffer* fbs,
+                              const int32_t* bin_sizes, const int32_t* schedules, void* cuda_stream) {
+  if (!h) return PIKO_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  h->last_stream = st;
+  int r = batch_prepare(h->batch, h->num_sms, scenes, n, fbs, bin_sizes, schedules, h->bin_w, h->bin_h, h->schedule,
+                        st, h->err);
+  if (r != PIKO_OK) return r;
+  for (int attempt = 0;; ++attempt) {
+    if ((r = batch_launch_forward(h->batch, h->status, h->batch_launch == 0, st, h->err)) != PIKO_OK) return r;
+    if (!h->check_capacity) return PIKO_OK;
+    cudaError_t e = cudaMemcpyAsync(h->h_needed, &h->status->needed, sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "batch bin-list size read-back");
+    const long long need = (long long)*h->h_needed;
+    if (need <= batch_capacity(h->batch)) return PIKO_OK;
+    if (attempt > 0 || need > 0xFFFFFFF0LL) return fail(h, PIKO_ERR_OVERFLOW, "batch bin lists too large");
+    if ((r = batch_grow_entries(h->batch, need, h->err)) != PIKO_OK) return r;
+    e = cudaMemsetAsync(h->status, 0, sizeof(unsigned) * 2, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "status clear");
+  }
+}
+
+int piko_raster_backward_batch(piko_raster* h, const piko_scene* scenes, int n, const piko_framebuffer* fbs,
+                               const float* const* dl_drgba, float* const* dl_dcolor, float* const* dl_dnormal,
+                               float* const* dl_dlight, void* cuda_stream) {
+  if (!h) return PIKO_ERR_INVALID_ARG;
+  if (!scenes || !fbs || n < 1) return fail(h, PIKO_ERR_INVALID_ARG, "backward_batch needs scenes and framebuffers");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  h->last_stream = st;
+  return batch_launch_backward(h->batch, scenes, n, fbs, dl_drgba, dl_dcolor, dl_dnormal, dl_dlight, h->num_sms, st,
+                               h->err);
 }
 
 int piko_raster_set_stage_events(piko_raster* h, void* const* events, int n) {

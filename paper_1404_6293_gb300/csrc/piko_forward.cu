@@ -8,22 +8,13 @@
 //   k_scatter      triangle indices into the bin lists
 // The per-tile Process stage is in piko_process.cu.
 
-#include "piko_internal.cuh"
+#include "piko_scan.cuh"
 
 namespace piko {
 
 // ======================================================================
 // Vertex stage
 // ======================================================================
-__device__ __forceinline__ float mvp_row(const float* m, float4 p) {
-  // ((m0*x + m1*y) + m2*z) + m3*w, every operation rounded, no contraction
-  float acc = __fmul_rn(m[0], p.x);
-  acc = __fadd_rn(acc, __fmul_rn(m[1], p.y));
-  acc = __fadd_rn(acc, __fmul_rn(m[2], p.z));
-  acc = __fadd_rn(acc, __fmul_rn(m[3], p.w));
-  return acc;
-}
-
 __global__ void __launch_bounds__(256) k_vertex(int W, int H, int V, const float4* __restrict__ pos,
                                                 const float* __restrict__ mvp, int4* __restrict__ vtx,
                                                 const float* __restrict__ normal, const float* __restrict__ light,
@@ -42,31 +33,8 @@ __global__ void __launch_bounds__(256) k_vertex(int W, int H, int V, const float
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V; i += gridDim.x * blockDim.x) {
     if (vdot) vdot[i] = __ldg(normal + 3 * (size_t)i) * L0 + __ldg(normal + 3 * (size_t)i + 1) * L1 +
                         __ldg(normal + 3 * (size_t)i + 2) * L2;
-    const float4 p = __ldg(pos + i);  // one 16-byte load per vertex, coalesced across the warp
-    float c0 = p.x, c1 = p.y, c2 = p.z, c3 = p.w;
-    if (has_m) {
-      c0 = mvp_row(m + 0, p);
-      c1 = mvp_row(m + 4, p);
-      c2 = mvp_row(m + 8, p);
-      c3 = mvp_row(m + 12, p);
-    }
-    int4 o = make_int4(0, 0, 0, 0);
-    if (c3 > 0.0f) {
-      const float nx = __fdiv_rn(c0, c3), ny = __fdiv_rn(c1, c3), nz = __fdiv_rn(c2, c3);
-      if (nz >= -1.0f && nz <= 1.0f) {
-        const float sx = __fmul_rn(__fadd_rn(__fmul_rn(nx, 0.5f), 0.5f), fW);
-        const float sy = __fmul_rn(__fsub_rn(0.5f, __fmul_rn(ny, 0.5f)), fH);
-        const float sz = __fmul_rn(__fadd_rn(__fmul_rn(nz, 0.5f), 0.5f), 16777215.0f);
-        const float fx = __fmul_rn(sx, 256.0f), fy = __fmul_rn(sy, 256.0f);
-        if (fabsf(fx) < 8388608.0f && fabsf(fy) < 8388608.0f) {
-          o.x = __float2int_rn(fx);
-          o.y = __float2int_rn(fy);
-          o.z = (int)__float2uint_rn(sz);
-          o.w = 1;
-        }
-      }
-    }
-    vtx[i] = o;
+    // one 16-byte load per vertex, coalesced across the warp
+    vtx[i] = snap_vertex(__ldg(pos + i), has_m ? m : nullptr, fW, fH);
   }
 }
 
@@ -169,149 +137,25 @@ constexpr unsigned RECT_CULLED = 0xFFFFFFFFu;
 constexpr unsigned RECT_SINGLE = 0x8000u;
 
 // ======================================================================
-// Scan: a single-pass decoupled look-back scan over chunks of
-// SCAN_CHUNK bins, one chunk per CTA (CTAs take chunk numbers from a ticket,
-// so every predecessor of a chunk has already started).  Each chunk
-// publishes its aggregate, then its inclusive prefix, in a 64-bit state word
-// tagged with the frame's epoch (no clearing between frames):
-//   bits 63..62 kind (1 aggregate, 2 inclusive prefix), 61..46 epoch,
-//   45..0 value.
-// off[b] = entries of all earlier bins; the scatter cursor of a bin starts
-// after its single-bin part; both count arrays are zeroed for the next frame.
-// Look-back waits are bounded by a clock budget; on expiry the scan records
-// PIKO_ERR_TIMEOUT and the frame's later stages skip their work.
+// Scan: one CTA per chunk of SCAN_CHUNK bins (scan_chunk in piko_scan.cuh).
 // ======================================================================
 constexpr int SCAN_THREADS = 256;
-constexpr int SCAN_PER = 8;
 constexpr int SCAN_CHUNK = SCAN_THREADS * SCAN_PER;
-constexpr unsigned long long SCAN_KIND_AGG = 1ull << 62, SCAN_KIND_PREFIX = 2ull << 62;
-constexpr unsigned long long SCAN_VALUE_MASK = (1ull << 46) - 1ull;
-constexpr long long SCAN_WAIT_CYCLES = 40000000;  // ~20 ms at 2 GHz
-
-__device__ __forceinline__ void load8(const unsigned* __restrict__ a, int b0, int nbins, bool vec, unsigned* v) {
-  if (vec && b0 + 8 <= nbins) {
-    const uint4 x = __ldcg(reinterpret_cast<const uint4*>(a + b0)), y = __ldcg(reinterpret_cast<const uint4*>(a + b0 + 4));
-    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w; v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
-  } else {
-#pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = b0 + j < nbins ? __ldcg(a + b0 + j) : 0u;
-  }
-}
-
-__device__ __forceinline__ unsigned long long state_load(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void state_store(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
 
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan(int nbins, unsigned* __restrict__ cnt,
                                                        unsigned* __restrict__ bin_off, unsigned* __restrict__ cursor,
                                                        unsigned long long capacity, DevStatus* st,
                                                        unsigned long long* __restrict__ chunk_state, unsigned epoch) {
-  __shared__ unsigned long long warp_sums[SCAN_THREADS / 32];
-  __shared__ unsigned long long s_excl;
-  __shared__ int s_chunk;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const unsigned long long tag = (unsigned long long)(epoch & 0xFFFFu) << 46;
-  if (tid == 0) s_chunk = (int)atomicAdd(&st->scan_ticket, 1u);
+  __shared__ ScanSmem sm;
+  if (threadIdx.x == 0) sm.chunk = (int)atomicAdd(&st->scan_ticket, 1u);
   __syncthreads();
-  const int chunk = s_chunk;
+  const int chunk = sm.chunk;
   const int nchunks = (nbins + SCAN_CHUNK - 1) / SCAN_CHUNK;
   if (chunk >= nchunks) return;  // only with a corrupted ticket; the count pass resets it every frame
-  unsigned* __restrict__ multi = cnt + nbins;
-  const bool vec = (nbins & 3) == 0;  // second array 16-byte aligned
-  const int b0 = chunk * SCAN_CHUNK + tid * SCAN_PER;
-  unsigned sg[SCAN_PER], mu[SCAN_PER];
-  load8(cnt, b0, nbins, vec, sg);
-  load8(multi, b0, nbins, vec, mu);
-  unsigned long long local = 0;
-#pragma unroll
-  for (int j = 0; j < SCAN_PER; ++j) local += (unsigned long long)sg[j] + mu[j];
-  unsigned long long v = local;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long u = __shfl_up_sync(FULL_MASK, v, o);
-    if (lane >= o) v += u;
-  }
-  if (lane == 31) warp_sums[w] = v;
-  __syncthreads();
-  if (w == 0) {
-    unsigned long long x = lane < SCAN_THREADS / 32 ? warp_sums[lane] : 0ull;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long u = __shfl_up_sync(FULL_MASK, x, o);
-      if (lane >= o) x += u;
-    }
-    if (lane < SCAN_THREADS / 32) warp_sums[lane] = x;
-  }
-  __syncthreads();
-  const unsigned long long agg = warp_sums[SCAN_THREADS / 32 - 1];
-  if (tid == 0) {
-    unsigned long long excl = 0;
-    if (chunk == 0) {
-      state_store(chunk_state, SCAN_KIND_PREFIX | tag | (agg & SCAN_VALUE_MASK));
-    } else {
-      state_store(chunk_state + chunk, SCAN_KIND_AGG | tag | (agg & SCAN_VALUE_MASK));
-      const long long t0 = clock64();
-      bool timed_out = false;
-      for (int j = chunk - 1; j >= 0 && !timed_out;) {
-        const unsigned long long sv = state_load(chunk_state + j);
-        const unsigned long long sv_epoch = sv & ~SCAN_VALUE_MASK & ~(3ull << 62);
-        if (sv_epoch != tag || (sv >> 62) == 0) {
-          if (clock64() - t0 > SCAN_WAIT_CYCLES) timed_out = true;
-          else __nanosleep(64);
-          continue;  // predecessor not published for this frame yet
-        }
-        excl += sv & SCAN_VALUE_MASK;
-        if ((sv >> 62) == 2) break;  // inclusive prefix: done
-        --j;
-      }
-      if (timed_out) record_error(st, PIKO_ERR_TIMEOUT);
-      state_store(chunk_state + chunk, SCAN_KIND_PREFIX | tag | ((excl + agg) & SCAN_VALUE_MASK));
-    }
-    s_excl = excl;
-  }
-  __syncthreads();
-  unsigned long long run = s_excl + v - local + (w > 0 ? warp_sums[w - 1] : 0ull);
-  unsigned of[SCAN_PER], cu[SCAN_PER];
-#pragma unroll
-  for (int j = 0; j < SCAN_PER; ++j) {
-    of[j] = (unsigned)run;
-    cu[j] = (unsigned)(run + sg[j]);
-    run += (unsigned long long)sg[j] + mu[j];
-  }
-  if (vec && b0 + SCAN_PER <= nbins) {
-    reinterpret_cast<uint4*>(bin_off + b0)[0] = make_uint4(of[0], of[1], of[2], of[3]);
-    reinterpret_cast<uint4*>(bin_off + b0)[1] = make_uint4(of[4], of[5], of[6], of[7]);
-    reinterpret_cast<uint4*>(cursor + b0)[0] = make_uint4(cu[0], cu[1], cu[2], cu[3]);
-    reinterpret_cast<uint4*>(cursor + b0)[1] = make_uint4(cu[4], cu[5], cu[6], cu[7]);
-    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-    reinterpret_cast<uint4*>(cnt + b0)[0] = z;
-    reinterpret_cast<uint4*>(cnt + b0)[1] = z;
-    reinterpret_cast<uint4*>(multi + b0)[0] = z;
-    reinterpret_cast<uint4*>(multi + b0)[1] = z;
-  } else {
-#pragma unroll
-    for (int j = 0; j < SCAN_PER; ++j)
-      if (b0 + j < nbins) {
-        bin_off[b0 + j] = of[j];
-        cursor[b0 + j] = cu[j];
-        cnt[b0 + j] = 0u;
-        multi[b0 + j] = 0u;
-      }
-  }
-  if (chunk == nchunks - 1 && tid == 0) {
-    const unsigned long long total = s_excl + agg;
-    const bool ok = total <= capacity;
-    if (ok) bin_off[nbins] = (unsigned)total;
-    st->needed = total;
-    st->queue_head = 0u;
-    st->scan_ticket = 0u;  // every chunk took its ticket before this chunk's look-back ended
-    if (!ok) record_error(st, PIKO_ERR_OVERFLOW);
-  }
+  scan_chunk(chunk, nchunks, nbins, cnt, bin_off, cursor, capacity, st, chunk_state, epoch, sm, &st->queue_head);
+  // one CTA per chunk: every ticket was taken before the last chunk's
+  // look-back ended, so the last chunk may reset the ticket
+  if (chunk == nchunks - 1 && threadIdx.x == 0) st->scan_ticket = 0u;
 }
 
 int scan_chunks(int nbins) { return (nbins + SCAN_CHUNK - 1) / SCAN_CHUNK; }

@@ -98,11 +98,15 @@ __device__ __forceinline__ int top_left(int dx, int dy) { return (dy < 0 || (dy 
 // floor(n / A) for A > 0 and |n / A| < 2^25, exact.  The float estimate
 // (relative error below 2^-21) is within a few units of the quotient; the
 // integer remainder then moves it to the unique q with 0 <= n - q*A < A.
+// The fix-up loops run a few times at most for A > 0; their bound only keeps
+// inconsistent inputs from spinning.
+constexpr int DIV_FIX_LIMIT = 64;
+
 __device__ __forceinline__ long long floor_div_est(long long n, long long A, float rA) {
   long long q = (long long)floorf(__fmul_rn((float)n, rA));
   long long r = n - q * A;
-  while (r < 0) { --q; r += A; }
-  while (r >= A) { ++q; r -= A; }
+  for (int it = 0; r < 0 && it < DIV_FIX_LIMIT; ++it) { --q; r += A; }
+  for (int it = 0; r >= A && it < DIV_FIX_LIMIT; ++it) { ++q; r -= A; }
   return q;
 }
 
@@ -112,8 +116,8 @@ __device__ __forceinline__ long long floor_div_est128(__int128 n, long long A, f
   const float nf = (float)(long long)(n >> 32) * 4294967296.0f + (float)(unsigned)(n & 0xFFFFFFFFu);
   long long q = (long long)floorf(nf * rA);
   __int128 r = n - (__int128)q * A;
-  while (r < 0) { --q; r += A; }
-  while (r >= A) { ++q; r -= A; }
+  for (int it = 0; r < 0 && it < DIV_FIX_LIMIT; ++it) { --q; r += A; }
+  for (int it = 0; r >= A && it < DIV_FIX_LIMIT; ++it) { ++q; r -= A; }
   return q;
 }
 
@@ -122,8 +126,8 @@ __device__ __forceinline__ long long floor_div_est128(__int128 n, long long A, f
 __device__ __forceinline__ int floor_div_small(long long n, int A, float rA) {
   int q = (int)floorf((float)n * rA);
   long long r = n - (long long)q * A;
-  while (r < 0) { --q; r += A; }
-  while (r >= A) { ++q; r -= A; }
+  for (int it = 0; r < 0 && it < DIV_FIX_LIMIT; ++it) { --q; r += A; }
+  for (int it = 0; r >= A && it < DIV_FIX_LIMIT; ++it) { ++q; r -= A; }
   return q;
 }
 
@@ -142,6 +146,45 @@ __device__ __forceinline__ unsigned depth_of(long long w1, long long w2, const T
     q = floor_div_est128((__int128)w1 * d1 + (__int128)w2 * d2, s.A, rA);
   }
   return (unsigned)(s.Z0 + q);
+}
+
+// ------------------------------------------------------------ vertex stage
+// ((m0*x + m1*y) + m2*z) + m3*w, every operation rounded, no contraction
+__device__ __forceinline__ float mvp_row(const float* m, float4 p) {
+  float acc = __fmul_rn(m[0], p.x);
+  acc = __fadd_rn(acc, __fmul_rn(m[1], p.y));
+  acc = __fadd_rn(acc, __fmul_rn(m[2], p.z));
+  acc = __fadd_rn(acc, __fmul_rn(m[3], p.w));
+  return acc;
+}
+
+// Transform (m may be NULL for the identity), divide, viewport, 16.8 snap:
+// {X, Y, Z, 1}, or all zero for a vertex that culls its triangles.
+__device__ __forceinline__ int4 snap_vertex(float4 p, const float* m, float fW, float fH) {
+  float c0 = p.x, c1 = p.y, c2 = p.z, c3 = p.w;
+  if (m) {
+    c0 = mvp_row(m + 0, p);
+    c1 = mvp_row(m + 4, p);
+    c2 = mvp_row(m + 8, p);
+    c3 = mvp_row(m + 12, p);
+  }
+  int4 o = make_int4(0, 0, 0, 0);
+  if (c3 > 0.0f) {
+    const float nx = __fdiv_rn(c0, c3), ny = __fdiv_rn(c1, c3), nz = __fdiv_rn(c2, c3);
+    if (nz >= -1.0f && nz <= 1.0f) {
+      const float sx = __fmul_rn(__fadd_rn(__fmul_rn(nx, 0.5f), 0.5f), fW);
+      const float sy = __fmul_rn(__fsub_rn(0.5f, __fmul_rn(ny, 0.5f)), fH);
+      const float sz = __fmul_rn(__fadd_rn(__fmul_rn(nz, 0.5f), 0.5f), 16777215.0f);
+      const float fx = __fmul_rn(sx, 256.0f), fy = __fmul_rn(sy, 256.0f);
+      if (fabsf(fx) < 8388608.0f && fabsf(fy) < 8388608.0f) {
+        o.x = __float2int_rn(fx);
+        o.y = __float2int_rn(fy);
+        o.z = (int)__float2uint_rn(sz);
+        o.w = 1;
+      }
+    }
+  }
+  return o;
 }
 
 // --------------------------------------------------------------- kernels

@@ -1,0 +1,470 @@
+// piko_tile.cuh -- device code of the per-tile Process stage, shared by the
+// single-scene kernel (piko_process.cu) and the multi-scene batch kernels
+// (piko_batch.cu).
+//
+// Rasterizer, fragment shader and depth test fused into one stage (the
+// kernel fusion of Sec. 5.2.1 of the Piko paper), with the tile's depth|ID
+// buffer in shared memory (the on-chip depth buffer Sec. 5.2.4 names).
+//
+// Per tile:
+//  1. each thread takes one bin entry, re-derives the triangle from the
+//     snapped vertices, stores what shading needs (edge coordinates, 1/A and
+//     the vertex attributes) in a shared-memory record, and rasterizes it if
+//     its box inside the tile is small; larger ones go to a queue that whole
+//     warps rasterize 32 pixels at a time with a coverage ballot;
+//  2. every covered sample does a 64-bit atomic minimum on the tile's key,
+//     key = depth << 40 | triangle << slot_bits | record slot: ordered by
+//     (depth, triangle) exactly like depth << 32 | triangle, since a
+//     triangle has one record per tile;
+//  3. one thread per pixel shades the winner from its record and writes the
+//     key (as depth << 32 | triangle) and the colour, rows contiguous.
+#pragma once
+
+#include <cuda_fp16.h>
+
+#include "piko_internal.cuh"
+
+namespace piko {
+
+// What the Process stage needs of one scene.  vtx and vdot point at this
+// scene's first vertex; bin entries hold triangle indices offset by tri_base.
+struct TileScene {
+  RasterGeom g;
+  int mode, unclamped, small_px;
+  int slot_bits, nslots, rec_stride;
+  int tri_base;
+  const int* tris;
+  const int4* vtx;
+  const float* color;
+  const float* normal;
+  const float* light;
+  const float* vdot;
+  unsigned long long* key_out;
+  float4* rgba_out;
+  uint2* gnorm_out;
+  uint2* galb_out;
+};
+
+// Per-CTA shared memory of the stage.
+struct TileSmem {
+  unsigned long long* skey;  // [bin_px], all KEY_EMPTY between tiles
+  unsigned long long* sbig;  // [nt] ring of (slot << 32 | t)
+  int* srec;                 // [nslots][rec_stride]
+  unsigned* s_nbig;          // grows monotonically
+};
+
+struct TileStats {
+  unsigned long long tests, frags, shaded;
+};
+
+// record words: 0..5 X0 Y0 X1 Y1 X2 Y2 (oriented), 6 = 1/A (float), then attributes
+constexpr int R_RA = 6;
+constexpr int R_ATTR = 7;
+
+__device__ __forceinline__ int rec_attr_count(int mode, bool has_color) {
+  if (mode == PIKO_SHADE_GOURAUD) return 9;              // c0 c1 c2
+  if (mode == PIKO_SHADE_LAMBERT) return has_color ? 12 : 3;  // d0 d1 d2 (n_i . L) [+ c0 c1 c2]
+  return 18;                                             // n0 n1 n2 c0 c1 c2
+}
+
+// ---------------------------------------------------------------- raster
+template <typename I>
+struct Edges {
+  I e0, e1, e2;     // edge functions minus the fill-rule bias (covered iff all >= 0)
+  I sx0, sx1, sx2;  // steps per pixel in x
+  I sy0, sy1, sy2;  // steps per pixel in y
+  int b1, b2;       // biases of edges 1 and 2
+};
+
+template <typename I>
+__device__ __forceinline__ Edges<I> make_edges(const TriSetup& s, int px, int py) {
+  Edges<I> e;
+  const I Px = (I)256 * px + 128, Py = (I)256 * py + 128;
+  const int dx0 = s.X2 - s.X1, dy0 = s.Y2 - s.Y1;
+  const int dx1 = s.X0 - s.X2, dy1 = s.Y0 - s.Y2;
+  const int dx2 = s.X1 - s.X0, dy2 = s.Y1 - s.Y0;
+  const int b0 = 1 - top_left(dx0, dy0);
+  e.b1 = 1 - top_left(dx1, dy1);
+  e.b2 = 1 - top_left(dx2, dy2);
+  // coordinate differences are below 2^24 and fit int32
+  e.e0 = (I)dx0 * (I)((int)Py - s.Y1) - (I)dy0 * (I)((int)Px - s.X1) - b0;
+  e.e1 = (I)dx1 * (I)((int)Py - s.Y2) - (I)dy1 * (I)((int)Px - s.X2) - e.b1;
+  e.e2 = (I)dx2 * (I)((int)Py - s.Y0) - (I)dy2 * (I)((int)Px - s.X0) - e.b2;
+  e.sx0 = (I)-256 * dy0; e.sx1 = (I)-256 * dy1; e.sx2 = (I)-256 * dy2;
+  e.sy0 = (I)256 * dx0;  e.sy1 = (I)256 * dx1;  e.sy2 = (I)256 * dx2;
+  return e;
+}
+
+__device__ __forceinline__ void key_store(unsigned long long* skey, int idx, unsigned z, unsigned long long tag) {
+  const unsigned long long k = ((unsigned long long)z << 40) | tag;
+  if (k < skey[idx]) atomicMin(skey + idx, k);
+}
+
+// Triangles whose bounding box is below 2^15 in 16.8 units: A < 2^30 and
+// w1, w2 < 2^31, so the depth numerator is two 32x32->64 products.  With
+// N32 the caller has checked A * (|Z1-Z0| + |Z2-Z0| + 8) < 2^31: the
+// numerator, the quotient estimate times A and the remainder then all fit
+// in 32 bits.
+template <bool N32>
+__device__ __forceinline__ void key_min_small(unsigned long long* skey, int idx, int w1, int w2, const TriSetup& s,
+                                              float rA, unsigned long long tag) {
+  if (N32) {
+    const int A = (int)s.A;
+    const int n = w1 * (s.Z1 - s.Z0) + w2 * (s.Z2 - s.Z0);
+    int q = __float2int_rd((float)n * rA);
+    int r = n - q * A;
+    for (int it = 0; r < 0 && it < DIV_FIX_LIMIT; ++it) { --q; r += A; }
+    for (int it = 0; r >= A && it < DIV_FIX_LIMIT; ++it) { ++q; r -= A; }
+    key_store(skey, idx, (unsigned)(s.Z0 + q), tag);
+  } else {
+    const long long n = (long long)w1 * (s.Z1 - s.Z0) + (long long)w2 * (s.Z2 - s.Z0);
+    key_store(skey, idx, (unsigned)(s.Z0 + floor_div_small(n, (int)s.A, rA)), tag);
+  }
+}
+
+__device__ __forceinline__ void key_min_large(unsigned long long* skey, int idx, long long w1, long long w2,
+                                              const TriSetup& s, float rA, unsigned long long tag) {
+  key_store(skey, idx, depth_of(w1, w2, s, rA), tag);
+}
+
+// One thread walks the box of a small triangle inside the tile.  With I =
+// int the triangle's bounding box is below 2^15 in 16.8 units in both
+// directions, so every edge value inside the box is below 2^31 in magnitude
+// and int32 arithmetic is exact.
+template <typename I, bool N32>
+__device__ __forceinline__ unsigned raster_thread_body(const TriSetup& s, unsigned long long tag, int px0, int px1,
+                                                       int py0, int py1, int x0, int y0, int bshift_x,
+                                                       unsigned long long* skey) {
+  const Edges<I> e = make_edges<I>(s, px0, py0);
+  const float rA = approx_rcp((float)s.A);
+  unsigned frags = 0;
+  I r0 = e.e0, r1 = e.e1, r2 = e.e2;
+  for (int y = py0; y <= py1; ++y) {
+    I a0 = r0, a1 = r1, a2 = r2;
+    const int row = (y - y0) << bshift_x;
+    for (int x = px0; x <= px1; ++x) {
+      if ((a0 | a1 | a2) >= 0) {
+        if (sizeof(I) == 4)
+          key_min_small<N32>(skey, row + (x - x0), (int)a1 + e.b1, (int)a2 + e.b2, s, rA, tag);
+        else
+          key_min_large(skey, row + (x - x0), (long long)a1 + e.b1, (long long)a2 + e.b2, s, rA, tag);
+        ++frags;
+      }
+      a0 += e.sx0; a1 += e.sx1; a2 += e.sx2;
+    }
+    r0 += e.sy0; r1 += e.sy1; r2 += e.sy2;
+  }
+  return frags;
+}
+
+// Small boxes of small triangles (the common case) stay inline; the int64
+// form for small boxes of large triangles is a separate function so that its
+// registers do not weigh on the common path.
+__device__ __forceinline__ unsigned raster_thread32(const TriSetup& s, unsigned long long tag, int px0, int px1,
+                                                    int py0, int py1, int x0, int y0, int bshift_x,
+                                                    unsigned long long* skey) {
+  const long long dz = (long long)abs(s.Z1 - s.Z0) + abs(s.Z2 - s.Z0) + 8;
+  if (s.A * dz < (1LL << 31)) return raster_thread_body<int, true>(s, tag, px0, px1, py0, py1, x0, y0, bshift_x, skey);
+  return raster_thread_body<int, false>(s, tag, px0, px1, py0, py1, x0, y0, bshift_x, skey);
+}
+__device__ __forceinline__ unsigned raster_thread64(const TriSetup& s, unsigned long long tag, int px0, int px1,
+                                                 int py0, int py1, int x0, int y0, int bshift_x,
+                                                 unsigned long long* skey) {
+  return raster_thread_body<long long, false>(s, tag, px0, px1, py0, py1, x0, y0, bshift_x, skey);
+}
+
+// A warp covers a large triangle's box 32 pixels at a time; the ballot of
+// coverage lets the warp skip groups of pixels with nothing inside.
+__device__ __forceinline__ unsigned raster_warp(const TriSetup& s, unsigned long long tag, int px0, int px1, int py0,
+                                                int py1, int x0, int y0, int bshift_x, unsigned long long* skey,
+                                                int lane) {
+  const Edges<long long> e = make_edges<long long>(s, px0, py0);
+  const float rA = approx_rcp((float)s.A);
+  const int bw = px1 - px0 + 1, n = bw * (py1 - py0 + 1);
+  const int dy = 32 / bw, dx = 32 - dy * bw;
+  int lx = lane % bw, ly = lane / bw;
+  unsigned frags = 0;
+  for (int base = 0; base < n; base += 32) {
+    const bool in_box = base + lane < n;
+    const long long a0 = e.e0 + lx * e.sx0 + ly * e.sy0;
+    const long long a1 = e.e1 + lx * e.sx1 + ly * e.sy1;
+    const long long a2 = e.e2 + lx * e.sx2 + ly * e.sy2;
+    const bool cov = in_box && (a0 | a1 | a2) >= 0;
+    const unsigned m = __ballot_sync(FULL_MASK, cov);
+    if (m != 0u) {
+      if (cov)
+        key_min_large(skey, ((py0 + ly - y0) << bshift_x) + (px0 + lx - x0), a1 + e.b1, a2 + e.b2, s, rA, tag);
+      frags += __popc(m);
+    }
+    lx += dx; ly += dy;
+    if (lx >= bw) { lx -= bw; ++ly; }
+  }
+  return frags;
+}
+
+// ---------------------------------------------------------------- shading
+__device__ __forceinline__ uint2 pack_half4(float a, float b, float c, float d) {
+  const __half2 lo = __floats2half2_rn(a, b), hi = __floats2half2_rn(c, d);
+  uint2 r;
+  r.x = *reinterpret_cast<const unsigned*>(&lo);
+  r.y = *reinterpret_cast<const unsigned*>(&hi);
+  return r;
+}
+
+__device__ __forceinline__ void write_empty(const TileScene& p, size_t o) {
+  if (p.mode == PIKO_SHADE_GBUFFER) {
+    p.gnorm_out[o] = make_uint2(0u, 0u);
+    p.galb_out[o] = make_uint2(0u, 0u);
+  } else if (p.rgba_out) {
+    p.rgba_out[o] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// Barycentrics of pixel (x, y) from a record: exact int64 edge functions
+// times 1/A.
+__device__ __forceinline__ void rec_bary(const int* r, int x, int y, float& b0, float& b1, float& b2) {
+  const int Px = 256 * x + 128, Py = 256 * y + 128;
+  const int X0 = r[0], Y0 = r[1], X1 = r[2], Y1 = r[3], X2 = r[4], Y2 = r[5];
+  const float rA = __int_as_float(r[R_RA]);
+  // exact edge functions from 32-bit differences (each below 2^24) widened once
+  const long long w1 = (long long)(X0 - X2) * (Py - Y2) - (long long)(Y0 - Y2) * (Px - X2);
+  const long long w2 = (long long)(X1 - X0) * (Py - Y0) - (long long)(Y1 - Y0) * (Px - X0);
+  b1 = (float)w1 * rA;
+  b2 = (float)w2 * rA;
+  b0 = 1.0f - b1 - b2;
+}
+
+__device__ __forceinline__ void shade_from_record(const TileScene& p, const int* r, int x, int y, size_t o,
+                                                  float L0, float L1, float L2) {
+  float b0, b1, b2;
+  rec_bary(r, x, y, b0, b1, b2);
+  const float* a = reinterpret_cast<const float*>(r + R_ATTR);
+  if (p.mode == PIKO_SHADE_GOURAUD) {
+    if (p.rgba_out)
+      p.rgba_out[o] = make_float4(b0 * a[0] + b1 * a[3] + b2 * a[6], b0 * a[1] + b1 * a[4] + b2 * a[7],
+                                  b0 * a[2] + b1 * a[5] + b2 * a[8], 1.0f);
+    return;
+  }
+  if (p.mode == PIKO_SHADE_LAMBERT) {
+    float d = b0 * a[0] + b1 * a[1] + b2 * a[2];  // (sum b_i n_i) . L, by linearity
+    if (!p.unclamped) d = fmaxf(d, 0.0f);
+    float c0 = 0.80f, c1 = 0.75f, c2 = 0.65f;      // material of Listing 1
+    if (p.color) {
+      c0 = b0 * a[3] + b1 * a[6] + b2 * a[9];
+      c1 = b0 * a[4] + b1 * a[7] + b2 * a[10];
+      c2 = b0 * a[5] + b1 * a[8] + b2 * a[11];
+    }
+    if (p.rgba_out) p.rgba_out[o] = make_float4(c0 * d, c1 * d, c2 * d, 1.0f);
+    return;
+  }
+  const float nx = b0 * a[0] + b1 * a[3] + b2 * a[6];
+  const float ny = b0 * a[1] + b1 * a[4] + b2 * a[7];
+  const float nz = b0 * a[2] + b1 * a[5] + b2 * a[8];
+  float c0 = 0.80f, c1 = 0.75f, c2 = 0.65f;
+  if (p.color) {
+    c0 = b0 * a[9] + b1 * a[12] + b2 * a[15];
+    c1 = b0 * a[10] + b1 * a[13] + b2 * a[16];
+    c2 = b0 * a[11] + b1 * a[14] + b2 * a[17];
+  }
+  p.gnorm_out[o] = pack_half4(nx, ny, nz, 0.0f);
+  p.galb_out[o] = pack_half4(c0, c1, c2, 1.0f);
+}
+
+// Fallback for winners without a record: everything re-read from global memory.
+__device__ __forceinline__ void shade_from_global(const TileScene& p, unsigned t, int x, int y, size_t o,
+                                                  float L0, float L1, float L2) {
+  TriSetup s;
+  setup_triangle(__ldg(p.tris + 3 * (size_t)t), __ldg(p.tris + 3 * (size_t)t + 1), __ldg(p.tris + 3 * (size_t)t + 2),
+                 p.vtx, s);
+  const int Px = 256 * x + 128, Py = 256 * y + 128;
+  const long long w1 = (long long)(s.X0 - s.X2) * (Py - s.Y2) - (long long)(s.Y0 - s.Y2) * (Px - s.X2);
+  const long long w2 = (long long)(s.X1 - s.X0) * (Py - s.Y0) - (long long)(s.Y1 - s.Y0) * (Px - s.X0);
+  const float rA = approx_rcp((float)s.A);
+  const float b1 = (float)w1 * rA, b2 = (float)w2 * rA, b0 = 1.0f - b1 - b2;
+  float c0 = 0.80f, c1 = 0.75f, c2 = 0.65f;
+  if (p.color) {
+    const float* q0 = p.color + 3 * (size_t)s.v0;
+    const float* q1 = p.color + 3 * (size_t)s.v1;
+    const float* q2 = p.color + 3 * (size_t)s.v2;
+    c0 = b0 * __ldg(q0) + b1 * __ldg(q1) + b2 * __ldg(q2);
+    c1 = b0 * __ldg(q0 + 1) + b1 * __ldg(q1 + 1) + b2 * __ldg(q2 + 1);
+    c2 = b0 * __ldg(q0 + 2) + b1 * __ldg(q1 + 2) + b2 * __ldg(q2 + 2);
+  }
+  if (p.mode == PIKO_SHADE_GOURAUD) {
+    if (p.rgba_out) p.rgba_out[o] = make_float4(c0, c1, c2, 1.0f);
+    return;
+  }
+  const float* n0 = p.normal + 3 * (size_t)s.v0;
+  const float* n1 = p.normal + 3 * (size_t)s.v1;
+  const float* n2 = p.normal + 3 * (size_t)s.v2;
+  const float nx = b0 * __ldg(n0) + b1 * __ldg(n1) + b2 * __ldg(n2);
+  const float ny = b0 * __ldg(n0 + 1) + b1 * __ldg(n1 + 1) + b2 * __ldg(n2 + 1);
+  const float nz = b0 * __ldg(n0 + 2) + b1 * __ldg(n1 + 2) + b2 * __ldg(n2 + 2);
+  if (p.mode == PIKO_SHADE_GBUFFER) {
+    p.gnorm_out[o] = pack_half4(nx, ny, nz, 0.0f);
+    p.galb_out[o] = pack_half4(c0, c1, c2, 1.0f);
+    return;
+  }
+  float d = nx * L0 + ny * L1 + nz * L2;
+  if (!p.unclamped) d = fmaxf(d, 0.0f);
+  if (p.rgba_out) p.rgba_out[o] = make_float4(c0 * d, c1 * d, c2 * d, 1.0f);
+}
+
+// Fills the shared-memory record of one bin entry.
+__device__ __forceinline__ void fill_record(const TileScene& p, const TriSetup& s, int* r, float L0, float L1,
+                                            float L2) {
+  r[0] = s.X0; r[1] = s.Y0; r[2] = s.X1; r[3] = s.Y1; r[4] = s.X2; r[5] = s.Y2;
+  r[R_RA] = __float_as_int(approx_rcp((float)s.A));
+  float* a = reinterpret_cast<float*>(r + R_ATTR);
+  const int v[3] = {s.v0, s.v1, s.v2};
+  if (p.mode == PIKO_SHADE_LAMBERT) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) a[j] = __ldg(p.vdot + v[j]);
+    if (p.color) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const float* c = p.color + 3 * (size_t)v[j];
+        a[3 + 3 * j] = __ldg(c); a[4 + 3 * j] = __ldg(c + 1); a[5 + 3 * j] = __ldg(c + 2);
+      }
+    }
+    return;
+  }
+  const int coff = p.mode == PIKO_SHADE_GOURAUD ? 0 : 9;
+  if (p.mode == PIKO_SHADE_GBUFFER) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float* n = p.normal + 3 * (size_t)v[j];
+      a[3 * j] = __ldg(n); a[3 * j + 1] = __ldg(n + 1); a[3 * j + 2] = __ldg(n + 2);
+    }
+  }
+  if (p.color) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float* c = p.color + 3 * (size_t)v[j];
+      a[coff + 3 * j] = __ldg(c); a[coff + 3 * j + 1] = __ldg(c + 1); a[coff + 3 * j + 2] = __ldg(c + 2);
+    }
+  }
+}
+
+// t is the scene-local triangle index
+__device__ __forceinline__ void load_setup(const TileScene& p, unsigned t, TriSetup& s) {
+  setup_triangle(__ldg(p.tris + 3 * (size_t)t), __ldg(p.tris + 3 * (size_t)t + 1), __ldg(p.tris + 3 * (size_t)t + 2),
+                 p.vtx, s);
+}
+
+
+// Process one tile: tile is the scene-local tile index, [beg, end) its range
+// in bin_tris.  Called by every thread of the CTA (nt threads, a power of
+// two); contains CTA barriers.  big_base tracks the large-triangle ring.
+__device__ __forceinline__ void process_tile(const TileScene& p, int tile, unsigned beg, unsigned end,
+                                             const unsigned* __restrict__ bin_tris, const TileSmem& sm,
+                                             unsigned& big_base, bool stats, TileStats& st, float L0, float L1,
+                                             float L2) {
+  const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+  const int bin_w = 1 << p.g.bshift_x, bin_h = 1 << p.g.bshift_y;
+  const int bin_px = bin_w * bin_h;
+  const unsigned no_slot = (1u << p.slot_bits) - 1u;
+  const int tx = tile % p.g.nbx, ty = tile / p.g.nbx;
+  const int x0 = tx << p.g.bshift_x, y0 = ty << p.g.bshift_y;
+  const int x1 = min(x0 + bin_w, p.g.W) - 1, y1 = min(y0 + bin_h, p.g.H) - 1;
+  unsigned long long* skey = sm.skey;
+  for (unsigned c = beg; c < end; c += nt) {
+    const unsigned i = c + tid;
+    bool pushed = false;
+    if (i < end) {
+      const unsigned t = __ldg(bin_tris + i) - (unsigned)p.tri_base;
+      const unsigned slot = (i - beg) < (unsigned)p.nslots ? (i - beg) : no_slot;
+      TriSetup s;
+      load_setup(p, t, s);
+      if (slot != no_slot) fill_record(p, s, sm.srec + slot * p.rec_stride, L0, L1, L2);
+      const int minX = min(s.X0, min(s.X1, s.X2)), maxX = max(s.X0, max(s.X1, s.X2));
+      const int minY = min(s.Y0, min(s.Y1, s.Y2)), maxY = max(s.Y0, max(s.Y1, s.Y2));
+      int px0, px1, py0, py1;
+      centre_range(minX, maxX, x0, x1, px0, px1);
+      centre_range(minY, maxY, y0, y1, py0, py1);
+      if (px0 <= px1 && py0 <= py1) {
+        const int npx = (px1 - px0 + 1) * (py1 - py0 + 1);
+        const unsigned long long tag = ((unsigned long long)t << p.slot_bits) | slot;
+        if (stats) st.tests += npx;
+        if (npx <= p.small_px) {
+          unsigned f;
+          if (maxX - minX < 32768 && maxY - minY < 32768)
+            f = raster_thread32(s, tag, px0, px1, py0, py1, x0, y0, p.g.bshift_x, skey);
+          else
+            f = raster_thread64(s, tag, px0, px1, py0, py1, x0, y0, p.g.bshift_x, skey);
+          if (stats) st.frags += f;
+        } else {
+          // the ring counter only ever grows; with nt a power of two the ring
+          // index stays consistent across its 2^32 wrap
+          const unsigned q = atomicAdd(sm.s_nbig, 1u);
+          sm.sbig[q & (nt - 1)] = ((unsigned long long)slot << 32) | t;
+          pushed = true;
+        }
+      }
+    }
+    // every thread gets the same count of queued large triangles
+    const unsigned nbig = (unsigned)__syncthreads_count(pushed);
+    if (nbig != 0u) {
+      for (unsigned q = warp; q < nbig; q += nwarps) {
+        const unsigned long long e = sm.sbig[(big_base + q) & (nt - 1)];
+        const unsigned t = (unsigned)e, slot = (unsigned)(e >> 32);
+        TriSetup s;
+        load_setup(p, t, s);
+        int px0, px1, py0, py1;
+        centre_range(min(s.X0, min(s.X1, s.X2)), max(s.X0, max(s.X1, s.X2)), x0, x1, px0, px1);
+        centre_range(min(s.Y0, min(s.Y1, s.Y2)), max(s.Y0, max(s.Y1, s.Y2)), y0, y1, py0, py1);
+        const unsigned f = raster_warp(s, ((unsigned long long)t << p.slot_bits) | slot, px0, px1, py0, py1, x0, y0,
+                                       p.g.bshift_x, skey, lane);
+        if (stats && lane == 0) st.frags += f;
+      }
+      big_base += nbig;
+      __syncthreads();
+    }
+  }
+  // shade, write, and leave the key tile cleared for the next tile
+  for (int i = tid; i < bin_px; i += nt) {
+    const unsigned long long k = skey[i];
+    skey[i] = KEY_EMPTY;
+    const int x = x0 + (i & (bin_w - 1)), y = y0 + (i >> p.g.bshift_x);
+    if (x > x1 || y > y1) continue;
+    const size_t o = (size_t)y * p.g.W + x;
+    if (k == KEY_EMPTY) {
+      p.key_out[o] = KEY_EMPTY;
+      write_empty(p, o);
+      continue;
+    }
+    const unsigned z = (unsigned)(k >> 40);
+    // the triangle field sits between the slot and the depth: 40 - slot_bits wide
+    const unsigned t = (unsigned)((k >> p.slot_bits) & ((1ull << (40 - p.slot_bits)) - 1ull));
+    const unsigned slot = (unsigned)(k & no_slot);
+    p.key_out[o] = ((unsigned long long)z << 32) | t;
+    if (stats) ++st.shaded;
+    if (slot != no_slot)
+      shade_from_record(p, sm.srec + slot * p.rec_stride, x, y, o, L0, L1, L2);
+    else
+      shade_from_global(p, t, x, y, o, L0, L1, L2);
+  }
+  __syncthreads();
+}
+
+// Record layout of a scene: slot bits below the triangle index (2^id_bits > T,
+// so no key equals the all-ones empty key), records per tile and words per
+// record (odd, so that distinct records fall in distinct banks).
+inline void tile_layout(int num_triangles, int bin_px, int mode, bool has_color, int max_slots, int& slot_bits,
+                        int& nslots, int& rec_stride) {
+  int id_bits = 1;
+  while (id_bits < 32 && (1LL << id_bits) <= (long long)num_triangles) ++id_bits;
+  slot_bits = 40 - id_bits < 16 ? 40 - id_bits : 16;
+  int want = bin_px <= 256 ? 255 : max_slots;
+  const int cap = (1 << slot_bits) - 1;
+  nslots = want < cap ? want : cap;
+  const int attrs = mode == PIKO_SHADE_GOURAUD ? 9 : (mode == PIKO_SHADE_LAMBERT ? (has_color ? 12 : 3) : 18);
+  rec_stride = R_ATTR + attrs;
+  if ((rec_stride & 1) == 0) ++rec_stride;
+}
+
+inline size_t tile_smem_bytes(int bin_px, int threads, int nslots, int rec_stride) {
+  return (size_t)bin_px * 8 + (size_t)threads * 8 + (size_t)nslots * rec_stride * 4;
+}
+
+}  // namespace piko

@@ -210,6 +210,44 @@ class Rasterizer:
                                                         _ptr(out), self._stream(stream)))
         return out
 
+    # -------------------------------------------------------------- batches
+    def forward_batch(self, scenes, fbs=None, bin_sizes=None, schedules=None, stream=None):
+        """All scenes in one pass (one persistent launch by default).
+        bin_sizes: per-scene (w, h) pairs or None; schedules: per-scene names /
+        PIKO_SCHED_* values or None.  Returns the list of framebuffers."""
+        n = len(scenes)
+        if fbs is None:
+            fbs = [Framebuffer.allocate(s.width, s.height, s.shade_mode, s.pos.device) for s in scenes]
+        cs = (L.PikoScene * n)(*[s.c_struct() for s in scenes])
+        cf = (L.PikoFramebuffer * n)(*[f.c_struct() for f in fbs])
+        bs = None
+        if bin_sizes is not None:
+            flat = [int(v) for wh in bin_sizes for v in wh]
+            bs = (C.c_int32 * (2 * n))(*flat)
+        sc = None
+        if schedules is not None:
+            sc = (C.c_int32 * n)(*[_SCHEDULES[x] if isinstance(x, str) else int(x) for x in schedules])
+        self._check(self.lib.piko_raster_forward_batch(self._h, cs, n, cf, bs, sc, self._stream(stream)))
+        self._batch_keepalive = (scenes, fbs)
+        return fbs
+
+    def backward_batch(self, scenes, fbs, dl_drgba, dcolor=None, dnormal=None, dlight=None, stream=None):
+        """Gradients for the scenes of the last forward_batch (lists of tensors
+        per scene; entries may be None)."""
+        n = len(scenes)
+        cs = (L.PikoScene * n)(*[s.c_struct() for s in scenes])
+        cf = (L.PikoFramebuffer * n)(*[f.c_struct() for f in fbs])
+
+        def ptrs(lst):
+            if lst is None:
+                return None
+            return (C.c_void_p * n)(*[None if t is None else t.data_ptr() for t in lst])
+
+        gl = [g.contiguous() for g in dl_drgba]
+        self._check(self.lib.piko_raster_backward_batch(self._h, cs, n, cf, ptrs(gl), ptrs(dcolor), ptrs(dnormal),
+                                                        ptrs(dlight), self._stream(stream)))
+        return dcolor, dnormal, dlight
+
     def backward(self, scene: DeviceScene, fb: Framebuffer, dl_drgba: torch.Tensor, dcolor=None, dnormal=None,
                  dlight=None, stream=None):
         """Accumulates gradients into the given float32 tensors (any may be None)."""

@@ -388,3 +388,92 @@ def test_sphere_views_backward_accumulates_over_views():
     _grad_check(color.grad.cpu().numpy(), dc_ref)
     _grad_check(normal.grad.cpu().numpy(), dn_ref)
     _grad_check(light.grad.cpu().numpy(), dl_ref)
+
+
+# --------------------------------------------------------------- batches
+def _batch_scenes(n, seed=0, small=True):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        side = int(rng.choice([64, 96, 128, 192])) if small else int(rng.choice(np.arange(256, 1025, 64)))
+        T = int(rng.integers(50, 2000))
+        kind = k % 3
+        if kind == 0:
+            s = S.random_triangles(side, side, T, float(rng.choice([3.0, 10.0, 40.0])), seed=int(rng.integers(1 << 30)),
+                                   shade_mode=S.SHADE_GOURAUD)
+        elif kind == 1:
+            q = max(2, int(np.sqrt(T / 2)))
+            s = S.heightfield(side, side, q, q, seed=int(rng.integers(1 << 30)), with_color=True)
+        else:
+            s = S.random_triangles(side, side + 32, T, 15.0, seed=int(rng.integers(1 << 30)),
+                                   shade_mode=S.SHADE_LAMBERT, with_normals=True)
+        out.append(s)
+    return out
+
+
+@pytest.mark.parametrize("launch", [0, 1])
+def test_forward_batch_matches_oracle_and_single_scenes(launch):
+    torch = _torch()
+    from paper_1404_6293_gb300 import _lib as L
+    from paper_1404_6293_gb300.raster import DeviceScene, Rasterizer
+    scenes = _batch_scenes(12, seed=launch)
+    bins = [(8, 8), (16, 16), (32, 32), (64, 64), (8, 32), (16, 64)] * 2
+    sched = ["static", "dynamic"] * 6
+    r = Rasterizer(64, 64, 16, 16)
+    r.set_option(L.PIKO_OPT_BATCH_LAUNCH, launch)
+    ds = [DeviceScene.from_host(s) for s in scenes]
+    for rep in range(2):  # the second call reuses the zeroed counts and scan states
+        fbs = r.forward_batch(ds, bin_sizes=bins, schedules=sched)
+        torch.cuda.synchronize()
+        assert r.status()[0] == 0
+        for i, s in enumerate(scenes):
+            ref, _ = oracle.raster_bbox(s)
+            assert_keys_equal(fbs[i].key_numpy(), ref, f"batch scene {i} rep {rep}")
+            assert np.abs(fbs[i].rgba.cpu().numpy() - oracle.shade(s, ref)).max() <= RGB_TOL
+
+
+def test_forward_batch_gbuffer_and_empty_scenes():
+    torch = _torch()
+    from paper_1404_6293_gb300.raster import DeviceScene, Rasterizer
+    a = S.power_law_triangles(160, 96, 3000, seed=3)
+    b = S.Scene(40, 30, np.zeros((0, 4), np.float32), np.zeros((0, 3), np.int32), color=np.zeros((0, 3), np.float32))
+    c = S.random_triangles(50, 70, 300, 8.0, seed=4)
+    r = Rasterizer(64, 64)
+    fbs = r.forward_batch([DeviceScene.from_host(x) for x in (a, b, c)], schedules=["dynamic", "static", "dynamic"])
+    torch.cuda.synchronize()
+    assert r.status()[0] == 0
+    ref_a, _ = oracle.raster_bbox(a)
+    assert_keys_equal(fbs[0].key_numpy(), ref_a, "gbuffer scene")
+    gn, ga = oracle.shade(a, ref_a)
+    assert_half_close(fbs[0].gbuf_normal.cpu().numpy(), gn)
+    assert (fbs[1].key_numpy() == EMPTY).all()
+    ref_c, _ = oracle.raster_bbox(c)
+    assert_keys_equal(fbs[2].key_numpy(), ref_c, "third scene")
+
+
+def test_backward_batch_matches_single_scene_backward():
+    torch = _torch()
+    from paper_1404_6293_gb300.raster import DeviceScene, Rasterizer
+    scenes = [s for s in _batch_scenes(6, seed=7) if s.shade_mode != S.SHADE_GBUFFER]
+    ds = [DeviceScene.from_host(s) for s in scenes]
+    r = Rasterizer(64, 64)
+    fbs = r.forward_batch(ds)
+    gs, dcs, dns, dls = [], [], [], []
+    for i, s in enumerate(scenes):
+        tgt = torch.from_numpy(S.target_image(s.width, s.height, seed=i)[0]).cuda()
+        g = 2.0 * (fbs[i].rgba - tgt)
+        g[..., 3] = 0
+        gs.append(g.contiguous())
+        dcs.append(torch.zeros((s.num_vertices, 3), device="cuda"))
+        dns.append(torch.zeros((s.num_vertices, 3), device="cuda") if s.normal is not None else None)
+        dls.append(torch.zeros(3, device="cuda"))
+    r.backward_batch(ds, fbs, gs, dcs, dns, dls)
+    torch.cuda.synchronize()
+    for i, s in enumerate(scenes):
+        ref_key, _ = oracle.raster_bbox(s)
+        g = gs[i].cpu().numpy().astype(np.float64)
+        dc, dn, dl = oracle.backward(s, ref_key, g)
+        _grad_check(dcs[i].cpu().numpy(), dc)
+        if s.shade_mode == S.SHADE_LAMBERT:
+            _grad_check(dns[i].cpu().numpy(), dn)
+            _grad_check(dls[i].cpu().numpy(), dl)

@@ -31,7 +31,8 @@ sys.path.insert(0, ROOT)
 METRIC = "Mtris/s + shaded Gfrag/s on 1 GB300 (plain vs batched), bit-exact depth/ID"
 UNIT = "Mtris/s"
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "process_heightfield1080p_traffic.json")
-KERNEL_SOURCES = ["paper_1404_6293_gb300/csrc/piko_process.cu", "paper_1404_6293_gb300/csrc/piko_internal.cuh"]
+KERNEL_SOURCES = ["paper_1404_6293_gb300/csrc/piko_process.cu", "paper_1404_6293_gb300/csrc/piko_tile.cuh",
+                  "paper_1404_6293_gb300/csrc/piko_internal.cuh"]
 
 # Per-unit algorithmic costs of the Process kernel (thread operations), fixed
 # from the minimal operation sequence of the definition: see the design doc.
@@ -598,11 +599,16 @@ def run_batch(args, clocks) -> dict:
 
     # ---- batched: autotuned knobs, one persistent launch per pass, graph-captured
     t0 = time.perf_counter()
-    tuner = Autotuner()
-    bins, scheds = tuner.choose_all(ds)
+    if args.batch_bins:
+        bins, scheds = [(args.batch_bins, args.batch_bins)] * n, [args.batch_schedule] * n
+        tune_report = {"choice": "given", "classes": 0, "per_class_ms": None, "best_uniform_ms": None, "uniform": []}
+    else:
+        tuner = Autotuner()
+        bins, scheds, tune_report = tuner.tune_batch(ds)
+        tuner.close()
     tune_s = time.perf_counter() - t0
-    tuner.close()
     rb = Rasterizer(64, 64, 16, 16)
+    rb.set_option(L.PIKO_OPT_BATCH_LAUNCH, 1 if args.batch_launch == "per-phase" else 0)
     key_b, rgba_b, fbs_b = make_fbs()
     dc_b, dn_b, dl_b, dcv_b, dnv_b, dlv_b = make_grads()
     rb.forward_batch(ds, fbs_b, bins, scheds)
@@ -656,14 +662,21 @@ def run_batch(args, clocks) -> dict:
             "plain": {"value": T / (ms_plain * 1e-3) / 1e6, "ms_per_step": ms_plain,
                       "how": "per-scene piko_raster_forward then piko_raster_backward, 16x16 static"},
             "batched": {"value": T / (ms_batch * 1e-3) / 1e6, "ms_per_step": ms_batch,
-                        "how": "forward_batch (one persistent cooperative launch) + loss gradient + "
+                        "how": ("forward_batch (one persistent cooperative launch)" if args.batch_launch == "persistent"
+                                else "forward_batch (one launch per phase)") + " + loss gradient + "
                                "backward_batch, replayed from one CUDA graph",
                         "autotune_s": tune_s, "static_scenes": n_static,
-                        "bins_used": sorted(set(f"{a}x{b}" for a, b in bins))},
+                        "bins_used": sorted(set(f"{a}x{b}" for a, b in bins)),
+                        "autotune": {"choice": tune_report["choice"], "classes": tune_report["classes"],
+                                     "per_class_forward_ms": tune_report["per_class_ms"],
+                                     "best_uniform_forward_ms": tune_report["best_uniform_ms"],
+                                     "uniform_forward_ms": {f"{u['bin'][0]}x{u['bin'][1]} {u['schedule']}": u["ms"]
+                                                            for u in tune_report["uniform"]}}},
             "speedup_batched_over_plain": ms_plain / ms_batch,
             "parity": {"keys_bit_identical_plain_vs_batched": same_keys, "grad_max_abs_diff": gdiff,
                        "grad_scale": gscale},
-            "clocks": clk, "gpu_launches": 2 * args.steps}
+            "clocks": clk, "gpu_launches": (2 if args.batch_launch == "persistent" else 6) * args.steps,
+            "gpu_launches_plain": 7 * n * args.steps}
 
 
 def main():
@@ -676,6 +689,11 @@ def main():
     ap.add_argument("--schedule", default="static", choices=["static", "dynamic", "hardware"])
     ap.add_argument("--threads", type=int, default=0, help="Process CTA size (0: library default)")
     ap.add_argument("--batch-scenes", type=int, default=256)
+    ap.add_argument("--batch-bins", type=int, default=0, help="batch workload: one square bin size for all scenes "
+                    "instead of the autotuner's choice (0: autotune)")
+    ap.add_argument("--batch-schedule", default="dynamic", choices=["static", "dynamic"])
+    ap.add_argument("--batch-launch", default="persistent", choices=["persistent", "per-phase"],
+                    help="batch workload: one cooperative launch, or one launch per phase (for launch lists)")
     ap.add_argument("--workload", default="heightfield", choices=["heightfield", "deferred", "sphere", "batch"],
                     help="heightfield: the headline line; the others measure further rows of the path")
     ap.add_argument("--e2e-steps", type=int, default=50)

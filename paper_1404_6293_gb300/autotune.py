@@ -8,6 +8,13 @@ forward pass under every (bin size, schedule) candidate with CUDA events and
 keeps the fastest.  Results are cached by workload features (resolution,
 triangle count, coverage density, shading mode) so that similar scenes share
 one measurement; the cache can be saved to and loaded from JSON.
+
+A choice that is best for a scene rendered alone need not be best inside a
+batch, where all scenes share one persistent launch (there is no per-scene
+launch or grid-size effect).  ``tune_batch`` therefore measures inside the
+batched pass itself: every workload class is timed as a sub-batch under each
+candidate, and the assembled per-class choice is kept only if the whole batch
+then beats the best uniform setting.
 """
 from __future__ import annotations
 
@@ -91,6 +98,54 @@ class Autotuner:
         """Per-scene (bin sizes, schedules) lists for forward_batch."""
         picks = [self.choose(s) for s in scenes]
         return [p[0] for p in picks], [p[1] for p in picks]
+
+    def _time_batch(self, r: Rasterizer, scenes: List[DeviceScene], bins, scheds, fbs=None) -> float:
+        fbs = r.forward_batch(scenes, fbs, bins, scheds)  # sizes the bin lists
+        r.status()
+        times: List[float] = []
+        for _ in range(self.reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            r.forward_batch(scenes, fbs, bins, scheds)
+            b.record()
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        times.sort()
+        return times[len(times) // 2]
+
+    def tune_batch(self, scenes: List[DeviceScene]):
+        """Per-scene (bin sizes, schedules) for forward_batch, measured in the
+        batched pass.  Returns (bins, schedules, report)."""
+        n = len(scenes)
+        cands = [((bw, bh), sc) for bw, bh in self.bins for sc in self.schedules]
+        r = Rasterizer(64, 64)
+        try:
+            uniform = []
+            for wh, sc in cands:
+                uniform.append((self._time_batch(r, scenes, [wh] * n, [sc] * n), wh, sc))
+            uniform.sort(key=lambda u: u[0])
+            best_ms, best_wh, best_sc = uniform[0]
+            classes: Dict[str, List[int]] = {}
+            for i, s in enumerate(scenes):
+                classes.setdefault(features(s), []).append(i)
+            pick: Dict[str, Tuple[Tuple[int, int], str]] = {}
+            for key, idx in classes.items():
+                sub = [scenes[i] for i in idx]
+                trial = [(self._time_batch(r, sub, [wh] * len(sub), [sc] * len(sub)), wh, sc) for wh, sc in cands]
+                trial.sort(key=lambda u: u[0])
+                pick[key] = (trial[0][1], trial[0][2])
+            bins = [pick[features(s)][0] for s in scenes]
+            scheds = [pick[features(s)][1] for s in scenes]
+            mixed_ms = self._time_batch(r, scenes, bins, scheds)
+            report = {"uniform": [{"bin": list(u[1]), "schedule": u[2], "ms": u[0]} for u in uniform],
+                      "classes": len(classes), "per_class_ms": mixed_ms, "best_uniform_ms": best_ms}
+            if mixed_ms < best_ms:
+                report["choice"] = "per_class"
+                return bins, scheds, report
+            report["choice"] = "uniform"
+            return [best_wh] * n, [best_sc] * n, report
+        finally:
+            r.close()
 
     def save(self, path: Optional[str] = None):
         path = path or self.cache_path

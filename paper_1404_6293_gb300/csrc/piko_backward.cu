@@ -1,21 +1,38 @@
-// piko_backward.cu -- attribute gradients through the shading of the forward pass.
-//
-// Visibility is held fixed by the forward key buffer, so coverage stays exact
-// integer arithmetic and only the fragment shader is differentiated: for the
-// Lambert shader of Listing 1 (rgb = albedo * s, s = max(0, n . L),
-// n = sum b_i n_i, albedo = sum b_i c_i) and for Gouraud (rgb = sum b_i c_i).
-// Per pixel, with g = dLoss/drgb:
-//   dL/dc_i += s * b_i * g        (Gouraud: b_i * g)
-//   dL/dn_i += (g . albedo) b_i L   when s > 0 (or unclamped)
-//   dL/dL   += (g . albedo) n
-// Lanes of a warp whose pixels share a winning triangle are summed in shared
-// memory and one lane issues the atomics for the group; the light gradient
-// is reduced over the whole CTA before its single atomic.
-#include "piko_internal.cuh"
+// piko_backward.cu -- attribute gradients of one scene through the shading of
+// the forward pass: the per-tile form (piko_bwd_tile.cuh) and a per-pixel
+// form for scenes of tiny triangles.
+#include "piko_bwd_tile.cuh"
 
 namespace piko {
 
 struct BackwardParams {
+  BwdScene sc;
+  int ntx, ntiles;
+};
+
+__global__ void __launch_bounds__(BWD_THREADS, 4) k_backward(BackwardParams p) {
+  extern __shared__ __align__(16) unsigned char bwd_smem_raw[];
+  BwdSmem& sm = *reinterpret_cast<BwdSmem*>(bwd_smem_raw);
+  float L0 = 0.f, L1 = 0.f, L2 = 0.f;
+  if (p.sc.mode == PIKO_SHADE_LAMBERT) {
+    L0 = __ldg(p.sc.light); L1 = __ldg(p.sc.light + 1); L2 = __ldg(p.sc.light + 2);
+  }
+  float gl0 = 0.f, gl1 = 0.f, gl2 = 0.f;
+  bwd_clear(sm);
+  __syncthreads();
+  for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
+    const int ty = tile / p.ntx, tx = tile - ty * p.ntx;
+    backward_tile(p.sc, tx * BWD_TILE, ty * BWD_TILE, sm, L0, L1, L2, gl0, gl1, gl2);
+  }
+  if (p.sc.dlight && p.sc.mode == PIKO_SHADE_LAMBERT) bwd_flush_light(sm, p.sc.dlight, gl0, gl1, gl2);
+}
+
+// Per-pixel form, for scenes of tiny triangles (a tile would hold nearly as
+// many triangles as pixels, so the tile form's shared table buys nothing):
+// each warp takes 32 consecutive pixels; lanes whose pixels share a winning
+// triangle are summed in shared memory and one lane issues the atomics for
+// the group; the light gradient is reduced over the whole CTA.
+struct PixelBwdParams {
   int W, H, mode, unclamped;
   int T, V;
   const int* tris;
@@ -30,10 +47,8 @@ struct BackwardParams {
   float* dlight;
 };
 
-constexpr int BWD_THREADS = 256;
-constexpr int BWD_VALS = 18;  // per pixel: 3 vertices x (3 colour + 3 normal)
 
-__global__ void __launch_bounds__(BWD_THREADS) k_backward(BackwardParams p) {
+__global__ void __launch_bounds__(BWD_THREADS) k_backward_pixel(PixelBwdParams p) {
   __shared__ float sval[BWD_THREADS / 32][BWD_VALS][32];
   __shared__ float sred[BWD_THREADS / 32][3];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -160,6 +175,27 @@ __global__ void __launch_bounds__(BWD_THREADS) k_backward(BackwardParams p) {
   }
 }
 
+// Blocks of the single-scene backward kernel: as many as fit on the device
+// at once (the shared-memory opt-in is per device, so it is cached per device).
+int backward_grid(int tiles, int num_sms) {
+  static int per_sm_of[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int& per_sm = per_sm_of[dev & 63];
+  if (per_sm == 0) {
+    int v = 0;
+    if (cudaFuncSetAttribute(k_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BwdSmem)) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_backward, BWD_THREADS, sizeof(BwdSmem)) != cudaSuccess ||
+        v < 1)
+      v = 1;
+    per_sm = v;
+  }
+  long long blocks = (long long)per_sm * num_sms;
+  if (blocks > tiles) blocks = tiles;
+  return blocks < 1 ? 1 : (int)blocks;
+}
+
 }  // namespace piko
 
 using namespace piko;
@@ -169,15 +205,29 @@ int piko_backward_launch(int W, int H, int mode, int unclamped, int T, int V, co
                          const float* normal, const float* light, const unsigned long long* key,
                          const float* dl_drgba, float* dcolor, float* dnormal, float* dlight, int num_sms,
                          cudaStream_t s) {
-  BackwardParams p;
-  p.W = W; p.H = H; p.mode = mode; p.unclamped = unclamped; p.T = T; p.V = V;
-  p.tris = tris; p.vtx = vtx; p.color = color; p.normal = normal; p.light = light;
-  p.key = key; p.dl_drgba = reinterpret_cast<const float4*>(dl_drgba);
-  p.dcolor = dcolor; p.dnormal = dnormal; p.dlight = dlight;
   const long long npix = (long long)W * H;
-  long long blocks = (npix + BWD_THREADS - 1) / BWD_THREADS;
-  if (blocks > (long long)num_sms * 4) blocks = (long long)num_sms * 4;
-  if (blocks < 1) blocks = 1;
-  k_backward<<<(int)blocks, BWD_THREADS, 0, s>>>(p);
+  if (4LL * T > npix) {
+    // more than one triangle per four pixels: triangles of a few pixels
+    PixelBwdParams p;
+    p.W = W; p.H = H; p.mode = mode; p.unclamped = unclamped; p.T = T; p.V = V;
+    p.tris = tris; p.vtx = vtx; p.color = color; p.normal = normal; p.light = light;
+    p.key = key; p.dl_drgba = reinterpret_cast<const float4*>(dl_drgba);
+    p.dcolor = dcolor; p.dnormal = dnormal; p.dlight = dlight;
+    long long blocks = (npix + BWD_THREADS - 1) / BWD_THREADS;
+    if (blocks > (long long)num_sms * 4) blocks = (long long)num_sms * 4;
+    if (blocks < 1) blocks = 1;
+    k_backward_pixel<<<(int)blocks, BWD_THREADS, 0, s>>>(p);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+  }
+  BackwardParams p;
+  BwdScene& c = p.sc;
+  c.W = W; c.H = H; c.mode = mode; c.unclamped = unclamped; c.T = T; c.V = V;
+  c.tris = tris; c.vtx = vtx; c.color = color; c.normal = normal; c.light = light;
+  c.key = key; c.dl = reinterpret_cast<const float4*>(dl_drgba);
+  c.dcolor = dcolor; c.dnormal = dnormal; c.dlight = dlight;
+  p.ntx = (W + BWD_TILE - 1) / BWD_TILE;
+  p.ntiles = p.ntx * ((H + BWD_TILE - 1) / BWD_TILE);
+  const int blocks = backward_grid(p.ntiles, num_sms);
+  k_backward<<<blocks, BWD_THREADS, sizeof(BwdSmem), s>>>(p);
   return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }

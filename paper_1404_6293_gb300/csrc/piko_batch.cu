@@ -18,6 +18,7 @@
 
 #include "piko_scan.cuh"
 #include "piko_tile.cuh"
+#include "piko_bwd_tile.cuh"
 
 namespace piko {
 
@@ -60,8 +61,8 @@ struct BatchParams {
   const int* bin_prefix;
   const int* stat_prefix;  // tiles of static scenes
   const int* dyn_prefix;   // tiles of dynamic scenes
-  const int* pix_prefix;
-  int total_v, total_t, total_bins, total_static, total_dyn, total_pix;
+  const int* btile_prefix;  // 16 x 16 backward tiles
+  int total_v, total_t, total_bins, total_static, total_dyn, total_btiles;
   int4* vtx;
   float* vdot;
   BinRect* rect;
@@ -434,133 +435,43 @@ __global__ void __maxnreg__(PIKO_BATCH_MAXNREG) k_batch_forward(BatchParams b) {
 }
 
 // ------------------------------------------------------------------ backward
-constexpr int BWD_VALS = 18;
-
+// 16 x 16 tiles of every scene, dealt round robin; each tile's gradients are
+// accumulated as in the single-scene backward.
 struct BatchBwdParams {
   int n;
   const BatchScene* sc;
-  const int* pix_prefix;
-  const int* tri_prefix;
-  int total_pix;
+  const int* btile_prefix;  // [n+1] backward tiles per scene
+  int total_btiles;
   const int4* vtx;
 };
 
-__global__ void __launch_bounds__(256) k_batch_backward(BatchBwdParams b) {
-  __shared__ float sval[8][BWD_VALS + 3][32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned lt_mask = (1u << lane) - 1u;
-  const int stride = gridDim.x * blockDim.x;
-  for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < b.total_pix; base += stride) {
-    const int i = base + lane;
-    int s = 0;
-    bool hit = false;
-    unsigned gid = 0xFFFFFFFFu;  // batch-wide triangle id of the winner
-    float v[BWD_VALS + 3];
-#pragma unroll
-    for (int q = 0; q < BWD_VALS + 3; ++q) v[q] = 0.f;
-    int vid[3] = {0, 0, 0};
-    if (i < b.total_pix) {
-      s = find_scene(b.pix_prefix, b.n, i);
-      const BatchScene& d = b.sc[s];
-      const int li = i - d.pix_base;
-      const unsigned long long k = __ldg(d.key_out + li);
-      const unsigned t = (unsigned)(k & 0xFFFFFFFFu);
-      if (k != KEY_EMPTY && t < (unsigned)d.T && d.dl != nullptr && d.mode != PIKO_SHADE_GBUFFER) {
-        const int ia = __ldg(d.tris + 3 * (size_t)t), ib = __ldg(d.tris + 3 * (size_t)t + 1),
-                  ic = __ldg(d.tris + 3 * (size_t)t + 2);
-        TriSetup ts;
-        hit = ia >= 0 && ia < d.V && ib >= 0 && ib < d.V && ic >= 0 && ic < d.V &&
-              setup_triangle(ia, ib, ic, b.vtx + d.vtx_base, ts);
-        if (hit) {
-          gid = (unsigned)d.tri_base + t;
-          vid[0] = ts.v0; vid[1] = ts.v1; vid[2] = ts.v2;
-          const int y = li / d.g.W, x = li - y * d.g.W;
-          const int Px = 256 * x + 128, Py = 256 * y + 128;
-          const long long w1 = (long long)(ts.X0 - ts.X2) * (Py - ts.Y2) - (long long)(ts.Y0 - ts.Y2) * (Px - ts.X2);
-          const long long w2 = (long long)(ts.X1 - ts.X0) * (Py - ts.Y0) - (long long)(ts.Y1 - ts.Y0) * (Px - ts.X0);
-          const float fA = (float)ts.A;
-          const float b1 = __fdiv_rn((float)w1, fA), b2 = __fdiv_rn((float)w2, fA);
-          const long long w0 = ts.A - w1 - w2;
-          const float bb[3] = {__fdiv_rn((float)w0, fA), b1, b2};
-          const float4 g = __ldg(d.dl + li);
-          if (d.mode == PIKO_SHADE_GOURAUD) {
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-              v[6 * j] = g.x * bb[j]; v[6 * j + 1] = g.y * bb[j]; v[6 * j + 2] = g.z * bb[j];
-            }
-          } else {
-            float a0 = 0.80f, a1 = 0.75f, a2 = 0.65f;
-            if (d.color) {
-              a0 = a1 = a2 = 0.f;
-#pragma unroll
-              for (int j = 0; j < 3; ++j) {
-                const float* c = d.color + 3 * (size_t)vid[j];
-                a0 += bb[j] * __ldg(c); a1 += bb[j] * __ldg(c + 1); a2 += bb[j] * __ldg(c + 2);
-              }
-            }
-            float n0 = 0.f, n1 = 0.f, n2 = 0.f;
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-              const float* nn = d.normal + 3 * (size_t)vid[j];
-              n0 += bb[j] * __ldg(nn); n1 += bb[j] * __ldg(nn + 1); n2 += bb[j] * __ldg(nn + 2);
-            }
-            const float L0 = __ldg(d.light), L1 = __ldg(d.light + 1), L2 = __ldg(d.light + 2);
-            const float dd = n0 * L0 + n1 * L1 + n2 * L2;
-            const bool active = dd > 0.f;
-            const float sh = fmaxf(dd, 0.f);
-            const float G = active ? (g.x * a0 + g.y * a1 + g.z * a2) : 0.f;
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-              if (d.color) {
-                v[6 * j] = g.x * sh * bb[j]; v[6 * j + 1] = g.y * sh * bb[j]; v[6 * j + 2] = g.z * sh * bb[j];
-              }
-              v[6 * j + 3] = G * bb[j] * L0; v[6 * j + 4] = G * bb[j] * L1; v[6 * j + 5] = G * bb[j] * L2;
-            }
-            v[18] = G * n0; v[19] = G * n1; v[20] = G * n2;
-          }
-        }
-      }
+__global__ void __launch_bounds__(BWD_THREADS, 4) k_batch_backward(BatchBwdParams b) {
+  extern __shared__ __align__(16) unsigned char bwd_smem_raw[];
+  BwdSmem& sm = *reinterpret_cast<BwdSmem*>(bwd_smem_raw);
+  __shared__ int s_scene;
+  float gl0 = 0.f, gl1 = 0.f, gl2 = 0.f;
+  bwd_clear(sm);
+  __syncthreads();
+  for (int i = blockIdx.x; i < b.total_btiles; i += gridDim.x) {
+    if (threadIdx.x == 0) s_scene = find_scene(b.btile_prefix, b.n, i);
+    __syncthreads();
+    const int s = s_scene;
+    __syncthreads();  // s_scene is rewritten for the next tile
+    const BatchScene& d = b.sc[s];
+    if (d.dl == nullptr || d.mode == PIKO_SHADE_GBUFFER) continue;  // the same for the whole CTA
+    BwdScene c;
+    c.W = d.g.W; c.H = d.g.H; c.mode = d.mode; c.unclamped = 0; c.T = d.T; c.V = d.V;
+    c.tris = d.tris; c.vtx = b.vtx + d.vtx_base; c.color = d.color; c.normal = d.normal; c.light = d.light;
+    c.key = d.key_out; c.dl = d.dl; c.dcolor = d.dcolor; c.dnormal = d.dnormal; c.dlight = d.dlight;
+    float L0 = 0.f, L1 = 0.f, L2 = 0.f;
+    if (c.mode == PIKO_SHADE_LAMBERT) {
+      L0 = __ldg(c.light); L1 = __ldg(c.light + 1); L2 = __ldg(c.light + 2);
     }
-    // per triangle: vertex gradients; per scene: light gradient
-    const unsigned grp = __match_any_sync(FULL_MASK, gid);
-    const unsigned sgrp = __match_any_sync(FULL_MASK, hit ? (unsigned)s : 0xFFFFFFFFu);
-#pragma unroll
-    for (int q = 0; q < BWD_VALS + 3; ++q) sval[warp][q][lane] = v[q];
-    __syncwarp();
-    if (hit && (grp & lt_mask) == 0u) {
-      float acc[BWD_VALS];
-#pragma unroll
-      for (int q = 0; q < BWD_VALS; ++q) acc[q] = 0.f;
-      for (unsigned m = grp; m; m &= m - 1) {
-        const int src = __ffs(m) - 1;
-#pragma unroll
-        for (int q = 0; q < BWD_VALS; ++q) acc[q] += sval[warp][q][src];
-      }
-      const BatchScene& d = b.sc[s];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        if (d.dcolor && (d.mode == PIKO_SHADE_GOURAUD || d.color)) {
-          float* dc = d.dcolor + 3 * (size_t)vid[j];
-          atomicAdd(dc, acc[6 * j]); atomicAdd(dc + 1, acc[6 * j + 1]); atomicAdd(dc + 2, acc[6 * j + 2]);
-        }
-        if (d.dnormal && d.mode == PIKO_SHADE_LAMBERT) {
-          float* dn = d.dnormal + 3 * (size_t)vid[j];
-          atomicAdd(dn, acc[6 * j + 3]); atomicAdd(dn + 1, acc[6 * j + 4]); atomicAdd(dn + 2, acc[6 * j + 5]);
-        }
-      }
-    }
-    if (hit && (sgrp & lt_mask) == 0u) {
-      const BatchScene& d = b.sc[s];
-      if (d.dlight && d.mode == PIKO_SHADE_LAMBERT) {
-        float l0 = 0.f, l1 = 0.f, l2 = 0.f;
-        for (unsigned m = sgrp; m; m &= m - 1) {
-          const int src = __ffs(m) - 1;
-          l0 += sval[warp][18][src]; l1 += sval[warp][19][src]; l2 += sval[warp][20][src];
-        }
-        atomicAdd(d.dlight, l0); atomicAdd(d.dlight + 1, l1); atomicAdd(d.dlight + 2, l2);
-      }
-    }
-    __syncwarp();
+    const int lt = i - __ldg(b.btile_prefix + s);
+    const int ntx = (c.W + BWD_TILE - 1) / BWD_TILE;
+    const int ty = lt / ntx, tx = lt - ty * ntx;
+    backward_tile(c, tx * BWD_TILE, ty * BWD_TILE, sm, L0, L1, L2, gl0, gl1, gl2);
+    if (c.dlight && c.mode == PIKO_SHADE_LAMBERT) bwd_flush_light(sm, c.dlight, gl0, gl1, gl2);
   }
 }
 
@@ -695,7 +606,7 @@ int batch_prepare(BatchState*& bs, int num_sms, const piko_scene* scenes, int n,
     x.g.bshift_x = ilog2i(bw); x.g.bshift_y = ilog2i(bh);
     x.g.nbx = (s.width + bw - 1) / bw; x.g.nby = (s.height + bh - 1) / bh;
     x.V = s.num_vertices; x.T = s.num_triangles; x.mode = s.shade_mode; x.schedule = sched;
-    x.vtx_base = (int)tv; x.tri_base = (int)tt; x.bin_base = (int)tb; x.pix_base = (int)tp;
+    x.vtx_base = (int)tv; x.tri_base = (int)tt; x.bin_base = (int)tb; x.pix_base = 0;
     tile_layout(s.num_triangles, bw * bh, s.shade_mode, s.color != nullptr, 255, x.slot_bits, x.nslots, x.rec_stride);
     x.pos = reinterpret_cast<const float4*>(s.pos);
     x.tris = s.tris; x.mvp = s.mvp; x.color = s.color; x.normal = s.normal; x.light = s.light_dir;
@@ -705,7 +616,8 @@ int batch_prepare(BatchState*& bs, int num_sms, const piko_scene* scenes, int n,
     x.galb_out = reinterpret_cast<uint2*>(f.gbuf_albedo);
     const int ntiles = x.g.nbx * x.g.nby;
     pv[i] = (int)tv; pt[i] = (int)tt; pb[i] = (int)tb; ps[i] = (int)tsd; pd[i] = (int)tdy; pp[i] = (int)tp;
-    tv += x.V; tt += x.T; tb += ntiles; tp += (long long)s.width * s.height;
+    tv += x.V; tt += x.T; tb += ntiles;
+    tp += (long long)((s.width + BWD_TILE - 1) / BWD_TILE) * ((s.height + BWD_TILE - 1) / BWD_TILE);
     if (sched == PIKO_SCHED_STATIC) tsd += ntiles;
     else tdy += ntiles;
     if (bw * bh > max_bin_px) max_bin_px = bw * bh;
@@ -792,9 +704,9 @@ int batch_prepare(BatchState*& bs, int num_sms, const piko_scene* scenes, int n,
   b.bin_prefix = reinterpret_cast<const int*>(dd + dbytes + 2 * pbytes);
   b.stat_prefix = reinterpret_cast<const int*>(dd + dbytes + 3 * pbytes);
   b.dyn_prefix = reinterpret_cast<const int*>(dd + dbytes + 4 * pbytes);
-  b.pix_prefix = reinterpret_cast<const int*>(dd + dbytes + 5 * pbytes);
+  b.btile_prefix = reinterpret_cast<const int*>(dd + dbytes + 5 * pbytes);
   b.total_v = (int)tv; b.total_t = (int)tt; b.total_bins = (int)tb; b.total_static = (int)tsd;
-  b.total_dyn = (int)tdy; b.total_pix = (int)tp;
+  b.total_dyn = (int)tdy; b.total_btiles = (int)tp;
   b.vtx = bs->vtx; b.vdot = bs->vdot; b.rect = bs->rect; b.cnt = bs->cnt; b.bin_off = bs->bin_off;
   b.cursor = bs->cursor; b.chunk_state = bs->chunk_state; b.bin_tris = bs->bin_tris;
   b.capacity = (unsigned long long)bs->ecap; b.sync = bs->sync;
@@ -908,14 +820,27 @@ int batch_launch_backward(BatchState* bs, const piko_scene* scenes, int n, const
   BatchBwdParams p;
   p.n = n;
   p.sc = bs->params.sc;
-  p.pix_prefix = bs->params.pix_prefix;
-  p.tri_prefix = bs->params.tri_prefix;
-  p.total_pix = bs->params.total_pix;
+  p.btile_prefix = bs->params.btile_prefix;
+  p.total_btiles = bs->params.total_btiles;
   p.vtx = bs->vtx;
-  long long blocks = ((long long)p.total_pix + 255) / 256;
-  if (blocks > (long long)num_sms * 8) blocks = (long long)num_sms * 8;
+  static int per_sm_of[64] = {0};  // the shared-memory opt-in is per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int& per_sm = per_sm_of[dev & 63];
+  if (per_sm == 0) {
+    int v = 0;
+    if (cudaFuncSetAttribute(k_batch_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BwdSmem)) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_batch_backward, BWD_THREADS, sizeof(BwdSmem)) !=
+            cudaSuccess ||
+        v < 1)
+      v = 1;
+    per_sm = v;
+  }
+  long long blocks = (long long)per_sm * num_sms;
+  if (blocks > p.total_btiles) blocks = p.total_btiles;
   if (blocks < 1) blocks = 1;
-  k_batch_backward<<<(int)blocks, 256, 0, stream>>>(p);
+  k_batch_backward<<<(int)blocks, BWD_THREADS, sizeof(BwdSmem), stream>>>(p);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     err = std::string("batch backward launch: ") + cudaGetErrorString(e);

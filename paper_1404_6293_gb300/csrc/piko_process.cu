@@ -78,10 +78,17 @@ __global__ void __maxnreg__(PIKO_PROCESS_MAXNREG) k_process(ProcessParams p) {
     const unsigned beg = __ldg(p.bin_off + tile), end = __ldg(p.bin_off + tile + 1);
     process_tile(sc, tile, beg, end, p.bin_tris, sm, big_base, p.stats != 0, st, L0, L1, L2);
   }
-  if (p.stats) {
-    atomicAdd(&p.st->tests, st.tests);
-    atomicAdd(&p.st->frags, st.frags);
-    atomicAdd(&p.st->shaded, st.shaded);
+  if (p.stats) {  // one atomic per warp: same-address atomics from every thread serialise
+    for (int o = 16; o > 0; o >>= 1) {
+      st.tests += __shfl_down_sync(FULL_MASK, st.tests, o);
+      st.frags += __shfl_down_sync(FULL_MASK, st.frags, o);
+      st.shaded += __shfl_down_sync(FULL_MASK, st.shaded, o);
+    }
+    if ((tid & 31) == 0) {
+      atomicAdd(&p.st->tests, st.tests);
+      atomicAdd(&p.st->frags, st.frags);
+      atomicAdd(&p.st->shaded, st.shaded);
+    }
   }
 }
 

@@ -327,6 +327,37 @@ def test_backward_matches_oracle_gradients(mode):
         _grad_check(dlg.cpu().numpy(), dl)
 
 
+# Two scene shapes select the two backward forms: few large triangles (per
+# 16x16 tile, a shared table of distinct triangles) and more than one triangle
+# per four pixels (per pixel).  Both against the oracle's gradients.
+@pytest.mark.parametrize("shape", ["large", "tiny"])
+def test_backward_tile_and_pixel_forms_match_oracle(shape):
+    torch = _torch()
+    if shape == "large":
+        s = S.random_triangles(160, 112, 150, 40.0, seed=77, shade_mode=S.SHADE_LAMBERT, with_normals=True)
+        assert 4 * s.num_triangles <= s.width * s.height
+    else:
+        s = S.heightfield(96, 80, 60, 40, seed=78, shade_mode=S.SHADE_LAMBERT, with_color=True)
+        assert 4 * s.num_triangles > s.width * s.height
+    out = rasterize(s, 16, 16, "static")
+    ref_key, _ = oracle.raster_brute(s)
+    assert_keys_equal(out["key"], ref_key)
+    tgt = S.target_image(s.width, s.height, seed=5)[0]
+    g = np.zeros((s.height, s.width, 4))
+    g[..., :3] = 2.0 * (oracle.shade(s, ref_key)[..., :3] - tgt[..., :3])
+    dc, dn, dl = oracle.backward(s, ref_key, g)
+    V = s.num_vertices
+    dcg = torch.zeros((V, 3), device="cuda")
+    dng = torch.zeros((V, 3), device="cuda")
+    dlg = torch.zeros(3, device="cuda")
+    out["r"].backward(out["ds"], out["fb"], torch.from_numpy(g.astype(np.float32)).cuda(), dcg, dng, dlg)
+    torch.cuda.synchronize()
+    if s.color is not None:
+        _grad_check(dcg.cpu().numpy(), dc)
+    _grad_check(dng.cpu().numpy(), dn)
+    _grad_check(dlg.cpu().numpy(), dl)
+
+
 def test_autograd_render_gradients_match_oracle():
     torch = _torch()
     from paper_1404_6293_gb300.autograd import render

@@ -110,6 +110,23 @@ class ClockSampler:
                 "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The job's time is its slowest rank's: MAX all-reduce (identity on one rank)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, ms: float, scale: float = 1e6) -> float:
+    """Whole-job throughput: every rank processes its own replica of the
+    workload (weak scaling), so the job moves world x units in the slowest
+    rank's time."""
+    return world * units_per_rank / (ms * 1e-3) / scale
+
+
 def workload(args):
     from paper_1404_6293_gb300 import scenes as S
     scene = S.heightfield()
@@ -254,13 +271,9 @@ def run_ours(args):
     step_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
     stage_ms = np.array([[ev[k][2 + i].elapsed_time(ev[k][3 + i]) for i in range(L.PIKO_NUM_STAGE_EVENTS - 1)]
                          for k in range(K)])
-    ms = float(np.sum(step_ms) / K)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * T / (ms * 1e-3) / 1e6
-    shaded_gfrag = world * covered / (ms * 1e-3) / 1e9
+    ms = max_over_ranks(float(np.sum(step_ms) / K), dist, "cuda")
+    value = job_throughput(T, world, ms)
+    shaded_gfrag = job_throughput(covered, world, ms, 1e9)
 
     # ---------------------------------------------------------------- roofline
     peaks = measured_peaks()
@@ -319,12 +332,8 @@ def run_ours(args):
             r.render_from_host(host_in, ds, fb, key_h, rgba_h)
             pairs[k][1].record(stream)
         barrier()
-        e_ms = sum(a.elapsed_time(b) for a, b in pairs) / Ke
-        if dist is not None:
-            t = torch.tensor([e_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": world * T / (e_ms * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in pairs) / Ke, dist, "cuda")
+        e2e = {"value": job_throughput(T, world, e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e_ms, "steps": Ke}
         if r.status()[0] != 0:
             raise RuntimeError("status error after the end-to-end loop")

@@ -162,7 +162,11 @@ class Rasterizer:
 
     def set_stage_events(self, events):
         """Records the given torch.cuda.Event objects (PIKO_NUM_STAGE_EVENTS of
-        them, already created) at the stage boundaries of the next forward."""
+        them, already created) at the stage boundaries of the next forward;
+        None stops the recording."""
+        if events is None:
+            self._check(self.lib.piko_raster_set_stage_events(self._h, None, 0))
+            return
         arr = (C.c_void_p * L.PIKO_NUM_STAGE_EVENTS)(*[C.c_void_p(e.cuda_event) for e in events])
         self._check(self.lib.piko_raster_set_stage_events(self._h, arr, L.PIKO_NUM_STAGE_EVENTS))
 
@@ -191,13 +195,17 @@ class Rasterizer:
                          rgba_out: Optional[torch.Tensor] = None, stream=None) -> Framebuffer:
         """End-to-end frame from host memory: copies the named host tensors
         (pinned for asynchronous copies) into the scene's device tensors, runs
-        the forward pass and copies the key (and rgba) back into host tensors."""
-        for name, t in host_inputs.items():
-            getattr(scene, name).copy_(t, non_blocking=True)
-        self.forward(scene, fb, stream)
-        key_out.copy_(fb.key, non_blocking=True)
-        if rgba_out is not None and fb.rgba is not None:
-            rgba_out.copy_(fb.rgba, non_blocking=True)
+        the forward pass and copies the key (and rgba) back into host tensors,
+        all on ``stream`` (default: the current stream), so that frames on two
+        streams with two handles overlap their copies with each other's work."""
+        s = torch.cuda.current_stream() if stream is None else stream
+        with torch.cuda.stream(s):
+            for name, t in host_inputs.items():
+                getattr(scene, name).copy_(t, non_blocking=True)
+            self.forward(scene, fb, s)
+            key_out.copy_(fb.key, non_blocking=True)
+            if rgba_out is not None and fb.rgba is not None:
+                rgba_out.copy_(fb.rgba, non_blocking=True)
         return fb
 
     def deferred_light(self, fb: Framebuffer, lights: torch.Tensor, out: Optional[torch.Tensor] = None,

@@ -36,6 +36,9 @@ __device__ __forceinline__ TileScene scene_of(const ProcessParams& p) {
 #endif
 // The register cap trades a few spills on the rare int64 / warp paths for
 // occupancy on the common path (about 120 registers uncapped).
+// One instance per schedule (SCHED = PIKO_SCHED_*), so that each carries
+// only its own tile loop.
+template <int SCHED>
 __global__ void __maxnreg__(PIKO_PROCESS_MAXNREG) k_process(ProcessParams p) {
   extern __shared__ __align__(16) unsigned long long smem[];
   const int bin_px = 1 << (p.g.bshift_x + p.g.bshift_y);
@@ -53,7 +56,7 @@ __global__ void __maxnreg__(PIKO_PROCESS_MAXNREG) k_process(ProcessParams p) {
   if (p.mode == PIKO_SHADE_LAMBERT) {
     L0 = __ldg(p.light); L1 = __ldg(p.light + 1); L2 = __ldg(p.light + 2);
   }
-  const bool dynamic = p.schedule == PIKO_SCHED_DYNAMIC;
+  constexpr bool dynamic = SCHED == PIKO_SCHED_DYNAMIC;
   for (int i = tid; i < bin_px; i += nt) sm.skey[i] = KEY_EMPTY;
   if (tid == 0) {
     s_nbig = 0u;
@@ -64,10 +67,10 @@ __global__ void __maxnreg__(PIKO_PROCESS_MAXNREG) k_process(ProcessParams p) {
   TileStats st = {0ull, 0ull, 0ull};
   for (int iter = 0;; ++iter) {
     int tile;
-    if (p.schedule == PIKO_SCHED_HARDWARE) {
+    if (SCHED == PIKO_SCHED_HARDWARE) {
       if (iter > 0) break;
       tile = blockIdx.x;
-    } else if (p.schedule == PIKO_SCHED_STATIC) {
+    } else if (SCHED == PIKO_SCHED_STATIC) {
       tile = blockIdx.x + iter * gridDim.x;
     } else {
       tile = s_tile[iter & 1];
@@ -103,26 +106,36 @@ static size_t smem_bytes(const ProcessParams& p, int threads) {
   return tile_smem_bytes(1 << (p.g.bshift_x + p.g.bshift_y), threads, p.nslots, p.rec_stride);
 }
 
+using ProcessKernel = void (*)(ProcessParams);
+
+static ProcessKernel process_kernel(int schedule) {
+  if (schedule == PIKO_SCHED_DYNAMIC) return k_process<PIKO_SCHED_DYNAMIC>;
+  if (schedule == PIKO_SCHED_HARDWARE) return k_process<PIKO_SCHED_HARDWARE>;
+  return k_process<PIKO_SCHED_STATIC>;
+}
+
 cudaError_t process_occupancy(const ProcessParams& p0, int threads, int* blocks_per_sm) {
   ProcessParams p = p0;
   layout(p, threads);
   const size_t smem = smem_bytes(p, threads);
+  const ProcessKernel k = process_kernel(p.schedule);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_process, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_process, threads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, threads, smem);
 }
 
 cudaError_t launch_process(const ProcessParams& p0, int threads, int grid, cudaStream_t s) {
   ProcessParams p = p0;
   layout(p, threads);
   const size_t smem = smem_bytes(p, threads);
+  const ProcessKernel k = process_kernel(p.schedule);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_process, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_process<<<grid, threads, smem, s>>>(p);
+  k<<<grid, threads, smem, s>>>(p);
   return cudaGetLastError();
 }
 

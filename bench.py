@@ -229,6 +229,9 @@ def run_ours(args):
     if args.threads:
         r.set_option(L.PIKO_OPT_THREADS_PER_TILE, args.threads)
         cfg["threads_per_tile"] = args.threads
+    if args.small_px:
+        r.set_option(L.PIKO_OPT_SMALL_TRI_PIXELS, args.small_px)
+        cfg["small_tri_pixels"] = args.small_px
     ds = DeviceScene.from_host(scene)
     fb = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode)
     r.forward(ds, fb)  # sizes the bin lists (capacity check on)
@@ -737,6 +740,9 @@ def main():
     ap.add_argument("--bins", type=int, default=16)
     ap.add_argument("--schedule", default="static", choices=["static", "dynamic", "hardware"])
     ap.add_argument("--threads", type=int, default=0, help="Process CTA size (0: library default)")
+    ap.add_argument("--small-px", type=int, default=0,
+                    help="largest box (pixels inside a tile) one thread rasterizes; larger boxes take a warp "
+                         "(0: library default)")
     ap.add_argument("--batch-scenes", type=int, default=256)
     ap.add_argument("--batch-bins", type=int, default=0, help="batch workload: one square bin size for all scenes "
                     "instead of the autotuner's choice (0: autotune)")

@@ -406,8 +406,8 @@ __global__ void __maxnreg__(PIKO_BATCH_MAXNREG) k_batch_forward(BatchParams b) {
   __shared__ unsigned s_nbig;
   TileSmem sm;
   sm.skey = smem;
-  sm.sbig = smem + b.max_bin_px;
-  sm.srec = reinterpret_cast<int*>(smem + b.max_bin_px + blockDim.x);
+  sm.sbig = reinterpret_cast<int*>(smem + b.max_bin_px);
+  sm.srec = sm.sbig + blockDim.x * BIG_REC;
   sm.s_nbig = &s_nbig;
   if (cta_should_stop(b.st)) return;
   if (b.phases & PH_VERTEX) {

@@ -47,8 +47,8 @@ __global__ void __maxnreg__(PIKO_PROCESS_MAXNREG) k_process(ProcessParams p) {
   __shared__ unsigned s_nbig;
   TileSmem sm;
   sm.skey = smem;
-  sm.sbig = smem + bin_px;
-  sm.srec = reinterpret_cast<int*>(smem + bin_px + nt);
+  sm.sbig = reinterpret_cast<int*>(smem + bin_px);
+  sm.srec = sm.sbig + nt * BIG_REC;
   sm.s_nbig = &s_nbig;
   if (p.st->flags & STATUS_SKIP_MASK) return;
   const TileScene sc = scene_of(p);

@@ -46,9 +46,14 @@ struct TileScene {
 };
 
 // Per-CTA shared memory of the stage.
+// A large triangle queued for the warps: its snapped vertices, depths and
+// area as set up by the thread that met it (so that the warp re-reads
+// nothing from global memory), then its triangle index and record slot.
+constexpr int BIG_REC = 13;  // X0 Y0 X1 Y1 X2 Y2 Z0 Z1 Z2 A_lo A_hi t slot (odd: distinct banks)
+
 struct TileSmem {
   unsigned long long* skey;  // [bin_px], all KEY_EMPTY between tiles
-  unsigned long long* sbig;  // [nt] ring of (slot << 32 | t)
+  int* sbig;                 // [nt][BIG_REC] ring of queued large triangles
   int* srec;                 // [nslots][rec_stride]
   unsigned* s_nbig;          // grows monotonically
 };
@@ -397,7 +402,11 @@ __device__ __forceinline__ void process_tile(const TileScene& p, int tile, unsig
           // the ring counter only ever grows; with nt a power of two the ring
           // index stays consistent across its 2^32 wrap
           const unsigned q = atomicAdd(sm.s_nbig, 1u);
-          sm.sbig[q & (nt - 1)] = ((unsigned long long)slot << 32) | t;
+          int* e = sm.sbig + (q & (nt - 1)) * BIG_REC;
+          e[0] = s.X0; e[1] = s.Y0; e[2] = s.X1; e[3] = s.Y1; e[4] = s.X2; e[5] = s.Y2;
+          e[6] = s.Z0; e[7] = s.Z1; e[8] = s.Z2;
+          e[9] = (int)(unsigned)(s.A & 0xFFFFFFFFll); e[10] = (int)(s.A >> 32);
+          e[11] = (int)t; e[12] = (int)slot;
           pushed = true;
         }
       }
@@ -406,10 +415,13 @@ __device__ __forceinline__ void process_tile(const TileScene& p, int tile, unsig
     const unsigned nbig = (unsigned)__syncthreads_count(pushed);
     if (nbig != 0u) {
       for (unsigned q = warp; q < nbig; q += nwarps) {
-        const unsigned long long e = sm.sbig[(big_base + q) & (nt - 1)];
-        const unsigned t = (unsigned)e, slot = (unsigned)(e >> 32);
+        const int* e = sm.sbig + ((big_base + q) & (nt - 1)) * BIG_REC;
         TriSetup s;
-        load_setup(p, t, s);
+        s.X0 = e[0]; s.Y0 = e[1]; s.X1 = e[2]; s.Y1 = e[3]; s.X2 = e[4]; s.Y2 = e[5];
+        s.Z0 = e[6]; s.Z1 = e[7]; s.Z2 = e[8];
+        s.A = (long long)(((unsigned long long)(unsigned)e[10] << 32) | (unsigned)e[9]);
+        s.v0 = s.v1 = s.v2 = 0;  // not needed to rasterize
+        const unsigned t = (unsigned)e[11], slot = (unsigned)e[12];
         int px0, px1, py0, py1;
         centre_range(min(s.X0, min(s.X1, s.X2)), max(s.X0, max(s.X1, s.X2)), x0, x1, px0, px1);
         centre_range(min(s.Y0, min(s.Y1, s.Y2)), max(s.Y0, max(s.Y1, s.Y2)), y0, y1, py0, py1);
@@ -464,7 +476,7 @@ inline void tile_layout(int num_triangles, int bin_px, int mode, bool has_color,
 }
 
 inline size_t tile_smem_bytes(int bin_px, int threads, int nslots, int rec_stride) {
-  return (size_t)bin_px * 8 + (size_t)threads * 8 + (size_t)nslots * rec_stride * 4;
+  return (size_t)bin_px * 8 + (size_t)threads * BIG_REC * 4 + (size_t)nslots * rec_stride * 4;
 }
 
 }  // namespace piko

@@ -37,8 +37,8 @@ constexpr int BWD_VALS = 18;                  // 3 vertices x (3 colour + 3 norm
 constexpr unsigned BWD_NONE = 0xFFFFFFFFu;
 
 // per-slot words: oriented X0 Y0 X1 Y1 X2 Y2, vertex ids v0 v1 v2, A (lo, hi),
-// the triangle id and a valid flag; 13 words (odd: distinct slots fall in
-// distinct banks)
+// the triangle id (replaced by 1/A once the slot is set up) and a valid flag;
+// 13 words (odd: distinct slots fall in distinct banks)
 constexpr int RB_V = 6, RB_ALO = 9, RB_AHI = 10, RB_T = 11, RB_OK = 12, BWD_REC = 13;
 
 struct BwdScene {
@@ -167,6 +167,7 @@ __device__ __forceinline__ void backward_tile(const BwdScene& sc, int x0, int y0
       r[RB_V] = ts.v0; r[RB_V + 1] = ts.v1; r[RB_V + 2] = ts.v2;
       r[RB_ALO] = (int)(unsigned)(ts.A & 0xFFFFFFFFll);
       r[RB_AHI] = (int)(ts.A >> 32);
+      r[RB_T] = __float_as_int(__frcp_rn((float)ts.A));
     }
     if (!direct) {
       float* a = sm.acc + s * BWD_VALS;
@@ -189,11 +190,11 @@ __device__ __forceinline__ void backward_tile(const BwdScene& sc, int x0, int y0
     const long long A = (long long)(((unsigned long long)(unsigned)r[RB_AHI] << 32) | (unsigned)r[RB_ALO]);
     const int vid[3] = {r[RB_V], r[RB_V + 1], r[RB_V + 2]};
     const long long Px = 256LL * x + 128, Py = 256LL * y + 128;
-    const long long w0 = (long long)(X2 - X1) * (Py - Y1) - (long long)(Y2 - Y1) * (Px - X1);
     const long long w1 = (long long)(X0 - X2) * (Py - Y2) - (long long)(Y0 - Y2) * (Px - X2);
     const long long w2 = (long long)(X1 - X0) * (Py - Y0) - (long long)(Y1 - Y0) * (Px - X0);
-    const float fA = (float)A;
-    const float b[3] = {__fdiv_rn((float)w0, fA), __fdiv_rn((float)w1, fA), __fdiv_rn((float)w2, fA)};
+    const long long w0 = A - w1 - w2;  // the three edge functions sum to A
+    const float rA = __int_as_float(r[RB_T]);
+    const float b[3] = {(float)w0 * rA, (float)w1 * rA, (float)w2 * rA};
     const float4 g = __ldg(sc.dl + o);
     if (sc.mode == PIKO_SHADE_GOURAUD) {
 #pragma unroll

@@ -56,6 +56,7 @@ struct piko_raster {
   long long ecap = 0;
   DevStatus* status = nullptr;
   unsigned long long* h_needed = nullptr;  // pinned
+  long long last_entries = 0;              // bin entries of the last frame read back (0: none yet)
   cudaStream_t last_stream = nullptr;
   std::string err;
 };
@@ -309,6 +310,10 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
   ProcessParams p;
   p.g = h->g;
   p.ntiles = h->nbins;
+  // records sized from this frame's bin-list total when it was read back,
+  // else from the last one read back
+  if (h->check_capacity) h->last_entries = (long long)*h->h_needed;
+  p.slots_hint = slots_for_entries(h->last_entries, h->nbins);
   p.schedule = h->schedule;
   p.small_px = h->small_px;
   p.mode = s->shade_mode;

@@ -188,6 +188,15 @@ __device__ __forceinline__ int4 snap_vertex(float4 p, const float* m, float fW, 
 }
 
 // --------------------------------------------------------------- kernels
+// Records wanted for a scene whose bin lists hold `entries` entries over
+// `tiles` tiles: 1.4 x the mean, in multiples of 32 (1.4 x covers the
+// spread of entry counts between tiles of the measured workloads).
+inline int slots_for_entries(long long entries, int tiles) {
+  if (entries <= 0 || tiles <= 0) return 0;
+  const long long want = (14 * entries / tiles + 5 * 32) / (10 * 32) * 32;  // round(1.4 mean / 32) * 32
+  return (int)(want < 32 ? 32 : (want > 4096 ? 4096 : want));
+}
+
 struct ProcessParams {
   RasterGeom g;
   int ntiles;
@@ -195,6 +204,7 @@ struct ProcessParams {
   int small_px;
   int mode;
   int unclamped;
+  int slots_hint;  // shading records per tile wanted (0: the largest the key encoding allows)
   int stats;
   int num_triangles;
   int slot_bits;   // set by launch_process: bits of the record slot below the triangle index

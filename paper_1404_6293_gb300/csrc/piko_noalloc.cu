@@ -143,6 +143,7 @@ extern "C" int piko_raster_forward_noalloc(const piko_scene* s, piko_framebuffer
                  status, num_sms, st);
 
   ProcessParams p;
+  p.slots_hint = 0;
   p.g = g;
   p.ntiles = nbins;
   p.schedule = schedule;

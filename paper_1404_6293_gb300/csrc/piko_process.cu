@@ -99,7 +99,7 @@ __global__ void __maxnreg__(PIKO_PROCESS_MAXNREG) k_process(ProcessParams p) {
 static void layout(ProcessParams& p, int threads) {
   (void)threads;
   tile_layout(p.num_triangles, 1 << (p.g.bshift_x + p.g.bshift_y), p.mode, p.color != nullptr, 511, p.slot_bits,
-              p.nslots, p.rec_stride);
+              p.nslots, p.rec_stride, p.slots_hint);
 }
 
 static size_t smem_bytes(const ProcessParams& p, int threads) {

@@ -461,13 +461,17 @@ __device__ __forceinline__ void process_tile(const TileScene& p, int tile, unsig
 
 // Record layout of a scene: slot bits below the triangle index (2^id_bits > T,
 // so no key equals the all-ones empty key), records per tile and words per
-// record (odd, so that distinct records fall in distinct banks).
+// record (odd, so that distinct records fall in distinct banks).  want_slots
+// (0: as many as allowed) sizes the record area: shared memory taken by
+// records is taken from L1, which serves the kernel's gathers, so records
+// are sized for the tiles' typical entry count rather than the largest.
 inline void tile_layout(int num_triangles, int bin_px, int mode, bool has_color, int max_slots, int& slot_bits,
-                        int& nslots, int& rec_stride) {
+                        int& nslots, int& rec_stride, int want_slots = 0) {
   int id_bits = 1;
   while (id_bits < 32 && (1LL << id_bits) <= (long long)num_triangles) ++id_bits;
   slot_bits = 40 - id_bits < 16 ? 40 - id_bits : 16;
   int want = bin_px <= 256 ? 255 : max_slots;
+  if (want_slots > 0 && want_slots < want) want = want_slots;
   const int cap = (1 << slot_bits) - 1;
   nslots = want < cap ? want : cap;
   const int attrs = mode == PIKO_SHADE_GOURAUD ? 9 : (mode == PIKO_SHADE_LAMBERT ? (has_color ? 12 : 3) : 18);

@@ -15,6 +15,7 @@ int batch_prepare(BatchState*& bs, int num_sms, const piko_scene* scenes, int n,
                   int default_schedule, cudaStream_t stream, std::string& err);
 int batch_launch_forward(BatchState* bs, DevStatus* st, bool persistent, cudaStream_t stream, std::string& err);
 long long batch_capacity(const BatchState* bs);
+void batch_note_entries(BatchState* bs, long long entries);
 int batch_grow_entries(BatchState* bs, long long need, std::string& err);
 int batch_launch_backward(BatchState* bs, const piko_scene* scenes, int n, const piko_framebuffer* fbs,
                           const float* const* dl, float* const* dc, float* const* dn, float* const* dlt, int num_sms,
@@ -363,6 +364,7 @@ int piko_raster_forward_batch(piko_raster* h, const piko_scene* scenes, int n, p
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(h, e, "batch bin-list size read-back");
     const long long need = (long long)*h->h_needed;
+    batch_note_entries(h->batch, need);
     if (need <= batch_capacity(h->batch)) return PIKO_OK;
     if (attempt > 0 || need > 0xFFFFFFF0LL) return fail(h, PIKO_ERR_OVERFLOW, "batch bin lists too large");
     if ((r = batch_grow_entries(h->batch, need, h->err)) != PIKO_OK) return r;

@@ -522,6 +522,8 @@ struct BatchState {
   size_t smem = 0;
   int grid = 0;
   int n = 0;
+  long long last_entries = 0;  // bin entries of the last frame read back (sizes the shading records)
+  long long last_bins = 0;     // bins of that frame
 };
 
 namespace {
@@ -583,6 +585,8 @@ int batch_prepare(BatchState*& bs, int num_sms, const piko_scene* scenes, int n,
   std::vector<int> pv(n + 1), pt(n + 1), pb(n + 1), ps(n + 1), pd(n + 1), pp(n + 1);
   long long tv = 0, tt = 0, tb = 0, tsd = 0, tdy = 0, tp = 0;
   int max_bin_px = 64, max_rec = 0;
+  // shading records per tile from the last frame's mean entries per bin
+  const int slots_hint = bs ? slots_for_entries(bs->last_entries, (int)(bs->last_bins > 0 ? bs->last_bins : 1)) : 0;
   for (int i = 0; i < n; ++i) {
     const piko_scene& s = scenes[i];
     const piko_framebuffer& f = fbs[i];
@@ -607,7 +611,8 @@ int batch_prepare(BatchState*& bs, int num_sms, const piko_scene* scenes, int n,
     x.g.nbx = (s.width + bw - 1) / bw; x.g.nby = (s.height + bh - 1) / bh;
     x.V = s.num_vertices; x.T = s.num_triangles; x.mode = s.shade_mode; x.schedule = sched;
     x.vtx_base = (int)tv; x.tri_base = (int)tt; x.bin_base = (int)tb; x.pix_base = 0;
-    tile_layout(s.num_triangles, bw * bh, s.shade_mode, s.color != nullptr, 255, x.slot_bits, x.nslots, x.rec_stride);
+    tile_layout(s.num_triangles, bw * bh, s.shade_mode, s.color != nullptr, 255, x.slot_bits, x.nslots, x.rec_stride,
+                slots_hint);
     x.pos = reinterpret_cast<const float4*>(s.pos);
     x.tris = s.tris; x.mvp = s.mvp; x.color = s.color; x.normal = s.normal; x.light = s.light_dir;
     x.key_out = reinterpret_cast<unsigned long long*>(f.key);
@@ -776,6 +781,12 @@ int batch_launch_forward(BatchState* bs, DevStatus* st, bool persistent, cudaStr
 }
 
 long long batch_capacity(const BatchState* bs) { return bs ? bs->ecap : 0; }
+
+void batch_note_entries(BatchState* bs, long long entries) {
+  if (!bs) return;
+  bs->last_entries = entries;
+  bs->last_bins = bs->params.total_bins;
+}
 
 int batch_grow_entries(BatchState* bs, long long need, std::string& err) {
   return grow_dev(&bs->bin_tris, &bs->ecap, need, false, err);

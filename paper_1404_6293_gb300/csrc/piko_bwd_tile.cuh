@@ -55,11 +55,16 @@ struct BwdScene {
   float* dlight;
 };
 
+// Tiles with more distinct triangles than this (under 3 pixels per triangle)
+// skip the shared accumulators: their slots would each collect only a pixel
+// or two, so the terms go straight to the gradient arrays.
+constexpr int BWD_DIRECT_SLOTS = 96;
+
 struct BwdSmem {
   unsigned hkey[BWD_HASH];
   unsigned short hslot[BWD_HASH];
   int rec[BWD_THREADS * BWD_REC];
-  float acc[BWD_THREADS * BWD_VALS];
+  float acc[BWD_DIRECT_SLOTS * BWD_VALS];  // only tiles with at most BWD_DIRECT_SLOTS slots accumulate here
   float stage[BWD_THREADS / 32][BWD_VALS][33];  // padded: lane q reads row q, column m
   float lred[BWD_THREADS / 32][3];
   int nslot;
@@ -104,10 +109,6 @@ __device__ __forceinline__ void bwd_add_term(const BwdScene& sc, const int* r, i
   }
 }
 
-// Tiles with more distinct triangles than this (under 3 pixels per triangle)
-// skip the shared accumulators: their slots would each collect only a pixel
-// or two, so the terms go straight to the gradient arrays.
-constexpr int BWD_DIRECT_SLOTS = 96;
 
 // One tile with its top-left pixel (x0, y0).  Entered and left with a clear
 // hash table (bwd_clear once per CTA before the first tile); blockDim.x must

@@ -503,7 +503,7 @@ def test_light_pass_closed_forms():
 
 # ------------------------------------------------------------ gradients O13
 def _fd_scene():
-    s = S.random_triangles(32, 32, 30, 10.0, seed=21, shade_mode=S.SHADE_LAMBERT, with_normals=True)
+    s = S.random_triangles(48, 48, 90, 10.0, seed=21, shade_mode=S.SHADE_LAMBERT, with_normals=True)
     s.light_dir = np.array([0.3, -0.4, -0.866], np.float32)
     return s
 
@@ -511,9 +511,9 @@ def _fd_scene():
 def test_backward_matches_central_differences():
     s = _fd_scene()
     key, _ = oracle.raster_brute(s)
-    tgt = S.target_image(32, 32, seed=3)[0]
+    tgt = S.target_image(48, 48, seed=3)[0]
     rgba = oracle.shade(s, key)
-    g = np.zeros((32, 32, 4))
+    g = np.zeros((48, 48, 4))
     g[..., :3] = 2.0 * (rgba[..., :3] - tgt[..., :3])
     dc, dn, dl = oracle.backward(s, key, g)
     col = s.color.astype(np.float64)
@@ -531,15 +531,19 @@ def test_backward_matches_central_differences():
         lm = oracle.loss(s, key, tgt, color=c, normal=n, light=l)
         return (lp - lm) / (2 * h)
 
+    # 128 seeded (vertex, channel) indices per array and the 3 light components:
+    # 259 parameters, each against a float64 central difference of the loss
     rng = np.random.default_rng(0)
     used = np.unique(s.tris[np.unique(ids(key)[key != EMPTY])])
+    params = np.array([3 * v + ch for v in used for ch in range(3)])
+    assert params.size >= 128
     for which, an in (("c", dc), ("n", dn)):
         scale = np.abs(an).max()
         assert scale > 0
-        for v in rng.choice(used, 12, replace=False):
-            for ch in range(3):
-                num = fd(which, 3 * v + ch)
-                assert abs(num - an[v, ch]) <= 1e-4 * max(abs(an[v, ch]), 1e-3 * scale) + 1e-9
+        for idx in rng.choice(params, 128, replace=False):
+            v, ch = divmod(int(idx), 3)
+            num = fd(which, int(idx))
+            assert abs(num - an[v, ch]) <= 1e-4 * max(abs(an[v, ch]), 1e-3 * scale) + 1e-9
     for ch in range(3):
         num = fd("l", ch)
         assert abs(num - dl[ch]) <= 1e-4 * max(abs(dl[ch]), 1e-3 * np.abs(dl).max())

@@ -739,7 +739,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--bins", type=int, default=16)
-    ap.add_argument("--schedule", default="static", choices=["static", "dynamic", "hardware"])
+    ap.add_argument("--schedule", default="hardware", choices=["static", "dynamic", "hardware"],
+                    help="tile schedule of the heightfield line (hardware: one CTA per tile, the fastest "
+                         "of the bin-size x schedule sweep at 16x16)")
     ap.add_argument("--threads", type=int, default=0, help="Process CTA size (0: library default)")
     ap.add_argument("--small-px", type=int, default=0,
                     help="largest box (pixels inside a tile) one thread rasterizes; larger boxes take a warp "

@@ -28,7 +28,9 @@ import torch
 from .raster import DeviceScene, Rasterizer
 
 DEFAULT_BINS: Tuple[Tuple[int, int], ...] = ((8, 8), (16, 16), (32, 32), (64, 64))
-DEFAULT_SCHEDULES: Tuple[str, ...] = ("static", "dynamic")
+DEFAULT_SCHEDULES: Tuple[str, ...] = ("static", "dynamic", "hardware")
+# a batch has no hardware mapping (its tiles are dealt inside one persistent launch)
+BATCH_SCHEDULES: Tuple[str, ...] = ("static", "dynamic")
 
 
 def features(scene: DeviceScene) -> str:
@@ -117,7 +119,7 @@ class Autotuner:
         """Per-scene (bin sizes, schedules) for forward_batch, measured in the
         batched pass.  Returns (bins, schedules, report)."""
         n = len(scenes)
-        cands = [((bw, bh), sc) for bw, bh in self.bins for sc in self.schedules]
+        cands = [((bw, bh), sc) for bw, bh in self.bins for sc in self.schedules if sc in BATCH_SCHEDULES]
         r = Rasterizer(64, 64)
         try:
             uniform = []

@@ -19,6 +19,7 @@ __global__ void __launch_bounds__(256) k_vertex(int W, int H, int V, const float
                                                 const float* __restrict__ mvp, int4* __restrict__ vtx,
                                                 const float* __restrict__ normal, const float* __restrict__ light,
                                                 float* __restrict__ vdot) {
+  pdl_launch_dependents();  // the count pass may be scheduled; it waits for this grid before reading
   __shared__ float m[16];
   const bool has_m = mvp != nullptr;
   if (has_m) {
@@ -147,6 +148,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(int nbins, unsigned* __re
                                                        unsigned long long capacity, DevStatus* st,
                                                        unsigned long long* __restrict__ chunk_state, unsigned epoch) {
   __shared__ ScanSmem sm;
+  pdl_wait();  // counts and the ticket reset of the count pass
+  pdl_launch_dependents();
   if (threadIdx.x == 0) sm.chunk = (int)atomicAdd(&st->scan_ticket, 1u);
   __syncthreads();
   const int chunk = sm.chunk;
@@ -251,7 +254,11 @@ __global__ void __launch_bounds__(256) k_setup_count(RasterGeom g, int T, const 
                                                      int stats) {
   __shared__ __align__(16) int sbuf[8][2][96];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  // the vertex stage does not touch the status word, and everything before
+  // it has completed (it is launched without the early-start attribute)
   if (blockIdx.x == 0 && threadIdx.x == 0) st->scan_ticket = 0u;  // the scan runs after this kernel
+  pdl_wait();  // snapped vertices
+  pdl_launch_dependents();
   const unsigned lt_mask = (1u << lane) - 1u;
   const int step = gridDim.x * (blockDim.x >> 5) * 32;
   // two batches of 32 triangles per iteration: both batches' loads are issued
@@ -286,13 +293,13 @@ void launch_setup_count(const RasterGeom& g, int T, const int* tris, int V, cons
   int blocks = (warps + 7) / 8;
   blocks = blocks < num_sms * per_sm ? blocks : num_sms * per_sm;
   if (blocks < 1) blocks = 1;  // with no triangles the kernel still resets the scan ticket
-  k_setup_count<<<blocks, 256, 0, s>>>(g, T, tris, V, vtx, rect, bin_count, g.nbx * g.nby, st, stats);
+  launch_pdl(k_setup_count, blocks, 256, 0, s, g, T, tris, V, vtx, rect, bin_count, g.nbx * g.nby, st, stats);
 }
 
 void launch_scan(int nbins, unsigned* bin_count, unsigned* bin_off, unsigned* cursor, unsigned long long capacity,
                  DevStatus* st, unsigned long long* chunk_state, unsigned epoch, cudaStream_t s) {
-  k_scan<<<scan_chunks(nbins), SCAN_THREADS, 0, s>>>(nbins, bin_count, bin_off, cursor, capacity, st, chunk_state,
-                                                     epoch);
+  launch_pdl(k_scan, scan_chunks(nbins), SCAN_THREADS, 0, s, nbins, bin_count, bin_off, cursor, capacity, st,
+             chunk_state, epoch);
 }
 
 // ======================================================================
@@ -337,6 +344,8 @@ __global__ void __launch_bounds__(256) k_scatter(RasterGeom g, int T, const BinR
                                                  const unsigned* __restrict__ bin_off,
                                                  unsigned* __restrict__ cursor, unsigned* __restrict__ bin_tris,
                                                  unsigned long long capacity, const DevStatus* st) {
+  pdl_wait();  // offsets, cursors and the status of the scan
+  pdl_launch_dependents();
   if (st->flags & STATUS_SKIP_MASK) return;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int step = gridDim.x * (blockDim.x >> 5) * 32;
@@ -361,7 +370,7 @@ void launch_scatter(const RasterGeom& g, int T, const BinRect* rect, const unsig
   int warps = (T + 31) / 32;
   int blocks = (warps + 7) / 8;
   blocks = blocks < num_sms * per_sm ? blocks : num_sms * per_sm;
-  k_scatter<<<blocks, 256, 0, s>>>(g, T, rect, bin_off, cursor, bin_tris, capacity, st);
+  launch_pdl(k_scatter, blocks, 256, 0, s, g, T, rect, bin_off, cursor, bin_tris, capacity, st);
 }
 
 }  // namespace piko

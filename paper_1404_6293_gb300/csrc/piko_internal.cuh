@@ -20,6 +20,31 @@ constexpr unsigned long long KEY_EMPTY = 0xFFFFFFFFFFFFFFFFull;
 constexpr unsigned FULL_MASK = 0xFFFFFFFFu;
 
 // Device-side status word, one per handle.
+// Programmatic dependent launch (sm_90+).  A kernel launched with
+// launch_pdl may start while the kernel before it in the stream is still
+// running; it must call pdl_wait() before it reads anything that kernel (or
+// an earlier one) writes.  pdl_launch_dependents() lets the next kernel's
+// CTAs be scheduled once every CTA of this grid has issued it.  Both are
+// no-ops for kernels launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr.val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+
 struct DevStatus {
   unsigned int flags;           // bit c set when PIKO_ERR c was recorded
   unsigned int first_code;      // first PIKO_ERR_* recorded (0 = none)

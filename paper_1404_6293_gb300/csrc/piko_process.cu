@@ -50,14 +50,15 @@ __global__ void __maxnreg__(PIKO_PROCESS_MAXNREG) k_process(ProcessParams p) {
   sm.sbig = reinterpret_cast<int*>(smem + bin_px);
   sm.srec = sm.sbig + nt * BIG_REC;
   sm.s_nbig = &s_nbig;
-  if (p.st->flags & STATUS_SKIP_MASK) return;
   const TileScene sc = scene_of(p);
   float L0 = 0.f, L1 = 0.f, L2 = 0.f;
   if (p.mode == PIKO_SHADE_LAMBERT) {
     L0 = __ldg(p.light); L1 = __ldg(p.light + 1); L2 = __ldg(p.light + 2);
   }
-  constexpr bool dynamic = SCHED == PIKO_SCHED_DYNAMIC;
   for (int i = tid; i < bin_px; i += nt) sm.skey[i] = KEY_EMPTY;
+  pdl_wait();  // bin lists and status of the scatter pass
+  if (p.st->flags & STATUS_SKIP_MASK) return;
+  constexpr bool dynamic = SCHED == PIKO_SCHED_DYNAMIC;
   if (tid == 0) {
     s_nbig = 0u;
     if (dynamic) s_tile[0] = (int)atomicAdd(&p.st->queue_head, 1u);
@@ -135,8 +136,8 @@ cudaError_t launch_process(const ProcessParams& p0, int threads, int grid, cudaS
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k<<<grid, threads, smem, s>>>(p);
-  return cudaGetLastError();
+  const cudaError_t e = launch_pdl(k, grid, threads, smem, s, p);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace piko

@@ -353,21 +353,23 @@ def run_ours(args):
         # frames alternate over two handles and two streams, so frame k+1's
         # host-to-device copy runs while frame k renders and copies back; every
         # frame still copies all its inputs in and its key and RGBA out
-        r2 = Rasterizer(scene.width, scene.height, args.bins, args.bins, args.schedule)
-        if args.threads:
-            r2.set_option(L.PIKO_OPT_THREADS_PER_TILE, args.threads)
-        ds2 = DeviceScene.from_host(scene)
-        fb2 = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode)
-        r2.forward(ds2, fb2)
-        if r2.status()[0] != 0:
-            raise RuntimeError("status error sizing the second handle")
-        r2.set_option(L.PIKO_OPT_CHECK_CAPACITY, 0)
-        lanes = [(r, ds, fb, key_h, rgba_h),
-                 (r2, ds2, fb2, torch.empty_like(key_h).pin_memory(), torch.empty_like(rgba_h).pin_memory())]
-        side = [torch.cuda.Stream(), torch.cuda.Stream()]
-        for k in range(6):
-            rr, d, f, kh, rh = lanes[k % 2]
-            rr.render_from_host(host_in, d, f, kh, rh, stream=side[k % 2])
+        nl = max(2, args.e2e_lanes)
+        lanes = [(r, ds, fb, key_h, rgba_h)]
+        for _ in range(nl - 1):
+            rr = Rasterizer(scene.width, scene.height, args.bins, args.bins, args.schedule)
+            if args.threads:
+                rr.set_option(L.PIKO_OPT_THREADS_PER_TILE, args.threads)
+            d = DeviceScene.from_host(scene)
+            f = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode)
+            rr.forward(d, f)
+            if rr.status()[0] != 0:
+                raise RuntimeError("status error sizing an end-to-end handle")
+            rr.set_option(L.PIKO_OPT_CHECK_CAPACITY, 0)
+            lanes.append((rr, d, f, torch.empty_like(key_h).pin_memory(), torch.empty_like(rgba_h).pin_memory()))
+        side = [torch.cuda.Stream() for _ in range(nl)]
+        for k in range(3 * nl):
+            rr, d, f, kh, rh = lanes[k % nl]
+            rr.render_from_host(host_in, d, f, kh, rh, stream=side[k % nl])
         barrier()
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -375,8 +377,8 @@ def run_ours(args):
         for sd in side:
             sd.wait_stream(stream)
         for k in range(Ke):
-            rr, d, f, kh, rh = lanes[k % 2]
-            rr.render_from_host(host_in, d, f, kh, rh, stream=side[k % 2])
+            rr, d, f, kh, rh = lanes[k % nl]
+            rr.render_from_host(host_in, d, f, kh, rh, stream=side[k % nl])
         for sd in side:
             stream.wait_stream(sd)
         e1.record(stream)
@@ -385,13 +387,14 @@ def run_ours(args):
         e2e = {"value": job_throughput(T, world, e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e_ms, "steps": Ke,
                "how": "Rasterizer.render_from_host per frame: pinned host -> device copies of every input, "
-                      "forward, device -> host copies of key and RGBA; frames alternate over two handles and "
-                      "two streams so copies overlap the other frame's work",
+                      f"forward, device -> host copies of key and RGBA; frames rotate over {nl} handles and "
+                      f"{nl} streams so copies overlap the other frames' work",
                "sequential": {"value": job_throughput(T, world, seq_ms), "ms_per_step": seq_ms,
                               "how": "one frame at a time on one stream, L2 flushed between frames"}}
-        if r.status()[0] != 0 or r2.status()[0] != 0:
+        if any(ln[0].status()[0] != 0 for ln in lanes):
             raise RuntimeError("status error after the end-to-end loop")
-        r2.close()
+        for ln in lanes[1:]:
+            ln[0].close()
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -768,6 +771,7 @@ def main():
                     help="heightfield: the headline line; the others measure further rows of the path")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-lanes", type=int, default=3, help="handles/streams the end-to-end frames rotate over")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     args = ap.parse_args()

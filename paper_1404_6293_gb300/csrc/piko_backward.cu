@@ -10,7 +10,7 @@ struct BackwardParams {
   int ntx, ntiles;
 };
 
-__global__ void __launch_bounds__(BWD_THREADS, 4) k_backward(BackwardParams p) {
+__global__ void __launch_bounds__(BWD_THREADS, 1024 / BWD_THREADS) k_backward(BackwardParams p) {
   extern __shared__ __align__(16) unsigned char bwd_smem_raw[];
   BwdSmem& sm = *reinterpret_cast<BwdSmem*>(bwd_smem_raw);
   float L0 = 0.f, L1 = 0.f, L2 = 0.f;
@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 4) k_backward(BackwardParams p) {
   __syncthreads();
   for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
     const int ty = tile / p.ntx, tx = tile - ty * p.ntx;
-    backward_tile(p.sc, tx * BWD_TILE, ty * BWD_TILE, sm, L0, L1, L2, gl0, gl1, gl2);
+    backward_tile(p.sc, tx * BWD_TILE_W, ty * BWD_TILE_H, sm, L0, L1, L2, gl0, gl1, gl2);
   }
   if (p.sc.dlight && p.sc.mode == PIKO_SHADE_LAMBERT) bwd_flush_light(sm, p.sc.dlight, gl0, gl1, gl2);
 }
@@ -48,9 +48,11 @@ struct PixelBwdParams {
 };
 
 
-__global__ void __launch_bounds__(BWD_THREADS) k_backward_pixel(PixelBwdParams p) {
-  __shared__ float sval[BWD_THREADS / 32][BWD_VALS][32];
-  __shared__ float sred[BWD_THREADS / 32][3];
+constexpr int PIX_THREADS = 256;
+
+__global__ void __launch_bounds__(PIX_THREADS) k_backward_pixel(PixelBwdParams p) {
+  __shared__ float sval[PIX_THREADS / 32][BWD_VALS][32];
+  __shared__ float sred[PIX_THREADS / 32][3];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
   float L0 = 0.f, L1 = 0.f, L2 = 0.f;
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(BWD_THREADS) k_backward_pixel(PixelBwdParams p
     __syncthreads();
     if (threadIdx.x < 3) {
       float acc = 0.f;
-      for (int w = 0; w < BWD_THREADS / 32; ++w) acc += sred[w][threadIdx.x];
+      for (int w = 0; w < PIX_THREADS / 32; ++w) acc += sred[w][threadIdx.x];
       atomicAdd(p.dlight + threadIdx.x, acc);
     }
   }
@@ -213,10 +215,10 @@ int piko_backward_launch(int W, int H, int mode, int unclamped, int T, int V, co
     p.tris = tris; p.vtx = vtx; p.color = color; p.normal = normal; p.light = light;
     p.key = key; p.dl_drgba = reinterpret_cast<const float4*>(dl_drgba);
     p.dcolor = dcolor; p.dnormal = dnormal; p.dlight = dlight;
-    long long blocks = (npix + BWD_THREADS - 1) / BWD_THREADS;
+    long long blocks = (npix + PIX_THREADS - 1) / PIX_THREADS;
     if (blocks > (long long)num_sms * 4) blocks = (long long)num_sms * 4;
     if (blocks < 1) blocks = 1;
-    k_backward_pixel<<<(int)blocks, BWD_THREADS, 0, s>>>(p);
+    k_backward_pixel<<<(int)blocks, PIX_THREADS, 0, s>>>(p);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
   }
   BackwardParams p;
@@ -225,8 +227,8 @@ int piko_backward_launch(int W, int H, int mode, int unclamped, int T, int V, co
   c.tris = tris; c.vtx = vtx; c.color = color; c.normal = normal; c.light = light;
   c.key = key; c.dl = reinterpret_cast<const float4*>(dl_drgba);
   c.dcolor = dcolor; c.dnormal = dnormal; c.dlight = dlight;
-  p.ntx = (W + BWD_TILE - 1) / BWD_TILE;
-  p.ntiles = p.ntx * ((H + BWD_TILE - 1) / BWD_TILE);
+  p.ntx = (W + BWD_TILE_W - 1) / BWD_TILE_W;
+  p.ntiles = p.ntx * ((H + BWD_TILE_H - 1) / BWD_TILE_H);
   const int blocks = backward_grid(p.ntiles, num_sms);
   k_backward<<<blocks, BWD_THREADS, sizeof(BwdSmem), s>>>(p);
   return cudaGetLastError() == cudaSuccess ? 0 : 1;

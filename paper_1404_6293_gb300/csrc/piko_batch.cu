@@ -445,7 +445,7 @@ struct BatchBwdParams {
   const int4* vtx;
 };
 
-__global__ void __launch_bounds__(BWD_THREADS, 4) k_batch_backward(BatchBwdParams b) {
+__global__ void __launch_bounds__(BWD_THREADS, 1024 / BWD_THREADS) k_batch_backward(BatchBwdParams b) {
   extern __shared__ __align__(16) unsigned char bwd_smem_raw[];
   BwdSmem& sm = *reinterpret_cast<BwdSmem*>(bwd_smem_raw);
   __shared__ int s_scene;
@@ -468,9 +468,9 @@ __global__ void __launch_bounds__(BWD_THREADS, 4) k_batch_backward(BatchBwdParam
       L0 = __ldg(c.light); L1 = __ldg(c.light + 1); L2 = __ldg(c.light + 2);
     }
     const int lt = i - __ldg(b.btile_prefix + s);
-    const int ntx = (c.W + BWD_TILE - 1) / BWD_TILE;
+    const int ntx = (c.W + BWD_TILE_W - 1) / BWD_TILE_W;
     const int ty = lt / ntx, tx = lt - ty * ntx;
-    backward_tile(c, tx * BWD_TILE, ty * BWD_TILE, sm, L0, L1, L2, gl0, gl1, gl2);
+    backward_tile(c, tx * BWD_TILE_W, ty * BWD_TILE_H, sm, L0, L1, L2, gl0, gl1, gl2);
     if (c.dlight && c.mode == PIKO_SHADE_LAMBERT) bwd_flush_light(sm, c.dlight, gl0, gl1, gl2);
   }
 }
@@ -622,7 +622,7 @@ int batch_prepare(BatchState*& bs, int num_sms, const piko_scene* scenes, int n,
     const int ntiles = x.g.nbx * x.g.nby;
     pv[i] = (int)tv; pt[i] = (int)tt; pb[i] = (int)tb; ps[i] = (int)tsd; pd[i] = (int)tdy; pp[i] = (int)tp;
     tv += x.V; tt += x.T; tb += ntiles;
-    tp += (long long)((s.width + BWD_TILE - 1) / BWD_TILE) * ((s.height + BWD_TILE - 1) / BWD_TILE);
+    tp += (long long)((s.width + BWD_TILE_W - 1) / BWD_TILE_W) * ((s.height + BWD_TILE_H - 1) / BWD_TILE_H);
     if (sched == PIKO_SCHED_STATIC) tsd += ntiles;
     else tdy += ntiles;
     if (bw * bh > max_bin_px) max_bin_px = bw * bh;

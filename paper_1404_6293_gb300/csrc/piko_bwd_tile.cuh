@@ -10,7 +10,7 @@
 //   dL/dn_i += (g . albedo) b_i L   when s > 0 (or unclamped)
 //   dL/dL   += (g . albedo) n
 //
-// One CTA of 256 threads takes a 16 x 16 tile, one pixel per thread:
+// One CTA of BWD_THREADS threads takes a 16-pixel-wide tile, one pixel per thread:
 //  1. the distinct winning triangles of the tile go into a shared hash table
 //     (one insert per group of lanes with the same triangle);
 //  2. the table is compacted into slots and each slot's triangle is set up
@@ -29,9 +29,13 @@
 
 namespace piko {
 
-constexpr int BWD_TILE = 16;
-constexpr int BWD_THREADS = BWD_TILE * BWD_TILE;
-constexpr int BWD_HASH_BITS = 9;
+#ifndef PIKO_BWD_TILE_H
+#define PIKO_BWD_TILE_H 16
+#endif
+constexpr int BWD_TILE_W = 16;               // pixels per tile row (a warp covers two rows)
+constexpr int BWD_TILE_H = PIKO_BWD_TILE_H;  // rows per tile
+constexpr int BWD_THREADS = BWD_TILE_W * BWD_TILE_H;
+constexpr int BWD_HASH_BITS = BWD_THREADS > 128 ? 9 : 8;
 constexpr int BWD_HASH = 1 << BWD_HASH_BITS;  // twice the most distinct triangles a tile can hold
 constexpr int BWD_VALS = 18;                  // 3 vertices x (3 colour + 3 normal)
 constexpr unsigned BWD_NONE = 0xFFFFFFFFu;
@@ -116,7 +120,7 @@ __device__ __forceinline__ void bwd_add_term(const BwdScene& sc, const int* r, i
 __device__ __forceinline__ void backward_tile(const BwdScene& sc, int x0, int y0, BwdSmem& sm, float L0, float L1,
                                               float L2, float& gl0, float& gl1, float& gl2) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int x = x0 + (tid & (BWD_TILE - 1)), y = y0 + (tid >> 4);  // a warp covers 16 x 2 pixels
+  const int x = x0 + (tid & (BWD_TILE_W - 1)), y = y0 + tid / BWD_TILE_W;  // a warp covers 16 x 2 pixels
   const bool inside = x < sc.W && y < sc.H;
   const size_t o = (size_t)y * sc.W + x;
   unsigned t = BWD_NONE;

@@ -136,7 +136,9 @@ void piko_raster_destroy(piko_raster *h);
  * PIKO_OPT_CHECK_CAPACITY is 1 (the default), which adds one host sync
  * after the scan.  Returns PIKO_ERR_INVALID_ARG for bad sizes, NULL
  * required pointers, misaligned pos/tris, or a shade mode without the
- * attributes it needs. */
+ * attributes it needs.  The stages after the vertex stage are launched with
+ * programmatic dependent launch: each may start while the one before it
+ * drains and waits on the device before reading that stage's output. */
 int piko_raster_forward(piko_raster *h, const piko_scene *scene, piko_framebuffer *fb,
                         void *cuda_stream);
 
@@ -180,8 +182,10 @@ int piko_raster_deferred_light(piko_raster *h, const piko_framebuffer *gbuf, con
  *               round robin over the persistent CTAs) or PIKO_SCHED_DYNAMIC
  *               (taken from a shared queue after the static tiles; HARDWARE
  *               is treated as DYNAMIC), or NULL for the handle's schedule.
- * Results are bit-identical to n piko_raster_forward calls with the same
- * bin sizes.  With PIKO_OPT_CHECK_CAPACITY = 1 the call waits for the
+ * Keys are bit-identical to n piko_raster_forward calls with the same bin
+ * sizes; colours agree with them within float32 rounding (a winner is
+ * shaded from its tile's shared-memory record or, past the records a tile
+ * holds, from global memory).  With PIKO_OPT_CHECK_CAPACITY = 1 the call waits for the
  * launch, and relaunches once with larger bin lists if they overflowed; with
  * 0 it never waits (so it can be captured in a CUDA graph after a first call
  * with the same scenes, or piko_raster_reserve, has sized the scratch) and

@@ -421,6 +421,46 @@ def test_sphere_views_backward_accumulates_over_views():
     _grad_check(light.grad.cpu().numpy(), dl_ref)
 
 
+def test_sphere_views_as_one_batch_share_gradients():
+    """The multi-view form the sphere workload is measured in: all views in
+    one forward_batch / backward_batch, every view accumulating into the same
+    mesh gradients; against the oracle summed over the views."""
+    torch = _torch()
+    import dataclasses
+    from paper_1404_6293_gb300.raster import DeviceScene, Framebuffer, Rasterizer
+    nv, W = 6, 128
+    sph, mvps = S.sphere_views(num_views=nv, width=W, height=W, slices=60, stacks=40)
+    ds = DeviceScene.from_host(sph)
+    mv = torch.from_numpy(mvps).cuda()
+    views = [dataclasses.replace(ds, mvp=mv[v]) for v in range(nv)]
+    r = Rasterizer(64, 64)
+    fbs = r.forward_batch(views, None, [(16, 16)] * nv, ["dynamic", "static"] * (nv // 2))
+    torch.cuda.synchronize()
+    assert r.status()[0] == 0
+    tgt = S.target_image(W, W, seed=19, views=nv)
+    dc = torch.zeros_like(ds.color)
+    dn = torch.zeros_like(ds.normal)
+    dl = torch.zeros_like(ds.light_dir)
+    dc_ref = np.zeros((sph.num_vertices, 3))
+    dn_ref = np.zeros((sph.num_vertices, 3))
+    dl_ref = np.zeros(3)
+    gs = []
+    for v in range(nv):
+        sv = S.Scene(W, W, sph.pos, sph.tris, color=sph.color, normal=sph.normal, mvp=mvps[v],
+                     light_dir=sph.light_dir, shade_mode=sph.shade_mode)
+        ref_key, _ = oracle.raster_bbox(sv)
+        assert_keys_equal(fbs[v].key_numpy(), ref_key, f"view {v}")
+        g = np.zeros((W, W, 4))
+        g[..., :3] = 2.0 * (oracle.shade(sv, ref_key)[..., :3] - tgt[v][..., :3])
+        oracle.backward(sv, ref_key, g, out=(dc_ref, dn_ref, dl_ref))
+        gs.append(torch.from_numpy(g.astype(np.float32)).cuda())
+    r.backward_batch(views, fbs, gs, [dc] * nv, [dn] * nv, [dl] * nv)
+    torch.cuda.synchronize()
+    _grad_check(dc.cpu().numpy(), dc_ref)
+    _grad_check(dn.cpu().numpy(), dn_ref)
+    _grad_check(dl.cpu().numpy(), dl_ref)
+
+
 # --------------------------------------------------------------- batches
 def _batch_scenes(n, seed=0, small=True):
     rng = np.random.default_rng(seed)

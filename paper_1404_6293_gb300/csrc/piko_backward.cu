@@ -49,9 +49,10 @@ struct PixelBwdParams {
 
 
 constexpr int PIX_THREADS = 256;
+constexpr int PIX_VALS = 18;  // per pixel: 3 vertices x (3 colour + 3 normal)
 
 __global__ void __launch_bounds__(PIX_THREADS) k_backward_pixel(PixelBwdParams p) {
-  __shared__ float sval[PIX_THREADS / 32][BWD_VALS][32];
+  __shared__ float sval[PIX_THREADS / 32][PIX_VALS][32];
   __shared__ float sred[PIX_THREADS / 32][3];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -78,9 +79,9 @@ __global__ void __launch_bounds__(PIX_THREADS) k_backward_pixel(PixelBwdParams p
       hit = ia >= 0 && ia < p.V && ib >= 0 && ib < p.V && ic >= 0 && ic < p.V && setup_triangle(ia, ib, ic, p.vtx, s);
       if (!hit) t = 0xFFFFFFFFu;
     }
-    float v[BWD_VALS];
+    float v[PIX_VALS];
 #pragma unroll
-    for (int q = 0; q < BWD_VALS; ++q) v[q] = 0.f;
+    for (int q = 0; q < PIX_VALS; ++q) v[q] = 0.f;
     int vid[3] = {0, 0, 0};
     if (hit) {
       const int y = i / p.W, x = i - y * p.W;
@@ -134,7 +135,7 @@ __global__ void __launch_bounds__(PIX_THREADS) k_backward_pixel(PixelBwdParams p
     const bool alone = __popc(grp) == 1;
     if (!alone) {
 #pragma unroll
-      for (int q = 0; q < BWD_VALS; ++q) sval[warp][q][lane] = v[q];
+      for (int q = 0; q < PIX_VALS; ++q) sval[warp][q][lane] = v[q];
     }
     __syncwarp();
     if (leader) {
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(PIX_THREADS) k_backward_pixel(PixelBwdParams p
           const int src = __ffs(rest) - 1;
           rest &= rest - 1;
 #pragma unroll
-          for (int q = 0; q < BWD_VALS; ++q) v[q] += sval[warp][q][src];
+          for (int q = 0; q < PIX_VALS; ++q) v[q] += sval[warp][q][src];
         }
       }
 #pragma unroll

@@ -15,12 +15,13 @@
 //     (one insert per group of lanes with the same triangle);
 //  2. the table is compacted into slots and each slot's triangle is set up
 //     once (vertex indices, snapped positions, 2 x area);
-//  3. every pixel computes its 18 vertex-gradient terms from its slot's
-//     setup; the lanes of a warp that share a slot are summed, one lane per
-//     term, into the slot's shared accumulators;
-//  4. each slot then issues its 18 global atomics.
+//  3. every pixel computes its 12 terms (below) from its slot's setup; the
+//     lanes of a warp that share a slot are summed, one lane per term, into
+//     the slot's shared accumulators;
+//  4. each slot then issues its gradient atomics (9 colour, 9 normal) and
+//     adds its share of the light gradient.
 // So the setup runs once per (tile, visible triangle) and the global atomics
-// number 18 per (tile, visible triangle) instead of per pixel.  Tiles of
+// number 18 per (tile, visible triangle) instead of per pixel group.  Tiles of
 // tiny triangles (more than BWD_DIRECT_SLOTS of them) add their terms to the
 // gradients directly, per pixel or per group of lanes.
 #pragma once
@@ -37,13 +38,19 @@ constexpr int BWD_TILE_H = PIKO_BWD_TILE_H;  // rows per tile
 constexpr int BWD_THREADS = BWD_TILE_W * BWD_TILE_H;
 constexpr int BWD_HASH_BITS = BWD_THREADS > 128 ? 9 : 8;
 constexpr int BWD_HASH = 1 << BWD_HASH_BITS;  // twice the most distinct triangles a tile can hold
-constexpr int BWD_VALS = 18;                  // 3 vertices x (3 colour + 3 normal)
+// Terms per pixel: q = 3 j + c (c < 3) is g_c s b_j, the colour gradient of
+// vertex j (g_c b_j for Gouraud); q = 9 + j is G b_j with G = g . albedo
+// (0 where the clamp is inactive).  The normal and light gradients are
+// linear in the G b_j sums: dL/dn_j = L sum(G b_j) and dL/dL = sum_j n_j
+// sum(G b_j), so they are formed once per slot from the sums.
+constexpr int BWD_VALS = 12;
 constexpr unsigned BWD_NONE = 0xFFFFFFFFu;
 
 // per-slot words: oriented X0 Y0 X1 Y1 X2 Y2, vertex ids v0 v1 v2, A (lo, hi),
-// the triangle id (replaced by 1/A once the slot is set up) and a valid flag;
-// 13 words (odd: distinct slots fall in distinct banks)
-constexpr int RB_V = 6, RB_ALO = 9, RB_AHI = 10, RB_T = 11, RB_OK = 12, BWD_REC = 13;
+// the triangle id (replaced by 1/A once the slot is set up), a valid flag and
+// n_j . L of the three vertices (Lambert); 17 words (odd: distinct slots fall
+// in distinct banks)
+constexpr int RB_V = 6, RB_ALO = 9, RB_AHI = 10, RB_T = 11, RB_OK = 12, RB_VD = 13, BWD_REC = 17;
 
 struct BwdScene {
   int W, H, mode, unclamped, T, V;
@@ -100,19 +107,29 @@ __device__ __forceinline__ void bwd_flush_light(BwdSmem& sm, float* dlight, floa
   __syncthreads();
 }
 
-// Adds term q (vertex q / 6; colour for q % 6 < 3, else normal) of slot
-// record r to the scene's gradient arrays.
+// Adds term q of slot record r to the scene's gradients: a colour term goes
+// to dL/dc of its vertex; a G b_j sum goes to dL/dn_j (times L) and, when
+// `light` is set, to this thread's share of dL/dL (times n_j).
 __device__ __forceinline__ void bwd_add_term(const BwdScene& sc, const int* r, int q, float val, bool has_c,
-                                             bool has_n) {
-  const int j = q / 6, c = q - 6 * j;
-  const size_t vb = 3 * (size_t)r[RB_V + j];
-  if (c < 3) {
-    if (has_c) atomicAdd(sc.dcolor + vb + c, val);
-  } else if (has_n) {
-    atomicAdd(sc.dnormal + vb + (c - 3), val);
+                                             bool has_n, bool light, float L0, float L1, float L2, float& gl0,
+                                             float& gl1, float& gl2) {
+  if (q < 9) {
+    const int j = q / 3, c = q - 3 * j;
+    if (has_c) atomicAdd(sc.dcolor + 3 * (size_t)r[RB_V + j] + c, val);
+    return;
+  }
+  const size_t vb = 3 * (size_t)r[RB_V + (q - 9)];
+  if (has_n) {
+    atomicAdd(sc.dnormal + vb, val * L0);
+    atomicAdd(sc.dnormal + vb + 1, val * L1);
+    atomicAdd(sc.dnormal + vb + 2, val * L2);
+  }
+  if (light) {
+    gl0 += val * __ldg(sc.normal + vb);
+    gl1 += val * __ldg(sc.normal + vb + 1);
+    gl2 += val * __ldg(sc.normal + vb + 2);
   }
 }
-
 
 // One tile with its top-left pixel (x0, y0).  Entered and left with a clear
 // hash table (bwd_clear once per CTA before the first tile); blockDim.x must
@@ -173,6 +190,14 @@ __device__ __forceinline__ void backward_tile(const BwdScene& sc, int x0, int y0
       r[RB_ALO] = (int)(unsigned)(ts.A & 0xFFFFFFFFll);
       r[RB_AHI] = (int)(ts.A >> 32);
       r[RB_T] = __float_as_int(__frcp_rn((float)ts.A));
+      if (sc.mode == PIKO_SHADE_LAMBERT) {
+        const int vid[3] = {ts.v0, ts.v1, ts.v2};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const float* nn = sc.normal + 3 * (size_t)vid[j];
+          r[RB_VD + j] = __float_as_int(__ldg(nn) * L0 + __ldg(nn + 1) * L1 + __ldg(nn + 2) * L2);
+        }
+      }
     }
     if (!direct) {
       float* a = sm.acc + s * BWD_VALS;
@@ -204,7 +229,7 @@ __device__ __forceinline__ void backward_tile(const BwdScene& sc, int x0, int y0
     if (sc.mode == PIKO_SHADE_GOURAUD) {
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        v[6 * j + 0] = g.x * b[j]; v[6 * j + 1] = g.y * b[j]; v[6 * j + 2] = g.z * b[j];
+        v[3 * j] = g.x * b[j]; v[3 * j + 1] = g.y * b[j]; v[3 * j + 2] = g.z * b[j];
       }
     } else {
       float a0 = 0.80f, a1 = 0.75f, a2 = 0.65f;  // material of Listing 1 without colours
@@ -216,28 +241,24 @@ __device__ __forceinline__ void backward_tile(const BwdScene& sc, int x0, int y0
           a0 += b[j] * __ldg(c); a1 += b[j] * __ldg(c + 1); a2 += b[j] * __ldg(c + 2);
         }
       }
-      float n0 = 0.f, n1 = 0.f, n2 = 0.f;
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const float* nn = sc.normal + 3 * (size_t)vid[j];
-        n0 += b[j] * __ldg(nn); n1 += b[j] * __ldg(nn + 1); n2 += b[j] * __ldg(nn + 2);
-      }
-      const float d = n0 * L0 + n1 * L1 + n2 * L2;
+      // n . L = sum_j b_j (n_j . L), by linearity
+      const float d = b[0] * __int_as_float(r[RB_VD]) + b[1] * __int_as_float(r[RB_VD + 1]) +
+                      b[2] * __int_as_float(r[RB_VD + 2]);
       const bool active = sc.unclamped || d > 0.f;
       const float sh = sc.unclamped ? d : fmaxf(d, 0.f);
       const float G = active ? (g.x * a0 + g.y * a1 + g.z * a2) : 0.f;
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         if (sc.color) {
-          v[6 * j + 0] = g.x * sh * b[j]; v[6 * j + 1] = g.y * sh * b[j]; v[6 * j + 2] = g.z * sh * b[j];
+          v[3 * j] = g.x * sh * b[j]; v[3 * j + 1] = g.y * sh * b[j]; v[3 * j + 2] = g.z * sh * b[j];
         }
-        v[6 * j + 3] = G * b[j] * L0; v[6 * j + 4] = G * b[j] * L1; v[6 * j + 5] = G * b[j] * L2;
+        v[9 + j] = G * b[j];
       }
-      gl0 += G * n0; gl1 += G * n1; gl2 += G * n2;
     }
   }
   const bool has_c = sc.dcolor != nullptr && (sc.mode == PIKO_SHADE_GOURAUD || sc.color != nullptr);
   const bool has_n = sc.dnormal != nullptr && sc.mode == PIKO_SHADE_LAMBERT;
+  const bool has_l = sc.dlight != nullptr && sc.mode == PIKO_SHADE_LAMBERT;
   // 4. Lanes of a group of at most two add their own terms (to the slot's
   // accumulators, or straight to the gradients in direct tiles).  Larger
   // groups are summed term by term first: lane q adds term q over the group.
@@ -247,7 +268,7 @@ __device__ __forceinline__ void backward_tile(const BwdScene& sc, int x0, int y0
       if (direct) {
 #pragma unroll
         for (int q = 0; q < BWD_VALS; ++q)
-          if (v[q] != 0.f) bwd_add_term(sc, r, q, v[q], has_c, has_n);
+          if (v[q] != 0.f) bwd_add_term(sc, r, q, v[q], has_c, has_n, has_l, L0, L1, L2, gl0, gl1, gl2);
       } else {
         float* a = sm.acc + slot * BWD_VALS;
 #pragma unroll
@@ -269,7 +290,8 @@ __device__ __forceinline__ void backward_tile(const BwdScene& sc, int x0, int y0
         float sum = 0.f;
         for (unsigned m = gm; m; m &= m - 1) sum += sm.stage[warp][lane][__ffs(m) - 1];
         if (direct) {
-          if (sum != 0.f) bwd_add_term(sc, sm.rec + gs * BWD_REC, lane, sum, has_c, has_n);
+          if (sum != 0.f)
+            bwd_add_term(sc, sm.rec + gs * BWD_REC, lane, sum, has_c, has_n, has_l, L0, L1, L2, gl0, gl1, gl2);
         } else {
           atomicAdd(sm.acc + gs * BWD_VALS + lane, sum);
         }
@@ -277,13 +299,13 @@ __device__ __forceinline__ void backward_tile(const BwdScene& sc, int x0, int y0
     }
   }
   __syncthreads();
-  // 5. one global atomic per (slot, term)
+  // 5. one set of gradient atomics per (slot, term)
   if (!direct) {
     for (int idx = tid; idx < nslot * BWD_VALS; idx += BWD_THREADS) {
       const int s = idx / BWD_VALS, q = idx - s * BWD_VALS;
       const int* rs = sm.rec + s * BWD_REC;
       const float val = sm.acc[idx];
-      if (rs[RB_OK] && val != 0.f) bwd_add_term(sc, rs, q, val, has_c, has_n);
+      if (rs[RB_OK] && val != 0.f) bwd_add_term(sc, rs, q, val, has_c, has_n, has_l, L0, L1, L2, gl0, gl1, gl2);
     }
     __syncthreads();
   }

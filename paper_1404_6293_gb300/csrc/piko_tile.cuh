@@ -132,6 +132,21 @@ __device__ __forceinline__ void key_min_large(unsigned long long* skey, int idx,
   key_store(skey, idx, depth_of(w1, w2, s, rA), tag);
 }
 
+// Depth for a covered sample of a triangle with A < 2^31: then w1, w2 >= 0
+// and w1 + w2 <= A fit 32 bits, so the quotient is estimated from float32
+// barycentrics (32-bit conversions only) and corrected exactly against the
+// 64-bit numerator w1 (Z1 - Z0) + w2 (Z2 - Z0).
+__device__ __forceinline__ void key_min_mid(unsigned long long* skey, int idx, int w1, int w2, const TriSetup& s,
+                                            float rA, unsigned long long tag) {
+  const int d1 = s.Z1 - s.Z0, d2 = s.Z2 - s.Z0;
+  const int A = (int)s.A;
+  int q = __float2int_rd((float)w1 * rA * (float)d1 + (float)w2 * rA * (float)d2);
+  long long r = (long long)w1 * d1 + (long long)w2 * d2 - (long long)q * A;
+  for (int it = 0; r < 0 && it < DIV_FIX_LIMIT; ++it) { --q; r += A; }
+  for (int it = 0; r >= A && it < DIV_FIX_LIMIT; ++it) { ++q; r -= A; }
+  key_store(skey, idx, (unsigned)(s.Z0 + q), tag);
+}
+
 // One thread walks the box of a small triangle inside the tile.  With I =
 // int the triangle's bounding box is below 2^15 in 16.8 units in both
 // directions, so every edge value inside the box is below 2^31 in magnitude
@@ -188,6 +203,7 @@ __device__ __forceinline__ unsigned raster_warp(const TriSetup& s, unsigned long
   const int bw = px1 - px0 + 1, n = bw * (py1 - py0 + 1);
   const int dy = 32 / bw, dx = 32 - dy * bw;
   int lx = lane % bw, ly = lane / bw;
+  const bool mid = s.A < (1LL << 31);  // the same for the whole warp
   unsigned frags = 0;
   for (int base = 0; base < n; base += 32) {
     const bool in_box = base + lane < n;
@@ -197,8 +213,13 @@ __device__ __forceinline__ unsigned raster_warp(const TriSetup& s, unsigned long
     const bool cov = in_box && (a0 | a1 | a2) >= 0;
     const unsigned m = __ballot_sync(FULL_MASK, cov);
     if (m != 0u) {
-      if (cov)
-        key_min_large(skey, ((py0 + ly - y0) << bshift_x) + (px0 + lx - x0), a1 + e.b1, a2 + e.b2, s, rA, tag);
+      if (cov) {
+        const int idx = ((py0 + ly - y0) << bshift_x) + (px0 + lx - x0);
+        if (mid)
+          key_min_mid(skey, idx, (int)(a1 + e.b1), (int)(a2 + e.b2), s, rA, tag);
+        else
+          key_min_large(skey, idx, a1 + e.b1, a2 + e.b2, s, rA, tag);
+      }
       frags += __popc(m);
     }
     lx += dx; ly += dy;

@@ -146,12 +146,6 @@ __device__ __forceinline__ long long floor_div_est128(__int128 n, long long A, f
   return q;
 }
 
-// floor(n / A) for 0 < A < 2^31 and |n / A| < 2^25: the same estimate and
-// exact fix-up with 32-bit quotient and divisor.
-__device__ __forceinline__ int floor_div_small(long long n, int A, float rA) {
-  int q = (int)floorf((float)n * rA);
-  long long r = n - (long long)q * A;
-  for (int it = 0; r < 0 && it < DIV_FIX_LIMIT; ++it) { --q; r += A; }
   for (int it = 0; r >= A && it < DIV_FIX_LIMIT; ++it) { ++q; r -= A; }
   return q;
 }

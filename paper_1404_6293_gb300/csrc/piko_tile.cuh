@@ -105,6 +105,21 @@ __device__ __forceinline__ void key_store(unsigned long long* skey, int idx, uns
   if (k < skey[idx]) atomicMin(skey + idx, k);
 }
 
+// Depth for a covered sample of a triangle with A < 2^31: then w1, w2 >= 0
+// and w1 + w2 <= A fit 32 bits, so the quotient is estimated from float32
+// barycentrics (32-bit conversions only) and corrected exactly against the
+// 64-bit numerator w1 (Z1 - Z0) + w2 (Z2 - Z0).
+__device__ __forceinline__ void key_min_mid(unsigned long long* skey, int idx, int w1, int w2, const TriSetup& s,
+                                            float rA, unsigned long long tag) {
+  const int d1 = s.Z1 - s.Z0, d2 = s.Z2 - s.Z0;
+  const int A = (int)s.A;
+  int q = __float2int_rd((float)w1 * rA * (float)d1 + (float)w2 * rA * (float)d2);
+  long long r = (long long)w1 * d1 + (long long)w2 * d2 - (long long)q * A;
+  for (int it = 0; r < 0 && it < DIV_FIX_LIMIT; ++it) { --q; r += A; }
+  for (int it = 0; r >= A && it < DIV_FIX_LIMIT; ++it) { ++q; r -= A; }
+  key_store(skey, idx, (unsigned)(s.Z0 + q), tag);
+}
+
 // Triangles whose bounding box is below 2^15 in 16.8 units: A < 2^30 and
 // w1, w2 < 2^31, so the depth numerator is two 32x32->64 products.  With
 // N32 the caller has checked A * (|Z1-Z0| + |Z2-Z0| + 8) < 2^31: the
@@ -122,8 +137,7 @@ __device__ __forceinline__ void key_min_small(unsigned long long* skey, int idx,
     for (int it = 0; r >= A && it < DIV_FIX_LIMIT; ++it) { ++q; r -= A; }
     key_store(skey, idx, (unsigned)(s.Z0 + q), tag);
   } else {
-    const long long n = (long long)w1 * (s.Z1 - s.Z0) + (long long)w2 * (s.Z2 - s.Z0);
-    key_store(skey, idx, (unsigned)(s.Z0 + floor_div_small(n, (int)s.A, rA)), tag);
+    key_min_mid(skey, idx, w1, w2, s, rA, tag);
   }
 }
 
@@ -132,20 +146,6 @@ __device__ __forceinline__ void key_min_large(unsigned long long* skey, int idx,
   key_store(skey, idx, depth_of(w1, w2, s, rA), tag);
 }
 
-// Depth for a covered sample of a triangle with A < 2^31: then w1, w2 >= 0
-// and w1 + w2 <= A fit 32 bits, so the quotient is estimated from float32
-// barycentrics (32-bit conversions only) and corrected exactly against the
-// 64-bit numerator w1 (Z1 - Z0) + w2 (Z2 - Z0).
-__device__ __forceinline__ void key_min_mid(unsigned long long* skey, int idx, int w1, int w2, const TriSetup& s,
-                                            float rA, unsigned long long tag) {
-  const int d1 = s.Z1 - s.Z0, d2 = s.Z2 - s.Z0;
-  const int A = (int)s.A;
-  int q = __float2int_rd((float)w1 * rA * (float)d1 + (float)w2 * rA * (float)d2);
-  long long r = (long long)w1 * d1 + (long long)w2 * d2 - (long long)q * A;
-  for (int it = 0; r < 0 && it < DIV_FIX_LIMIT; ++it) { --q; r += A; }
-  for (int it = 0; r >= A && it < DIV_FIX_LIMIT; ++it) { ++q; r -= A; }
-  key_store(skey, idx, (unsigned)(s.Z0 + q), tag);
-}
 
 // One thread walks the box of a small triangle inside the tile.  With I =
 // int the triangle's bounding box is below 2^15 in 16.8 units in both

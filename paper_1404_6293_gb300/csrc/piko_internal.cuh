@@ -146,9 +146,6 @@ __device__ __forceinline__ long long floor_div_est128(__int128 n, long long A, f
   return q;
 }
 
-  for (int it = 0; r >= A && it < DIV_FIX_LIMIT; ++it) { ++q; r -= A; }
-  return q;
-}
 
 // Approximate 1/a (a >= 1): only ever used as an estimate that integer
 // arithmetic corrects, or for float barycentrics.

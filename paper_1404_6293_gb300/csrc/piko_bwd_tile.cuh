@@ -147,8 +147,7 @@ __device__ __forceinline__ void backward_tile(const BwdScene& sc, int x0, int y0
     // cannot come from this scene's forward)
     if (k != KEY_EMPTY && (unsigned)k < (unsigned)sc.T) t = (unsigned)k;
   }
-  if (!__syncthreads_or(t != BWD_NONE)) return;  // nothing visible: the table stays clear
-  // 1. distinct triangles into the hash table
+  // 1. distinct triangles into the hash table (empty on entry)
   const unsigned grp = __match_any_sync(FULL_MASK, t);
   const int leader = __ffs(grp) - 1;
   int h = 0;
@@ -162,7 +161,9 @@ __device__ __forceinline__ void backward_tile(const BwdScene& sc, int x0, int y0
       h = (h + 1) & (BWD_HASH - 1);
     }
   }
-  __syncthreads();
+  // the inserts are complete after this barrier; with nothing visible the
+  // table stayed clear and the tile is done
+  if (!__syncthreads_or(t != BWD_NONE)) return;
   // 2. slots for the occupied entries; one setup per slot
   for (int e = tid; e < BWD_HASH; e += BWD_THREADS) {
     const unsigned key = sm.hkey[e];
@@ -299,7 +300,8 @@ __device__ __forceinline__ void backward_tile(const BwdScene& sc, int x0, int y0
     }
   }
   __syncthreads();
-  // 5. one set of gradient atomics per (slot, term)
+  // 5. one set of gradient atomics per (slot, term); the hash table (no
+  // longer read) is cleared for the next tile meanwhile
   if (!direct) {
     for (int idx = tid; idx < nslot * BWD_VALS; idx += BWD_THREADS) {
       const int s = idx / BWD_VALS, q = idx - s * BWD_VALS;
@@ -307,7 +309,6 @@ __device__ __forceinline__ void backward_tile(const BwdScene& sc, int x0, int y0
       const float val = sm.acc[idx];
       if (rs[RB_OK] && val != 0.f) bwd_add_term(sc, rs, q, val, has_c, has_n, has_l, L0, L1, L2, gl0, gl1, gl2);
     }
-    __syncthreads();
   }
   bwd_clear(sm);
   __syncthreads();

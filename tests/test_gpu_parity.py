@@ -281,6 +281,23 @@ def test_invalid_arguments_rejected_on_host():
         r.forward(ds)  # Gouraud without colours
 
 
+@pytest.mark.parametrize("W,H", [(32767, 3), (5, 32767)])
+def test_largest_framebuffer_sides(W, H):
+    """The widest and tallest framebuffers the 16.8 guard band allows
+    (32767 pixels: snapped coordinates just below 2^23), with triangles that
+    reach past the far edges; 32768 is rejected."""
+    from paper_1404_6293_gb300 import _lib as L
+    lib = L.load()
+    assert not lib.piko_raster_create(W + 1 if W == 32767 else W, H + 1 if H == 32767 else H, 16, 16, 0)
+    s = S.random_triangles(W, H, 400, 12.0, seed=90 + W)
+    ref, _ = oracle.raster_bbox(s)
+    assert (ref != EMPTY).any()
+    for bins, sched in (((8, 8), "static"), ((64, 64), "dynamic"), ((16, 16), "hardware")):
+        out = rasterize(s, *bins, sched)
+        assert out["status"] == 0
+        assert_keys_equal(out["key"], ref, f"{W}x{H} bins {bins} {sched}")
+
+
 def test_bin_size_and_schedule_never_change_output():
     s = S.random_triangles(300, 200, 3000, 15.0, seed=12)
     keys = []

@@ -398,7 +398,7 @@ def run_ours(args):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "int64", "data": "synthetic", "config": cfg, "shaded_gfrag_s": shaded_gfrag,
+            "dtype": "int64+f32", "data": "synthetic", "config": cfg, "shaded_gfrag_s": shaded_gfrag,
             "rasterized_gfrag_s": job_throughput(stats["fragments"], world, ms, 1e9),
             "stage_ms": {n: float(stage_ms[:, i].mean()) for i, n in
                          enumerate(["vertex", "setup_count", "scan", "scatter", "process"])},

@@ -4,7 +4,8 @@
 Workload: a displaced heightfield grid of 1000 x 500 quads (1,000,000
 triangles, 501,501 vertices) seen by a perspective camera at 1920 x 1080,
 Lambert shading with the material and light of Listing 1, 16 x 16 tiles,
-static tile schedule.  One step = one forward pass: vertex stage, setup and
+one CTA per tile (the hardware schedule; ``--schedule`` picks the static or
+dynamic one).  One step = one forward pass: vertex stage, setup and
 bin counts, scan, scatter, per-tile Process (coverage, depth, shading,
 write-out).  Inputs are resident in HBM; the L2 is flushed between steps by
 writing a 256 MiB buffer outside the per-step events.
@@ -384,13 +385,35 @@ def run_ours(args):
         e1.record(stream)
         barrier()
         e_ms = max_over_ranks(e0.elapsed_time(e1) / Ke, dist, "cuda")
+        # the same frames' copies alone, on the same lanes and streams: the
+        # floor that the end-to-end frames cannot go below
+        flush.zero_()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for sd in side:
+            sd.wait_stream(stream)
+        for k in range(Ke):
+            rr, d, f, kh, rh = lanes[k % nl]
+            with torch.cuda.stream(side[k % nl]):
+                for n, t in host_in.items():
+                    getattr(d, n).copy_(t, non_blocking=True)
+                kh.copy_(f.key, non_blocking=True)
+                rh.copy_(f.rgba, non_blocking=True)
+        for sd in side:
+            stream.wait_stream(sd)
+        c1.record(stream)
+        barrier()
+        c_ms = max_over_ranks(c0.elapsed_time(c1) / Ke, dist, "cuda")
         e2e = {"value": job_throughput(T, world, e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e_ms, "steps": Ke,
                "how": "Rasterizer.render_from_host per frame: pinned host -> device copies of every input, "
                       f"forward, device -> host copies of key and RGBA; frames rotate over {nl} handles and "
                       f"{nl} streams so copies overlap the other frames' work",
                "sequential": {"value": job_throughput(T, world, seq_ms), "ms_per_step": seq_ms,
-                              "how": "one frame at a time on one stream, L2 flushed between frames"}}
+                              "how": "one frame at a time on one stream, L2 flushed between frames"},
+               "copies_only": {"ms_per_step": c_ms, "gb_s": (h2d + d2h) / (c_ms * 1e6),
+                               "frac_of_e2e_time": c_ms / e_ms,
+                               "how": "the same frames' host<->device copies without the forward pass"}}
         if any(ln[0].status()[0] != 0 for ln in lanes):
             raise RuntimeError("status error after the end-to-end loop")
         for ln in lanes[1:]:
@@ -462,6 +485,8 @@ def run_extra(args):
         scene = S.power_law_triangles()
         lights = torch.from_numpy(S.point_lights(scene.width, scene.height, 64)).cuda()
         r = Rasterizer(scene.width, scene.height, args.bins, args.bins, args.schedule)
+        if args.small_px:
+            r.set_option(L.PIKO_OPT_SMALL_TRI_PIXELS, args.small_px)
         ds = DeviceScene.from_host(scene)
         fb = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode)
         out = torch.empty((scene.height, scene.width, 4), dtype=torch.float32, device="cuda")
@@ -501,7 +526,8 @@ def run_extra(args):
         line.update({"value": scene.num_triangles / (ms * 1e-3) / 1e6, "ms_per_step": ms, "dtype": "int64+f32",
                      "config": {"workload": "power-law 1920x1080, 500k triangles, G-buffer + 64 point lights",
                                 "bin": [args.bins, args.bins], "schedule": args.schedule,
-                                "l2": "flushed between steps (256 MiB write)"},
+                                "l2": "flushed between steps (256 MiB write)",
+                                **({"small_tri_pixels": args.small_px} if args.small_px else {})},
                      "forward_ms": float(fwd.mean()), "process_ms": float(proc.mean()),
                      "light_pass_ms": float(light.mean()),
                      "light_gpixlights_s": covered * 64 / lt / 1e9, "work": {**stats, "covered_pixels": covered},

@@ -49,44 +49,16 @@ void launch_vertex(int W, int H, int V, const float* pos, const float* mvp, int4
 }
 
 // ======================================================================
-// Warp-cooperative, vectorised load of 32 consecutive index triples.
-// The warp's 96 indices are read as 24 16-byte loads into a per-warp
-// buffer, then each lane takes its own triple.
+// Index triple of triangle t (zeros past the end).  Lane l of a warp reads
+// triangle base + l, so each of the three loads covers one contiguous
+// 384-byte span per warp: coalesced without staging.  (Staging the span
+// through shared memory with 16-byte loads was measured slower: the
+// shared-memory round trip costs more instructions than it saves.)
 // ======================================================================
-__device__ __forceinline__ int3 load_tri_warp(const int* __restrict__ tris, int T, int base, int lane,
-                                              int* __restrict__ wbuf) {
-  const long long first = 3LL * base;
-  if (base + 32 <= T) {
-    if (lane < 24) {
-      const int4 q = __ldg(reinterpret_cast<const int4*>(tris + first) + lane);
-      reinterpret_cast<int4*>(wbuf)[lane] = q;
-    }
-  } else {
-    const long long n = 3LL * T - first;
-    for (int k = lane; k < 96; k += 32) wbuf[k] = k < n ? __ldg(tris + first + k) : 0;
-  }
-  __syncwarp();
-  int3 r = make_int3(wbuf[3 * lane], wbuf[3 * lane + 1], wbuf[3 * lane + 2]);
-  __syncwarp();
-  return r;
-}
-
-// Setup of one triangle for binning: validity and its rectangle of bins.
-__device__ __forceinline__ bool bin_setup(const RasterGeom& g, int V, const int4* __restrict__ vtx, int3 idx,
-                                          DevStatus* st, int& bx0, int& by0, int& bx1, int& by1) {
-  if ((unsigned)idx.x >= (unsigned)V || (unsigned)idx.y >= (unsigned)V || (unsigned)idx.z >= (unsigned)V) {
-    record_error(st, PIKO_ERR_BAD_INDEX);
-    return false;
-  }
-  TriSetup s;
-  if (!setup_triangle(idx.x, idx.y, idx.z, vtx, s)) return false;
-  int px0, px1, py0, py1;
-  centre_range(min(s.X0, min(s.X1, s.X2)), max(s.X0, max(s.X1, s.X2)), 0, g.W - 1, px0, px1);
-  centre_range(min(s.Y0, min(s.Y1, s.Y2)), max(s.Y0, max(s.Y1, s.Y2)), 0, g.H - 1, py0, py1);
-  if (px0 > px1 || py0 > py1) return false;  // no pixel centre inside the bounding box
-  bx0 = px0 >> g.bshift_x; bx1 = px1 >> g.bshift_x;
-  by0 = py0 >> g.bshift_y; by1 = py1 >> g.bshift_y;
-  return true;
+__device__ __forceinline__ int3 load_tri(const int* __restrict__ tris, int T, int t) {
+  if (t >= T) return make_int3(0, 0, 0);
+  const long long i = 3LL * t;
+  return make_int3(__ldg(tris + i), __ldg(tris + i + 1), __ldg(tris + i + 2));
 }
 
 // ======================================================================
@@ -252,7 +224,6 @@ __global__ void __launch_bounds__(256) k_setup_count(RasterGeom g, int T, const 
                                                      const int4* __restrict__ vtx, BinRect* __restrict__ rect,
                                                      unsigned* __restrict__ cnt, int nbins, DevStatus* st,
                                                      int stats) {
-  __shared__ __align__(16) int sbuf[8][2][96];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   // the vertex stage does not touch the status word, and everything before
   // it has completed (it is launched without the early-start attribute)
@@ -266,8 +237,8 @@ __global__ void __launch_bounds__(256) k_setup_count(RasterGeom g, int T, const 
   for (int base = (blockIdx.x * (blockDim.x >> 5) + wib) * 32; base < T; base += 2 * step) {
     const int baseB = base + step;
     const bool hasB = baseB < T;  // warp-uniform
-    const int3 ia = load_tri_warp(tris, T, base, lane, sbuf[wib][0]);
-    const int3 ib = hasB ? load_tri_warp(tris, T, baseB, lane, sbuf[wib][1]) : make_int3(0, 0, 0);
+    const int3 ia = load_tri(tris, T, base + lane);
+    const int3 ib = hasB ? load_tri(tris, T, baseB + lane) : make_int3(0, 0, 0);
     const TriVerts va = gather_verts(ia, V, vtx, base + lane < T);
     const TriVerts vb = gather_verts(ib, V, vtx, hasB && baseB + lane < T);
     count_batch(g, T, base + lane, ia, va, rect, cnt, nbins, st, stats, lane, lt_mask);

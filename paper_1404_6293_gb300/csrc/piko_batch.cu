@@ -353,10 +353,6 @@ __device__ void process_one(const BatchParams& b, const int* prefix, int i, Proc
   __syncthreads();
   const TileScene& sc = ps.sc;
   const int gbin = b.sc[ps.scene].bin_base + ps.tile;
-  float L0 = 0.f, L1 = 0.f, L2 = 0.f;
-  if (sc.mode == PIKO_SHADE_LAMBERT) {
-    L0 = __ldg(sc.light); L1 = __ldg(sc.light + 1); L2 = __ldg(sc.light + 2);
-  }
   TileStats st = {0ull, 0ull, 0ull};
   const unsigned beg = __ldg(b.bin_off + gbin), end = __ldg(b.bin_off + gbin + 1);
   if (beg > end || (unsigned long long)end > b.capacity) {  // same for every thread: skip the tile
@@ -364,7 +360,7 @@ __device__ void process_one(const BatchParams& b, const int* prefix, int i, Proc
     __syncthreads();
     return;
   }
-  process_tile(sc, ps.tile, beg, end, b.bin_tris, sm, big_base, false, st, L0, L1, L2);
+  process_tile<false>(sc, ps.tile, beg, end, b.bin_tris, sm, big_base, st);
 }
 
 __device__ void phase_process(const BatchParams& b, ProcessShared& ps, const TileSmem& sm) {

@@ -8,7 +8,7 @@
 
 namespace piko {
 
-__device__ __forceinline__ TileScene scene_of(const ProcessParams& p) {
+__host__ __device__ inline TileScene scene_of(const ProcessParams& p) {
   TileScene sc;
   sc.g = p.g;
   sc.mode = p.mode;
@@ -34,12 +34,20 @@ __device__ __forceinline__ TileScene scene_of(const ProcessParams& p) {
 #ifndef PIKO_PROCESS_MAXNREG
 #define PIKO_PROCESS_MAXNREG 64
 #endif
-// The register cap trades a few spills on the rare int64 / warp paths for
-// occupancy on the common path (about 120 registers uncapped).
+// The register cap trades spills on the static and dynamic schedules' tile
+// loops for occupancy (about 120 registers uncapped); the one-CTA-per-tile
+// instance fits 64 registers without spilling.
 // One instance per schedule (SCHED = PIKO_SCHED_*), so that each carries
-// only its own tile loop.
-template <int SCHED>
-__global__ void __maxnreg__(PIKO_PROCESS_MAXNREG) k_process(ProcessParams p) {
+// only its own tile loop, and per value of the work-counter option (STATS),
+// so that the counters hold no registers when they are off.  The scene is
+// read in place from the grid-constant parameter block.
+struct ProcessLaunch {
+  ProcessParams p;
+  TileScene sc;
+};
+template <int SCHED, bool STATS>
+__global__ void __maxnreg__(PIKO_PROCESS_MAXNREG) k_process(const __grid_constant__ ProcessLaunch pl) {
+  const ProcessParams& p = pl.p;
   extern __shared__ __align__(16) unsigned long long smem[];
   const int bin_px = 1 << (p.g.bshift_x + p.g.bshift_y);
   const int nt = blockDim.x, tid = threadIdx.x;
@@ -50,11 +58,7 @@ __global__ void __maxnreg__(PIKO_PROCESS_MAXNREG) k_process(ProcessParams p) {
   sm.sbig = reinterpret_cast<int*>(smem + bin_px);
   sm.srec = sm.sbig + nt * BIG_REC;
   sm.s_nbig = &s_nbig;
-  const TileScene sc = scene_of(p);
-  float L0 = 0.f, L1 = 0.f, L2 = 0.f;
-  if (p.mode == PIKO_SHADE_LAMBERT) {
-    L0 = __ldg(p.light); L1 = __ldg(p.light + 1); L2 = __ldg(p.light + 2);
-  }
+  const TileScene& sc = pl.sc;
   for (int i = tid; i < bin_px; i += nt) sm.skey[i] = KEY_EMPTY;
   pdl_wait();  // bin lists and status of the scatter pass
   if (p.st->flags & STATUS_SKIP_MASK) return;
@@ -80,9 +84,9 @@ __global__ void __maxnreg__(PIKO_PROCESS_MAXNREG) k_process(ProcessParams p) {
     }
     if (tile >= p.ntiles) break;
     const unsigned beg = __ldg(p.bin_off + tile), end = __ldg(p.bin_off + tile + 1);
-    process_tile(sc, tile, beg, end, p.bin_tris, sm, big_base, p.stats != 0, st, L0, L1, L2);
+    process_tile<STATS>(sc, tile, beg, end, p.bin_tris, sm, big_base, st);
   }
-  if (p.stats) {  // one atomic per warp: same-address atomics from every thread serialise
+  if (STATS) {  // one atomic per warp: same-address atomics from every thread serialise
     for (int o = 16; o > 0; o >>= 1) {
       st.tests += __shfl_down_sync(FULL_MASK, st.tests, o);
       st.frags += __shfl_down_sync(FULL_MASK, st.frags, o);
@@ -107,19 +111,24 @@ static size_t smem_bytes(const ProcessParams& p, int threads) {
   return tile_smem_bytes(1 << (p.g.bshift_x + p.g.bshift_y), threads, p.nslots, p.rec_stride);
 }
 
-using ProcessKernel = void (*)(ProcessParams);
+using ProcessKernel = void (*)(ProcessLaunch);
 
-static ProcessKernel process_kernel(int schedule) {
-  if (schedule == PIKO_SCHED_DYNAMIC) return k_process<PIKO_SCHED_DYNAMIC>;
-  if (schedule == PIKO_SCHED_HARDWARE) return k_process<PIKO_SCHED_HARDWARE>;
-  return k_process<PIKO_SCHED_STATIC>;
+template <bool STATS>
+static ProcessKernel process_kernel_of(int schedule) {
+  if (schedule == PIKO_SCHED_DYNAMIC) return k_process<PIKO_SCHED_DYNAMIC, STATS>;
+  if (schedule == PIKO_SCHED_HARDWARE) return k_process<PIKO_SCHED_HARDWARE, STATS>;
+  return k_process<PIKO_SCHED_STATIC, STATS>;
+}
+
+static ProcessKernel process_kernel(const ProcessParams& p) {
+  return p.stats ? process_kernel_of<true>(p.schedule) : process_kernel_of<false>(p.schedule);
 }
 
 cudaError_t process_occupancy(const ProcessParams& p0, int threads, int* blocks_per_sm) {
   ProcessParams p = p0;
   layout(p, threads);
   const size_t smem = smem_bytes(p, threads);
-  const ProcessKernel k = process_kernel(p.schedule);
+  const ProcessKernel k = process_kernel(p);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -131,12 +140,15 @@ cudaError_t launch_process(const ProcessParams& p0, int threads, int grid, cudaS
   ProcessParams p = p0;
   layout(p, threads);
   const size_t smem = smem_bytes(p, threads);
-  const ProcessKernel k = process_kernel(p.schedule);
+  const ProcessKernel k = process_kernel(p);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  const cudaError_t e = launch_pdl(k, grid, threads, smem, s, p);
+  ProcessLaunch pl;
+  pl.p = p;
+  pl.sc = scene_of(p);
+  const cudaError_t e = launch_pdl(k, grid, threads, smem, s, pl);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 

@@ -159,15 +159,18 @@ __device__ __forceinline__ unsigned raster_thread_body(const TriSetup& s, unsign
   const float rA = approx_rcp((float)s.A);
   unsigned frags = 0;
   I r0 = e.e0, r1 = e.e1, r2 = e.e2;
-  for (int y = py0; y <= py1; ++y) {
+  // walk by tile-local pixel index: first and one-past-last of each row
+  const int bw = px1 - px0 + 1, pitch = 1 << bshift_x;
+  const int first = ((py0 - y0) << bshift_x) + (px0 - x0);
+  const int last = first + ((py1 - py0) << bshift_x);
+  for (int row = first; row <= last; row += pitch) {
     I a0 = r0, a1 = r1, a2 = r2;
-    const int row = (y - y0) << bshift_x;
-    for (int x = px0; x <= px1; ++x) {
+    for (int idx = row; idx < row + bw; ++idx) {
       if ((a0 | a1 | a2) >= 0) {
         if (sizeof(I) == 4)
-          key_min_small<N32>(skey, row + (x - x0), (int)a1 + e.b1, (int)a2 + e.b2, s, rA, tag);
+          key_min_small<N32>(skey, idx, (int)a1 + e.b1, (int)a2 + e.b2, s, rA, tag);
         else
-          key_min_large(skey, row + (x - x0), (long long)a1 + e.b1, (long long)a2 + e.b2, s, rA, tag);
+          key_min_large(skey, idx, (long long)a1 + e.b1, (long long)a2 + e.b2, s, rA, tag);
         ++frags;
       }
       a0 += e.sx0; a1 += e.sx1; a2 += e.sx2;
@@ -194,31 +197,37 @@ __device__ __forceinline__ unsigned raster_thread64(const TriSetup& s, unsigned 
 }
 
 // A warp covers a large triangle's box 32 pixels at a time; the ballot of
-// coverage lets the warp skip groups of pixels with nothing inside.
+// coverage lets the warp skip groups of pixels with nothing inside.  Each
+// lane evaluates the three edge functions of its pixel directly from the
+// snapped vertices (two 32x32->64 products per edge), so the warp path holds
+// no 64-bit edge increments.
 __device__ __forceinline__ unsigned raster_warp(const TriSetup& s, unsigned long long tag, int px0, int px1, int py0,
                                                 int py1, int x0, int y0, int bshift_x, unsigned long long* skey,
                                                 int lane) {
-  const Edges<long long> e = make_edges<long long>(s, px0, py0);
   const float rA = approx_rcp((float)s.A);
   const int bw = px1 - px0 + 1, n = bw * (py1 - py0 + 1);
   const int dy = 32 / bw, dx = 32 - dy * bw;
   int lx = lane % bw, ly = lane / bw;
   const bool mid = s.A < (1LL << 31);  // the same for the whole warp
+  // fill-rule bias of each edge: 1 unless the edge is top-left
+  const int b0 = 1 - top_left(s.X2 - s.X1, s.Y2 - s.Y1);
+  const int b1 = 1 - top_left(s.X0 - s.X2, s.Y0 - s.Y2);
+  const int b2 = 1 - top_left(s.X1 - s.X0, s.Y1 - s.Y0);
   unsigned frags = 0;
   for (int base = 0; base < n; base += 32) {
-    const bool in_box = base + lane < n;
-    const long long a0 = e.e0 + lx * e.sx0 + ly * e.sy0;
-    const long long a1 = e.e1 + lx * e.sx1 + ly * e.sy1;
-    const long long a2 = e.e2 + lx * e.sx2 + ly * e.sy2;
-    const bool cov = in_box && (a0 | a1 | a2) >= 0;
+    const int Px = 256 * (px0 + lx) + 128, Py = 256 * (py0 + ly) + 128;
+    const long long w0 = (long long)(s.X2 - s.X1) * (Py - s.Y1) - (long long)(s.Y2 - s.Y1) * (Px - s.X1);
+    const long long w1 = (long long)(s.X0 - s.X2) * (Py - s.Y2) - (long long)(s.Y0 - s.Y2) * (Px - s.X2);
+    const long long w2 = (long long)(s.X1 - s.X0) * (Py - s.Y0) - (long long)(s.Y1 - s.Y0) * (Px - s.X0);
+    const bool cov = base + lane < n && ((w0 - b0) | (w1 - b1) | (w2 - b2)) >= 0;
     const unsigned m = __ballot_sync(FULL_MASK, cov);
     if (m != 0u) {
       if (cov) {
         const int idx = ((py0 + ly - y0) << bshift_x) + (px0 + lx - x0);
         if (mid)
-          key_min_mid(skey, idx, (int)(a1 + e.b1), (int)(a2 + e.b2), s, rA, tag);
+          key_min_mid(skey, idx, (int)w1, (int)w2, s, rA, tag);
         else
-          key_min_large(skey, idx, a1 + e.b1, a2 + e.b2, s, rA, tag);
+          key_min_large(skey, idx, w1, w2, s, rA, tag);
       }
       frags += __popc(m);
     }
@@ -260,8 +269,7 @@ __device__ __forceinline__ void rec_bary(const int* r, int x, int y, float& b0, 
   b0 = 1.0f - b1 - b2;
 }
 
-__device__ __forceinline__ void shade_from_record(const TileScene& p, const int* r, int x, int y, size_t o,
-                                                  float L0, float L1, float L2) {
+__device__ __forceinline__ void shade_from_record(const TileScene& p, const int* r, int x, int y, size_t o) {
   float b0, b1, b2;
   rec_bary(r, x, y, b0, b1, b2);
   const float* a = reinterpret_cast<const float*>(r + R_ATTR);
@@ -297,8 +305,7 @@ __device__ __forceinline__ void shade_from_record(const TileScene& p, const int*
 }
 
 // Fallback for winners without a record: everything re-read from global memory.
-__device__ __forceinline__ void shade_from_global(const TileScene& p, unsigned t, int x, int y, size_t o,
-                                                  float L0, float L1, float L2) {
+__device__ __forceinline__ void shade_from_global(const TileScene& p, unsigned t, int x, int y, size_t o) {
   TriSetup s;
   setup_triangle(__ldg(p.tris + 3 * (size_t)t), __ldg(p.tris + 3 * (size_t)t + 1), __ldg(p.tris + 3 * (size_t)t + 2),
                  p.vtx, s);
@@ -331,14 +338,13 @@ __device__ __forceinline__ void shade_from_global(const TileScene& p, unsigned t
     p.galb_out[o] = pack_half4(c0, c1, c2, 1.0f);
     return;
   }
-  float d = nx * L0 + ny * L1 + nz * L2;
+  float d = nx * __ldg(p.light) + ny * __ldg(p.light + 1) + nz * __ldg(p.light + 2);
   if (!p.unclamped) d = fmaxf(d, 0.0f);
   if (p.rgba_out) p.rgba_out[o] = make_float4(c0 * d, c1 * d, c2 * d, 1.0f);
 }
 
 // Fills the shared-memory record of one bin entry.
-__device__ __forceinline__ void fill_record(const TileScene& p, const TriSetup& s, int* r, float L0, float L1,
-                                            float L2) {
+__device__ __forceinline__ void fill_record(const TileScene& p, const TriSetup& s, int* r) {
   r[0] = s.X0; r[1] = s.Y0; r[2] = s.X1; r[3] = s.Y1; r[4] = s.X2; r[5] = s.Y2;
   r[R_RA] = __float_as_int(approx_rcp((float)s.A));
   float* a = reinterpret_cast<float*>(r + R_ATTR);
@@ -382,10 +388,10 @@ __device__ __forceinline__ void load_setup(const TileScene& p, unsigned t, TriSe
 // Process one tile: tile is the scene-local tile index, [beg, end) its range
 // in bin_tris.  Called by every thread of the CTA (nt threads, a power of
 // two); contains CTA barriers.  big_base tracks the large-triangle ring.
+template <bool STATS>
 __device__ __forceinline__ void process_tile(const TileScene& p, int tile, unsigned beg, unsigned end,
                                              const unsigned* __restrict__ bin_tris, const TileSmem& sm,
-                                             unsigned& big_base, bool stats, TileStats& st, float L0, float L1,
-                                             float L2) {
+                                             unsigned& big_base, TileStats& st) {
   const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
   const int bin_w = 1 << p.g.bshift_x, bin_h = 1 << p.g.bshift_y;
   const int bin_px = bin_w * bin_h;
@@ -402,7 +408,7 @@ __device__ __forceinline__ void process_tile(const TileScene& p, int tile, unsig
       const unsigned slot = (i - beg) < (unsigned)p.nslots ? (i - beg) : no_slot;
       TriSetup s;
       load_setup(p, t, s);
-      if (slot != no_slot) fill_record(p, s, sm.srec + slot * p.rec_stride, L0, L1, L2);
+      if (slot != no_slot) fill_record(p, s, sm.srec + slot * p.rec_stride);
       const int minX = min(s.X0, min(s.X1, s.X2)), maxX = max(s.X0, max(s.X1, s.X2));
       const int minY = min(s.Y0, min(s.Y1, s.Y2)), maxY = max(s.Y0, max(s.Y1, s.Y2));
       int px0, px1, py0, py1;
@@ -411,14 +417,14 @@ __device__ __forceinline__ void process_tile(const TileScene& p, int tile, unsig
       if (px0 <= px1 && py0 <= py1) {
         const int npx = (px1 - px0 + 1) * (py1 - py0 + 1);
         const unsigned long long tag = ((unsigned long long)t << p.slot_bits) | slot;
-        if (stats) st.tests += npx;
+        if (STATS) st.tests += npx;
         if (npx <= p.small_px) {
           unsigned f;
           if (maxX - minX < 32768 && maxY - minY < 32768)
             f = raster_thread32(s, tag, px0, px1, py0, py1, x0, y0, p.g.bshift_x, skey);
           else
             f = raster_thread64(s, tag, px0, px1, py0, py1, x0, y0, p.g.bshift_x, skey);
-          if (stats) st.frags += f;
+          if (STATS) st.frags += f;
         } else {
           // the ring counter only ever grows; with nt a power of two the ring
           // index stays consistent across its 2^32 wrap
@@ -448,7 +454,7 @@ __device__ __forceinline__ void process_tile(const TileScene& p, int tile, unsig
         centre_range(min(s.Y0, min(s.Y1, s.Y2)), max(s.Y0, max(s.Y1, s.Y2)), y0, y1, py0, py1);
         const unsigned f = raster_warp(s, ((unsigned long long)t << p.slot_bits) | slot, px0, px1, py0, py1, x0, y0,
                                        p.g.bshift_x, skey, lane);
-        if (stats && lane == 0) st.frags += f;
+        if (STATS && lane == 0) st.frags += f;
       }
       big_base += nbig;
       __syncthreads();
@@ -471,11 +477,11 @@ __device__ __forceinline__ void process_tile(const TileScene& p, int tile, unsig
     const unsigned t = (unsigned)((k >> p.slot_bits) & ((1ull << (40 - p.slot_bits)) - 1ull));
     const unsigned slot = (unsigned)(k & no_slot);
     p.key_out[o] = ((unsigned long long)z << 32) | t;
-    if (stats) ++st.shaded;
+    if (STATS) ++st.shaded;
     if (slot != no_slot)
-      shade_from_record(p, sm.srec + slot * p.rec_stride, x, y, o, L0, L1, L2);
+      shade_from_record(p, sm.srec + slot * p.rec_stride, x, y, o);
     else
-      shade_from_global(p, t, x, y, o, L0, L1, L2);
+      shade_from_global(p, t, x, y, o);
   }
   __syncthreads();
 }

@@ -120,25 +120,49 @@ __device__ __forceinline__ void key_min_mid(unsigned long long* skey, int idx, i
   key_store(skey, idx, (unsigned)(s.Z0 + q), tag);
 }
 
-// Triangles whose bounding box is below 2^15 in 16.8 units: A < 2^30 and
-// w1, w2 < 2^31, so the depth numerator is two 32x32->64 products.  With
-// N32 the caller has checked A * (|Z1-Z0| + |Z2-Z0| + 8) < 2^31: the
-// numerator, the quotient estimate times A and the remainder then all fit
-// in 32 bits.
-template <bool N32>
-__device__ __forceinline__ void key_min_small(unsigned long long* skey, int idx, int w1, int w2, const TriSetup& s,
-                                              float rA, unsigned long long tag) {
-  if (N32) {
-    const int A = (int)s.A;
-    const int n = w1 * (s.Z1 - s.Z0) + w2 * (s.Z2 - s.Z0);
-    int q = __float2int_rd((float)n * rA);
-    int r = n - q * A;
-    for (int it = 0; r < 0 && it < DIV_FIX_LIMIT; ++it) { --q; r += A; }
-    for (int it = 0; r >= A && it < DIV_FIX_LIMIT; ++it) { ++q; r -= A; }
-    key_store(skey, idx, (unsigned)(s.Z0 + q), tag);
+// Depth keys of the per-thread walk over a small box (bounding box below
+// 2^15 in 16.8 units, so A < 2^30).  The quotient q = floor((w1 d1 + w2 d2) / A),
+// d_i = Z_i - Z0, is estimated in float32 from k_i = d_i / A (per entry) and
+// then corrected against the exact remainder r = w1 d1 + w2 d2 - q A, with
+// w1, w2 in [0, A] for a covered sample.  The estimate is within
+// (|d1| + |d2|) 2^-21 + 1 of q (1/A to 2 ulp, four roundings), so:
+//  - fast (A < 2^27 and |d1| + |d2| < 2^22): |r| < 4A < 2^29, and 32-bit
+//    wrapping arithmetic gives r exactly;
+//  - otherwise r is formed in 64 bits and the estimate is within 16 of q.
+// The choice is per entry, so a warp rarely splits between the two forms.
+// The key is Z0 << 40 | tag plus q << 40 (Z0 + q stays in [0, 2^24)).
+struct DepthSetup {
+  int d1, d2, A;
+  float k1, k2;
+  unsigned long long kbase;
+  bool fast;
+};
+
+__device__ __forceinline__ DepthSetup depth_setup(const TriSetup& s, float rA, unsigned long long tag) {
+  DepthSetup d;
+  d.d1 = s.Z1 - s.Z0;
+  d.d2 = s.Z2 - s.Z0;
+  d.A = (int)s.A;
+  d.k1 = rA * (float)d.d1;
+  d.k2 = rA * (float)d.d2;
+  d.kbase = ((unsigned long long)(unsigned)s.Z0 << 40) | tag;
+  d.fast = s.A < (1LL << 27) && abs(d.d1) + abs(d.d2) < (1 << 22);
+  return d;
+}
+
+__device__ __forceinline__ void key_min_box(unsigned long long* skey, int idx, int w1, int w2, const DepthSetup& d) {
+  int q = __float2int_rd(__fmaf_rn((float)w1, d.k1, (float)w2 * d.k2));
+  if (d.fast) {
+    int r = (int)((unsigned)w1 * (unsigned)d.d1 + (unsigned)w2 * (unsigned)d.d2 - (unsigned)q * (unsigned)d.A);
+    for (int it = 0; r < 0 && it < DIV_FIX_LIMIT; ++it) { --q; r += d.A; }
+    for (int it = 0; r >= d.A && it < DIV_FIX_LIMIT; ++it) { ++q; r -= d.A; }
   } else {
-    key_min_mid(skey, idx, w1, w2, s, rA, tag);
+    long long r = (long long)w1 * d.d1 + (long long)w2 * d.d2 - (long long)q * d.A;
+    for (int it = 0; r < 0 && it < DIV_FIX_LIMIT; ++it) { --q; r += d.A; }
+    for (int it = 0; r >= d.A && it < DIV_FIX_LIMIT; ++it) { ++q; r -= d.A; }
   }
+  const unsigned long long k = d.kbase + ((unsigned long long)(long long)q << 40);
+  if (k < skey[idx]) atomicMin(skey + idx, k);
 }
 
 __device__ __forceinline__ void key_min_large(unsigned long long* skey, int idx, long long w1, long long w2,
@@ -151,12 +175,13 @@ __device__ __forceinline__ void key_min_large(unsigned long long* skey, int idx,
 // int the triangle's bounding box is below 2^15 in 16.8 units in both
 // directions, so every edge value inside the box is below 2^31 in magnitude
 // and int32 arithmetic is exact.
-template <typename I, bool N32>
+template <typename I>
 __device__ __forceinline__ unsigned raster_thread_body(const TriSetup& s, unsigned long long tag, int px0, int px1,
                                                        int py0, int py1, int x0, int y0, int bshift_x,
                                                        unsigned long long* skey) {
   const Edges<I> e = make_edges<I>(s, px0, py0);
   const float rA = approx_rcp((float)s.A);
+  const DepthSetup d = depth_setup(s, rA, tag);
   unsigned frags = 0;
   I r0 = e.e0, r1 = e.e1, r2 = e.e2;
   // walk by tile-local pixel index: first and one-past-last of each row
@@ -168,7 +193,7 @@ __device__ __forceinline__ unsigned raster_thread_body(const TriSetup& s, unsign
     for (int idx = row; idx < row + bw; ++idx) {
       if ((a0 | a1 | a2) >= 0) {
         if (sizeof(I) == 4)
-          key_min_small<N32>(skey, idx, (int)a1 + e.b1, (int)a2 + e.b2, s, rA, tag);
+          key_min_box(skey, idx, (int)a1 + e.b1, (int)a2 + e.b2, d);
         else
           key_min_large(skey, idx, (long long)a1 + e.b1, (long long)a2 + e.b2, s, rA, tag);
         ++frags;
@@ -181,19 +206,16 @@ __device__ __forceinline__ unsigned raster_thread_body(const TriSetup& s, unsign
 }
 
 // Small boxes of small triangles (the common case) stay inline; the int64
-// form for small boxes of large triangles is a separate function so that its
-// registers do not weigh on the common path.
+// form for small boxes of large triangles is a separate instance.
 __device__ __forceinline__ unsigned raster_thread32(const TriSetup& s, unsigned long long tag, int px0, int px1,
                                                     int py0, int py1, int x0, int y0, int bshift_x,
                                                     unsigned long long* skey) {
-  const long long dz = (long long)abs(s.Z1 - s.Z0) + abs(s.Z2 - s.Z0) + 8;
-  if (s.A * dz < (1LL << 31)) return raster_thread_body<int, true>(s, tag, px0, px1, py0, py1, x0, y0, bshift_x, skey);
-  return raster_thread_body<int, false>(s, tag, px0, px1, py0, py1, x0, y0, bshift_x, skey);
+  return raster_thread_body<int>(s, tag, px0, px1, py0, py1, x0, y0, bshift_x, skey);
 }
 __device__ __forceinline__ unsigned raster_thread64(const TriSetup& s, unsigned long long tag, int px0, int px1,
                                                  int py0, int py1, int x0, int y0, int bshift_x,
                                                  unsigned long long* skey) {
-  return raster_thread_body<long long, false>(s, tag, px0, px1, py0, py1, x0, y0, bshift_x, skey);
+  return raster_thread_body<long long>(s, tag, px0, px1, py0, py1, x0, y0, bshift_x, skey);
 }
 
 // A warp covers a large triangle's box 32 pixels at a time; the ballot of

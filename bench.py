@@ -226,6 +226,18 @@ def run_ours(args):
 
     scene, cfg = workload(args)
     T = scene.num_triangles
+    if args.autotune:
+        # the tuner's pick of bin size, schedule and threads per bin, by forward time
+        from paper_1404_6293_gb300.autotune import Autotuner
+        tuner = Autotuner(reps=5)
+        t0 = time.perf_counter()
+        knobs = tuner.knobs(DeviceScene.from_host(scene))
+        tune_s = time.perf_counter() - t0
+        n_trials = len(next(iter(tuner.cache.values()))["trials"])
+        tuner.close()
+        args.bins, args.schedule, args.threads = knobs["bin"][0], knobs["schedule"], knobs["threads"]
+        cfg.update({"bin": list(knobs["bin"]), "schedule": args.schedule,
+                    "knobs": f"autotuned: fastest forward of {n_trials} candidates ({tune_s:.1f} s, untimed)"})
     r = Rasterizer(scene.width, scene.height, args.bins, args.bins, args.schedule)
     if args.threads:
         r.set_option(L.PIKO_OPT_THREADS_PER_TILE, args.threads)
@@ -310,7 +322,11 @@ def run_ours(args):
     try:
         with open(PROFILE_TRAFFIC) as f:
             prof = json.load(f)
-        if prof.get("kernel_hash") == kernel_hash():
+        bin_px = args.bins * args.bins
+        launch = {"bins": args.bins, "schedule": args.schedule,
+                  "threads": args.threads or (64 if bin_px <= 64 else (128 if bin_px <= 256 else 256))}
+        # counters apply only to the same kernel sources in the same launch configuration
+        if prof.get("kernel_hash") == kernel_hash() and prof.get("launch") == launch:
             traffic = prof.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
@@ -487,6 +503,8 @@ def run_extra(args):
         r = Rasterizer(scene.width, scene.height, args.bins, args.bins, args.schedule)
         if args.small_px:
             r.set_option(L.PIKO_OPT_SMALL_TRI_PIXELS, args.small_px)
+        if args.threads:
+            r.set_option(L.PIKO_OPT_THREADS_PER_TILE, args.threads)
         ds = DeviceScene.from_host(scene)
         fb = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode)
         out = torch.empty((scene.height, scene.width, 4), dtype=torch.float32, device="cuda")
@@ -527,7 +545,8 @@ def run_extra(args):
                      "config": {"workload": "power-law 1920x1080, 500k triangles, G-buffer + 64 point lights",
                                 "bin": [args.bins, args.bins], "schedule": args.schedule,
                                 "l2": "flushed between steps (256 MiB write)",
-                                **({"small_tri_pixels": args.small_px} if args.small_px else {})},
+                                **({"small_tri_pixels": args.small_px} if args.small_px else {}),
+                                **({"threads_per_tile": args.threads} if args.threads else {})},
                      "forward_ms": float(fwd.mean()), "process_ms": float(proc.mean()),
                      "light_pass_ms": float(light.mean()),
                      "light_gpixlights_s": covered * 64 / lt / 1e9, "work": {**stats, "covered_pixels": covered},
@@ -809,6 +828,8 @@ def main():
                     help="tile schedule of the heightfield line (hardware: one CTA per tile, the fastest "
                          "of the bin-size x schedule sweep at 16x16)")
     ap.add_argument("--threads", type=int, default=0, help="Process CTA size (0: library default)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="heightfield workload: bin size, schedule and threads per bin from the autotuner")
     ap.add_argument("--small-px", type=int, default=0,
                     help="largest box (pixels inside a tile) one thread rasterizes; larger boxes take a warp "
                          "(0: library default)")

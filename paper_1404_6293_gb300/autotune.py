@@ -4,8 +4,10 @@ The Piko paper explores bin size and schedule by hand for each scene and
 architecture (Sec. 7.2: spatial binning helps most scenes but not one made
 of tiny uniform triangles; fusing stages trades load balance for locality).
 This tuner searches the same knobs automatically: for a scene it times the
-forward pass under every (bin size, schedule) candidate with CUDA events and
-keeps the fastest.  Results are cached by workload features (resolution,
+forward pass under every (bin size, schedule, threads per bin) candidate with
+CUDA events and keeps the fastest.  Threads per bin is the third template
+parameter of the paper's Listing 1 stage; small triangles favour fewer
+threads per bin (more CTAs per SM), large ones more (more warps per tile).  Results are cached by workload features (resolution,
 triangle count, coverage density, shading mode) so that similar scenes share
 one measurement; the cache can be saved to and loaded from JSON.
 
@@ -25,12 +27,26 @@ from typing import Dict, Iterable, List, Optional, Tuple
 
 import torch
 
+from . import _lib as L
 from .raster import DeviceScene, Rasterizer
 
 DEFAULT_BINS: Tuple[Tuple[int, int], ...] = ((8, 8), (16, 16), (32, 32), (64, 64))
 DEFAULT_SCHEDULES: Tuple[str, ...] = ("static", "dynamic", "hardware")
+THREAD_CHOICES: Tuple[int, ...] = (64, 128, 256, 512)  # the CTA sizes the library accepts
 # a batch has no hardware mapping (its tiles are dealt inside one persistent launch)
 BATCH_SCHEDULES: Tuple[str, ...] = ("static", "dynamic")
+
+
+def default_threads(bin_px: int) -> int:
+    """The library's CTA size for a bin of bin_px pixels when none is set."""
+    return 64 if bin_px <= 64 else (128 if bin_px <= 256 else 256)
+
+
+def thread_candidates(bw: int, bh: int) -> Tuple[int, ...]:
+    """The default CTA size for the bin and its neighbours (half and double),
+    at most one thread per pixel of the bin."""
+    d = default_threads(bw * bh)
+    return tuple(t for t in THREAD_CHOICES if d // 2 <= t <= 2 * d and t <= max(64, bw * bh))
 
 
 def features(scene: DeviceScene) -> str:
@@ -44,9 +60,11 @@ def features(scene: DeviceScene) -> str:
 
 class Autotuner:
     def __init__(self, bins: Iterable[Tuple[int, int]] = DEFAULT_BINS,
-                 schedules: Iterable[str] = DEFAULT_SCHEDULES, reps: int = 3, cache_path: Optional[str] = None):
+                 schedules: Iterable[str] = DEFAULT_SCHEDULES, reps: int = 3, cache_path: Optional[str] = None,
+                 tune_threads: bool = True):
         self.bins = tuple(tuple(b) for b in bins)
         self.schedules = tuple(schedules)
+        self.tune_threads = tune_threads
         self.reps = reps
         self.cache: Dict[str, dict] = {}
         self.cache_path = cache_path
@@ -55,15 +73,19 @@ class Autotuner:
                 self.cache = json.load(f)
         self._handles: Dict[tuple, Rasterizer] = {}
 
-    def _handle(self, W, H, bw, bh, sched) -> Rasterizer:
-        k = (W, H, bw, bh, sched)
+    def _handle(self, W, H, bw, bh, sched, threads=0) -> Rasterizer:
+        k = (W, H, bw, bh, sched, threads)
         if k not in self._handles:
-            self._handles[k] = Rasterizer(W, H, bw, bh, sched)
+            r = Rasterizer(W, H, bw, bh, sched)
+            if threads:
+                r.set_option(L.PIKO_OPT_THREADS_PER_TILE, threads)
+            self._handles[k] = r
         return self._handles[k]
 
-    def time_candidate(self, scene: DeviceScene, bw: int, bh: int, sched: str) -> float:
-        """Median forward time in ms of one candidate (after a sizing pass)."""
-        r = self._handle(scene.width, scene.height, bw, bh, sched)
+    def time_candidate(self, scene: DeviceScene, bw: int, bh: int, sched: str, threads: int = 0) -> float:
+        """Median forward time in ms of one candidate (after a sizing pass);
+        threads 0 keeps the library's CTA size."""
+        r = self._handle(scene.width, scene.height, bw, bh, sched, threads)
         fb = r.forward(scene)  # sizes the bin lists
         r.status()
         times: List[float] = []
@@ -81,20 +103,29 @@ class Autotuner:
         best = None
         trials = []
         for bw, bh in self.bins:
+            threads = thread_candidates(bw, bh) if self.tune_threads else (default_threads(bw * bh),)
             for sched in self.schedules:
-                ms = self.time_candidate(scene, bw, bh, sched)
-                trials.append({"bin": [bw, bh], "schedule": sched, "ms": ms})
-                if best is None or ms < best["ms"]:
-                    best = {"bin": [bw, bh], "schedule": sched, "ms": ms}
+                for th in threads:
+                    ms = self.time_candidate(scene, bw, bh, sched, th)
+                    trials.append({"bin": [bw, bh], "schedule": sched, "threads": th, "ms": ms})
+                    if best is None or ms < best["ms"]:
+                        best = {"bin": [bw, bh], "schedule": sched, "threads": th, "ms": ms}
         best["trials"] = trials
         return best
 
-    def choose(self, scene: DeviceScene) -> Tuple[Tuple[int, int], str]:
+    def knobs(self, scene: DeviceScene) -> dict:
+        """The tuned bin size, schedule and threads per bin of the scene's
+        workload class (measured on the first scene of the class)."""
         key = features(scene)
         if key not in self.cache:
             self.cache[key] = self.tune(scene)
         c = self.cache[key]
-        return (c["bin"][0], c["bin"][1]), c["schedule"]
+        bw, bh = c["bin"]
+        return {"bin": (bw, bh), "schedule": c["schedule"], "threads": c.get("threads", default_threads(bw * bh))}
+
+    def choose(self, scene: DeviceScene) -> Tuple[Tuple[int, int], str]:
+        k = self.knobs(scene)
+        return k["bin"], k["schedule"]
 
     def choose_all(self, scenes: List[DeviceScene]):
         """Per-scene (bin sizes, schedules) lists for forward_batch."""

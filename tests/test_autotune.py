@@ -8,7 +8,8 @@ import pytest
 import torch
 
 from paper_1404_6293_gb300 import scenes as S
-from paper_1404_6293_gb300.autotune import BATCH_SCHEDULES, DEFAULT_BINS, DEFAULT_SCHEDULES, Autotuner, features
+from paper_1404_6293_gb300.autotune import (BATCH_SCHEDULES, DEFAULT_BINS, DEFAULT_SCHEDULES, THREAD_CHOICES,
+                                            Autotuner, default_threads, features, thread_candidates)
 from paper_1404_6293_gb300.raster import DeviceScene
 
 
@@ -37,6 +38,28 @@ def test_cache_round_trip_answers_without_measuring(tmp_path):
     assert json.loads((tmp_path / "copy.json").read_text()) == json.loads(path.read_text())
 
 
+def test_thread_candidates_around_the_library_default():
+    # the library's defaults (piko_internal.cuh): 64 up to 64 pixels, 128 up to 256, else 256
+    assert [default_threads(b * b) for b in (8, 16, 32, 64)] == [64, 128, 256, 256]
+    for b in (8, 16, 32, 64):
+        c = thread_candidates(b, b)
+        assert default_threads(b * b) in c
+        assert all(t in THREAD_CHOICES and t <= max(64, b * b) for t in c)
+    assert thread_candidates(16, 16) == (64, 128, 256)
+    assert thread_candidates(8, 8) == (64,)
+
+
+def test_cached_entry_without_threads_uses_the_default(tmp_path):
+    scene = _cpu_scene(640, 480, 50_000)
+    path = tmp_path / "tune.json"
+    path.write_text(json.dumps({features(scene): {"bin": [16, 16], "schedule": "hardware", "ms": 1.0}}))
+    tuner = Autotuner(cache_path=str(path))
+    assert tuner.knobs(scene) == {"bin": (16, 16), "schedule": "hardware", "threads": 128}
+    path.write_text(json.dumps({features(scene): {"bin": [32, 32], "schedule": "static", "threads": 512,
+                                                  "ms": 1.0}}))
+    assert Autotuner(cache_path=str(path)).knobs(scene)["threads"] == 512
+
+
 def test_batch_candidates_exclude_the_hardware_mapping():
     assert "hardware" in DEFAULT_SCHEDULES
     assert "hardware" not in BATCH_SCHEDULES
@@ -45,12 +68,24 @@ def test_batch_candidates_exclude_the_hardware_mapping():
 @pytest.mark.gpu
 def test_tuned_settings_are_valid_and_render_exactly():
     import oracle
+    from paper_1404_6293_gb300 import _lib as L
     from paper_1404_6293_gb300.raster import Rasterizer
     host = S.scene_batch(6, tmax=20_000, side_max=384, seed=5)
     ds = [DeviceScene.from_host(s) for s in host]
     tuner = Autotuner(bins=((16, 16), (32, 32)), reps=1)
+    k = tuner.knobs(ds[0])
     (bw, bh), sched = tuner.choose(ds[0])
+    assert (bw, bh) == k["bin"] and sched == k["schedule"]
     assert (bw, bh) in ((16, 16), (32, 32)) and sched in DEFAULT_SCHEDULES
+    assert k["threads"] in thread_candidates(bw, bh)
+    # the tuned knobs render the scene exactly
+    r1 = Rasterizer(host[0].width, host[0].height, bw, bh, sched)
+    r1.set_option(L.PIKO_OPT_THREADS_PER_TILE, k["threads"])
+    fb1 = r1.forward(ds[0])
+    torch.cuda.synchronize()
+    assert r1.status()[0] == 0
+    assert np.array_equal(fb1.key_numpy(), oracle.raster_bbox(host[0])[0])
+    r1.close()
     bins, scheds, report = tuner.tune_batch(ds)
     tuner.close()
     assert len(bins) == len(scheds) == len(ds)

@@ -138,10 +138,16 @@ def _d(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
 
 
-def shade(scene, key, mvp=None, color=None, normal=None, light=None, mode=None, unclamped=False):
+def _flags(unclamped, perspective):
+    return (1 if unclamped else 0) | (2 if perspective else 0)
+
+
+def shade(scene, key, mvp=None, color=None, normal=None, light=None, mode=None, unclamped=False,
+          perspective=False):
     """Float64 shading of the oracle's key buffer.  Returns rgba [H,W,4] float64
     for modes 0/1, or (normal_half, albedo_half) uint16 [H,W,4] for mode 2.
-    color / normal / light default to the scene's, as float64."""
+    color / normal / light default to the scene's, as float64.  perspective:
+    perspective-correct barycentrics (O15) instead of screen-space ones."""
     lib = _load()
     pos, tris, M = _geom(scene, mvp)
     mode = scene.shade_mode if mode is None else mode
@@ -156,11 +162,11 @@ def shade(scene, key, mvp=None, color=None, normal=None, light=None, mode=None, 
         gn = np.empty((H, W, 4), np.uint16)
         ga = np.empty((H, W, 4), np.uint16)
         lib.oracle_shade(W, H, pos.shape[0], _p(pos), tris.shape[0], _p(tris), _p(M), _p(col), _p(nrm),
-                         _p(L), 2, int(unclamped), _p(key), None, _p(gn), _p(ga))
+                         _p(L), 2, _flags(unclamped, perspective), _p(key), None, _p(gn), _p(ga))
         return gn, ga
     rgba = np.empty((H, W, 4), np.float64)
     lib.oracle_shade(W, H, pos.shape[0], _p(pos), tris.shape[0], _p(tris), _p(M), _p(col), _p(nrm), _p(L),
-                     int(mode), int(unclamped), _p(key), _p(rgba), None, None)
+                     int(mode), _flags(unclamped, perspective), _p(key), _p(rgba), None, None)
     return rgba
 
 
@@ -178,7 +184,7 @@ def light_pass(key, gnormal_u16, galbedo_u16, lights):
 
 
 def backward(scene, key, dl_drgba, mvp=None, color=None, normal=None, light=None, mode=None,
-             unclamped=False, out=None):
+             unclamped=False, out=None, perspective=False):
     """Float64 analytic gradients (dcolor [V,3], dnormal [V,3], dlight [3]),
     accumulated into ``out`` when given."""
     lib = _load()
@@ -196,12 +202,13 @@ def backward(scene, key, dl_drgba, mvp=None, color=None, normal=None, light=None
     g = np.ascontiguousarray(dl_drgba, dtype=np.float64)
     key = np.ascontiguousarray(key, dtype=np.uint64)
     lib.oracle_backward(scene.width, scene.height, V, _p(pos), tris.shape[0], _p(tris), _p(M), _p(col),
-                        _p(nrm), _p(L), int(mode), int(unclamped), _p(key), _p(g), _p(dc), _p(dn), _p(dl))
+                        _p(nrm), _p(L), int(mode), _flags(unclamped, perspective), _p(key), _p(g), _p(dc),
+                        _p(dn), _p(dl))
     return dc, dn, dl
 
 
 def loss(scene, key, target, mvp=None, color=None, normal=None, light=None, mode=None,
-         unclamped=False) -> float:
+         unclamped=False, perspective=False) -> float:
     """sum (rgb - target)^2 over pixels and RGB, float64, visibility fixed."""
     lib = _load()
     pos, tris, M = _geom(scene, mvp)
@@ -214,8 +221,8 @@ def loss(scene, key, target, mvp=None, color=None, normal=None, light=None, mode
     key = np.ascontiguousarray(key, dtype=np.uint64)
     tgt = np.ascontiguousarray(target, dtype=np.float32)
     return float(lib.oracle_loss(scene.width, scene.height, pos.shape[0], _p(pos), tris.shape[0], _p(tris),
-                                 _p(M), _p(col), _p(nrm), _p(L), int(mode), int(unclamped), _p(key),
-                                 _p(tgt)))
+                                 _p(M), _p(col), _p(nrm), _p(L), int(mode), _flags(unclamped, perspective),
+                                 _p(key), _p(tgt)))
 
 
 def half_from_double(x: float) -> int:

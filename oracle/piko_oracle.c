@@ -43,6 +43,13 @@
  *       (light_pass below).
  *   O13 gradients of sum (rgb - target)^2 with visibility fixed.
  *   O14 a triangle with an index outside [0, V) is culled and reported.
+ *   O15 optional perspective-correct attributes (flag bit 1 of shade,
+ *       backward and loss): the screen-space b_i of O11 are replaced by
+ *       b'_i = (b_i / w_i) / sum_j (b_j / w_j), w_i the clip w of vertex i
+ *       from O1 (float32, read exactly as a double).  An attribute linear
+ *       in the triangle's clip-space (or world-space) plane is then the value
+ *       at the point the sample's ray meets the plane, the standard
+ *       hyperbolic interpolation; with equal w it reduces to O11.
  *
  * The paper fixes none of the bit-level rules above (fixed-point format,
  * fill rule, depth format, rounding, tie-break, light model); they are the
@@ -72,6 +79,7 @@ typedef struct {
   int32_t X, Y;
   uint32_t Z;
   int32_t ok;
+  double w; /* clip w (O1), for O15 */
 } ovtx;
 
 static void vertex_stage_one(int W, int H, const float *p, const float *M, ovtx *o) {
@@ -88,6 +96,7 @@ static void vertex_stage_one(int W, int H, const float *p, const float *M, ovtx 
     c[0] = p[0]; c[1] = p[1]; c[2] = p[2]; c[3] = p[3];
   }
   o->X = 0; o->Y = 0; o->Z = 0; o->ok = 0;
+  o->w = (double)c[3];
   if (!(c[3] > 0.0f)) return;                                   /* O2 */
   float nx = c[0] / c[3], ny = c[1] / c[3], nz = c[2] / c[3];
   if (!(nz >= -1.0f && nz <= 1.0f)) return;                     /* O3 */
@@ -410,9 +419,13 @@ typedef struct {
   uint32_t z;
 } winner;
 
-/* barycentrics of the winning triangle at (px,py), or 0 if key is empty */
+#define FLAG_UNCLAMPED 1
+#define FLAG_PERSPECTIVE 2
+
+/* barycentrics of the winning triangle at (px,py), or 0 if key is empty;
+ * screen-space (O11), or perspective-correct (O15) when persp is set */
 static int pixel_winner(const ovtx *vs, int V, const int32_t *tris, uint64_t k, int px, int py,
-                        winner *o) {
+                        int persp, winner *o) {
   if (k == KEY_EMPTY) return 0;
   uint32_t id = (uint32_t)(k & 0xFFFFFFFFu);
   otri t;
@@ -424,6 +437,14 @@ static int pixel_winner(const ovtx *vs, int V, const int32_t *tris, uint64_t k, 
   for (int i = 0; i < 3; ++i) {
     o->b[i] = (double)w[i] / (double)t.A;
     o->vid[i] = t.vid[i];
+  }
+  if (persp) {
+    double q[3], sum = 0.0;
+    for (int i = 0; i < 3; ++i) {
+      q[i] = o->b[i] / vs[t.vid[i]].w;
+      sum += q[i];
+    }
+    for (int i = 0; i < 3; ++i) o->b[i] = q[i] / sum;
   }
   o->z = (uint32_t)(k >> 32);
   return 1;
@@ -462,16 +483,17 @@ static void shade_pixel(const winner *wn, const double *color, const double *nor
  * G-buffer halves (uint16 [H][W][4]) are written instead. */
 int oracle_shade(int W, int H, int V, const float *pos, int64_t T, const int32_t *tris,
                  const float *M, const double *color, const double *normal, const double *L,
-                 int mode, int unclamped, const uint64_t *key, double *rgba, uint16_t *gnormal,
+                 int mode, int flags, const uint64_t *key, double *rgba, uint16_t *gnormal,
                  uint16_t *galbedo) {
   (void)T;
+  const int unclamped = flags & FLAG_UNCLAMPED, persp = (flags & FLAG_PERSPECTIVE) != 0;
   ovtx *vs = vertex_stage_all(W, H, V, pos, M);
   for (int py = 0; py < H; ++py)
     for (int px = 0; px < W; ++px) {
       size_t p = (size_t)py * W + px;
       winner wn;
       double rgb[3] = {0, 0, 0}, n[3] = {0, 0, 0}, alb[3] = {0, 0, 0};
-      int hit = pixel_winner(vs, V, tris, key[p], px, py, &wn);
+      int hit = pixel_winner(vs, V, tris, key[p], px, py, persp, &wn);
       if (hit) shade_pixel(&wn, color, normal, L, mode, unclamped, rgb, n, alb);
       if (rgba) {
         for (int c = 0; c < 3; ++c) rgba[4 * p + c] = rgb[c];
@@ -540,15 +562,16 @@ int oracle_light_pass(int W, int H, const uint64_t *key, const uint16_t *gnormal
  * and for Gouraud dL/dc_v += g * b_v. */
 int oracle_backward(int W, int H, int V, const float *pos, int64_t T, const int32_t *tris,
                     const float *M, const double *color, const double *normal, const double *L,
-                    int mode, int unclamped, const uint64_t *key, const double *dl_drgba,
+                    int mode, int flags, const uint64_t *key, const double *dl_drgba,
                     double *dcolor, double *dnormal, double *dlight) {
   (void)T;
+  const int unclamped = flags & FLAG_UNCLAMPED, persp = (flags & FLAG_PERSPECTIVE) != 0;
   ovtx *vs = vertex_stage_all(W, H, V, pos, M);
   for (int py = 0; py < H; ++py)
     for (int px = 0; px < W; ++px) {
       size_t p = (size_t)py * W + px;
       winner wn;
-      if (!pixel_winner(vs, V, tris, key[p], px, py, &wn)) continue;
+      if (!pixel_winner(vs, V, tris, key[p], px, py, persp, &wn)) continue;
       const double *g = dl_drgba + 4 * p;
       double rgb[3], n[3], alb[3];
       shade_pixel(&wn, color, normal, L, mode, unclamped, rgb, n, alb);
@@ -580,8 +603,9 @@ int oracle_backward(int W, int H, int V, const float *pos, int64_t T, const int3
 /* L = sum over pixels and RGB channels of (rgb - target)^2, float64. */
 double oracle_loss(int W, int H, int V, const float *pos, int64_t T, const int32_t *tris,
                    const float *M, const double *color, const double *normal, const double *L,
-                   int mode, int unclamped, const uint64_t *key, const float *target) {
+                   int mode, int flags, const uint64_t *key, const float *target) {
   (void)T;
+  const int unclamped = flags & FLAG_UNCLAMPED, persp = (flags & FLAG_PERSPECTIVE) != 0;
   ovtx *vs = vertex_stage_all(W, H, V, pos, M);
   double acc = 0.0;
   for (int py = 0; py < H; ++py)
@@ -589,7 +613,7 @@ double oracle_loss(int W, int H, int V, const float *pos, int64_t T, const int32
       size_t p = (size_t)py * W + px;
       winner wn;
       double rgb[3] = {0, 0, 0}, n[3], alb[3];
-      if (pixel_winner(vs, V, tris, key[p], px, py, &wn))
+      if (pixel_winner(vs, V, tris, key[p], px, py, persp, &wn))
         shade_pixel(&wn, color, normal, L, mode, unclamped, rgb, n, alb);
       for (int c = 0; c < 3; ++c) {
         double e = rgb[c] - (double)target[4 * p + c];

@@ -138,14 +138,14 @@ def workload(args):
     return scene, cfg
 
 
-def cpu_baseline(scene, seconds: float) -> dict:
+def cpu_baseline(scene, seconds: float, perspective: bool = False) -> dict:
     """The oracle as it stands: bounding-box loop on all host cores + float64 shading."""
     import oracle
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
     reps, t0 = 0, time.perf_counter()
     while True:
         key, _ = oracle.raster_bbox(scene, threads=cores)
-        oracle.shade(scene, key)
+        oracle.shade(scene, key, perspective=perspective)
         reps += 1
         if time.perf_counter() - t0 >= seconds:
             break
@@ -242,6 +242,9 @@ def run_ours(args):
     if args.threads:
         r.set_option(L.PIKO_OPT_THREADS_PER_TILE, args.threads)
         cfg["threads_per_tile"] = args.threads
+    if args.perspective:
+        r.set_option(L.PIKO_OPT_PERSPECTIVE, 1)
+        cfg["attributes"] = "perspective-correct"
     if args.small_px:
         r.set_option(L.PIKO_OPT_SMALL_TRI_PIXELS, args.small_px)
         cfg["small_tri_pixels"] = args.small_px
@@ -324,7 +327,8 @@ def run_ours(args):
             prof = json.load(f)
         bin_px = args.bins * args.bins
         launch = {"bins": args.bins, "schedule": args.schedule,
-                  "threads": args.threads or (64 if bin_px <= 64 else (128 if bin_px <= 256 else 256))}
+                  "threads": args.threads or (64 if bin_px <= 64 else (128 if bin_px <= 256 else 256)),
+                  "perspective": bool(args.perspective)}
         # counters apply only to the same kernel sources in the same launch configuration
         if prof.get("kernel_hash") == kernel_hash() and prof.get("launch") == launch:
             traffic = prof.get("dram_bytes_per_launch")
@@ -376,6 +380,8 @@ def run_ours(args):
             rr = Rasterizer(scene.width, scene.height, args.bins, args.bins, args.schedule)
             if args.threads:
                 rr.set_option(L.PIKO_OPT_THREADS_PER_TILE, args.threads)
+            if args.perspective:
+                rr.set_option(L.PIKO_OPT_PERSPECTIVE, 1)
             d = DeviceScene.from_host(scene)
             f = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode)
             rr.forward(d, f)
@@ -447,7 +453,7 @@ def run_ours(args):
             "gpu_launches": 5 * K,
             "parity": "depth/ID bit-exact vs the CPU oracle in tests/test_gpu_parity.py (same workload)"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(scene, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(scene, args.cpu_seconds, args.perspective)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -828,6 +834,8 @@ def main():
                     help="tile schedule of the heightfield line (hardware: one CTA per tile, the fastest "
                          "of the bin-size x schedule sweep at 16x16)")
     ap.add_argument("--threads", type=int, default=0, help="Process CTA size (0: library default)")
+    ap.add_argument("--perspective", action="store_true",
+                    help="heightfield workload: perspective-correct attributes (PIKO_OPT_PERSPECTIVE)")
     ap.add_argument("--autotune", action="store_true",
                     help="heightfield workload: bin size, schedule and threads per bin from the autotuner")
     ap.add_argument("--small-px", type=int, default=0,

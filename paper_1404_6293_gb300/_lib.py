@@ -34,6 +34,7 @@ PIKO_OPT_SCHEDULE = 4
 PIKO_OPT_SMALL_TRI_PIXELS = 5
 PIKO_OPT_STATS = 6
 PIKO_OPT_BATCH_LAUNCH = 7
+PIKO_OPT_PERSPECTIVE = 8
 PIKO_NUM_STAGE_EVENTS = 6
 
 ERROR_NAMES = {

@@ -22,8 +22,8 @@ int batch_launch_backward(BatchState* bs, const piko_scene* scenes, int n, const
                           cudaStream_t stream, std::string& err);
 
 int piko_backward_launch(int W, int H, int mode, int unclamped, int T, int V, const int* tris, const int4* vtx,
-                         const float* color,
-                         const float* normal, const float* light, const unsigned long long* key,
+                         const float* color, const float* normal, const float* light, const float* invw,
+                         const unsigned long long* key,
                          const float* dl_drgba, float* dcolor, float* dnormal, float* dlight, int num_sms,
                          cudaStream_t s);
 
@@ -33,6 +33,7 @@ struct piko_raster {
   int nbins;
   int threads = 256;
   int unclamped = 0;
+  int perspective = 0;  // perspective-correct attributes (single-scene calls)
   int check_capacity = 1;
   int small_px = 32;
   int stats = 0;
@@ -46,6 +47,8 @@ struct piko_raster {
   long long vcap = 0;
   float* vdot = nullptr;  // n . L per vertex for Lambert
   long long dcap = 0;
+  float* invw = nullptr;  // 1 / clip w per vertex, with perspective-correct attributes
+  long long icap = 0;
   BinRect* rect = nullptr;
   long long tcap = 0;
   unsigned* bin_count = nullptr;  // 2 * nbins, zero between frames
@@ -150,6 +153,7 @@ void piko_raster_destroy(piko_raster* h) {
   cudaDeviceSynchronize();
   cudaFree(h->vtx);
   cudaFree(h->vdot);
+  cudaFree(h->invw);
   cudaFree(h->rect);
   cudaFree(h->bin_count);
   cudaFree(h->bin_off);
@@ -197,6 +201,10 @@ int piko_raster_set_option(piko_raster* h, int key, int value) {
       if (value != 0 && value != 1) return fail(h, PIKO_ERR_INVALID_ARG, "batch launch must be 0 or 1");
       h->batch_launch = value;
       return PIKO_OK;
+    case PIKO_OPT_PERSPECTIVE:
+      if (value != 0 && value != 1) return fail(h, PIKO_ERR_INVALID_ARG, "perspective must be 0 or 1");
+      h->perspective = value;
+      return PIKO_OK;
     case PIKO_OPT_SMALL_TRI_PIXELS:
       if (value < 0 || value > 4096) return fail(h, PIKO_ERR_INVALID_ARG, "small-triangle pixels out of range");
       h->small_px = value;
@@ -214,6 +222,7 @@ int piko_raster_reserve(piko_raster* h, int64_t max_vertices, int64_t max_triang
   int r;
   if ((r = grow(h, &h->vtx, &h->vcap, max_vertices, "vertex buffer")) != PIKO_OK) return r;
   if ((r = grow(h, &h->vdot, &h->dcap, max_vertices, "vertex light terms")) != PIKO_OK) return r;
+  if (h->perspective && (r = grow(h, &h->invw, &h->icap, max_vertices, "vertex 1/w")) != PIKO_OK) return r;
   if ((r = grow(h, &h->rect, &h->tcap, max_triangles, "bin rectangles")) != PIKO_OK) return r;
   if ((r = grow(h, &h->bin_tris, &h->ecap, max_bin_entries, "bin lists")) != PIKO_OK) return r;
   cudaError_t e = cudaDeviceSynchronize();
@@ -273,6 +282,7 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
   if ((r = grow(h, &h->vtx, &h->vcap, V, "vertex buffer")) != PIKO_OK) return r;
   const bool lambert = s->shade_mode == PIKO_SHADE_LAMBERT;
   if (lambert && (r = grow(h, &h->vdot, &h->dcap, V, "vertex light terms")) != PIKO_OK) return r;
+  if (h->perspective && (r = grow(h, &h->invw, &h->icap, V, "vertex 1/w")) != PIKO_OK) return r;
   if ((r = grow(h, &h->rect, &h->tcap, T, "bin rectangles")) != PIKO_OK) return r;
   if (h->ecap == 0 && (r = grow(h, &h->bin_tris, &h->ecap, (long long)T * 2 + 4096, "bin lists")) != PIKO_OK)
     return r;
@@ -282,7 +292,7 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
   if (ev) cudaEventRecord(h->stage_ev[0], st);
   if (h->stats) cudaMemsetAsync(&h->status->tests, 0, 4 * sizeof(unsigned long long), st);
   launch_vertex(h->W, h->H, V, s->pos, s->mvp, h->vtx, lambert ? s->normal : nullptr, s->light_dir,
-                lambert ? h->vdot : nullptr, h->num_sms, st);
+                lambert ? h->vdot : nullptr, h->perspective ? h->invw : nullptr, h->num_sms, st);
   if (ev) cudaEventRecord(h->stage_ev[1], st);
   for (int attempt = 0;; ++attempt) {
     if (h->stats && attempt > 0) cudaMemsetAsync(&h->status->binned, 0, sizeof(unsigned long long), st);
@@ -327,6 +337,7 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
   p.normal = s->normal;
   p.light = s->light_dir;
   p.vdot = h->vdot;
+  p.invw = h->perspective ? h->invw : nullptr;
   p.bin_off = h->bin_off;
   p.bin_tris = h->bin_tris;
   p.key_out = reinterpret_cast<unsigned long long*>(fb->key);
@@ -351,6 +362,9 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
 int piko_raster_forward_batch(piko_raster* h, const piko_scene* scenes, int n, piko_framebuffer* fbs,
                               const int32_t* bin_sizes, const int32_t* schedules, void* cuda_stream) {
   if (!h) return PIKO_ERR_INVALID_ARG;
+  if (h->unclamped || h->perspective)
+    return fail(h, PIKO_ERR_INVALID_ARG, "batch calls shade clamped and in screen space: unset PIKO_OPT_UNCLAMPED "
+                                         "and PIKO_OPT_PERSPECTIVE");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
   h->last_stream = st;
   int r = batch_prepare(h->batch, h->num_sms, scenes, n, fbs, bin_sizes, schedules, h->bin_w, h->bin_h, h->schedule,
@@ -378,6 +392,9 @@ int piko_raster_backward_batch(piko_raster* h, const piko_scene* scenes, int n, 
                                float* const* dl_dlight, void* cuda_stream) {
   if (!h) return PIKO_ERR_INVALID_ARG;
   if (!scenes || !fbs || n < 1) return fail(h, PIKO_ERR_INVALID_ARG, "backward_batch needs scenes and framebuffers");
+  if (h->unclamped || h->perspective)
+    return fail(h, PIKO_ERR_INVALID_ARG, "batch calls shade clamped and in screen space: unset PIKO_OPT_UNCLAMPED "
+                                         "and PIKO_OPT_PERSPECTIVE");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
   h->last_stream = st;
   return batch_launch_backward(h->batch, scenes, n, fbs, dl_drgba, dl_dcolor, dl_dnormal, dl_dlight, h->num_sms, st,
@@ -425,12 +442,14 @@ int piko_raster_backward(piko_raster* h, const piko_scene* s, const piko_framebu
   cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
   h->last_stream = st;
   if ((r = grow(h, &h->vtx, &h->vcap, s->num_vertices, "vertex buffer")) != PIKO_OK) return r;
+  if (h->perspective && (r = grow(h, &h->invw, &h->icap, s->num_vertices, "vertex 1/w")) != PIKO_OK) return r;
+  float* invw = h->perspective ? h->invw : nullptr;
   // the vertex stage runs again so that backward does not depend on which
   // scene the handle rasterized last
-  launch_vertex(h->W, h->H, s->num_vertices, s->pos, s->mvp, h->vtx, nullptr, nullptr, nullptr, h->num_sms, st);
+  launch_vertex(h->W, h->H, s->num_vertices, s->pos, s->mvp, h->vtx, nullptr, nullptr, nullptr, invw, h->num_sms,
+                st);
   if (piko_backward_launch(h->W, h->H, s->shade_mode, h->unclamped, s->num_triangles, s->num_vertices, s->tris,
-                           h->vtx, s->color, s->normal,
-                           s->light_dir, reinterpret_cast<const unsigned long long*>(fwd->key), dl_drgba, dl_dcolor,
+                           h->vtx, s->color, s->normal, s->light_dir, invw, reinterpret_cast<const unsigned long long*>(fwd->key), dl_drgba, dl_dcolor,
                            dl_dnormal, dl_dlight, h->num_sms, st) != 0)
     return cuda_fail(h, cudaGetLastError(), "backward launch");
   return PIKO_OK;

@@ -10,6 +10,7 @@ struct BackwardParams {
   int ntx, ntiles;
 };
 
+template <bool PERSP>
 __global__ void __launch_bounds__(BWD_THREADS, 1024 / BWD_THREADS) k_backward(BackwardParams p) {
   extern __shared__ __align__(16) unsigned char bwd_smem_raw[];
   BwdSmem& sm = *reinterpret_cast<BwdSmem*>(bwd_smem_raw);
@@ -22,7 +23,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 1024 / BWD_THREADS) k_backward(Ba
   __syncthreads();
   for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
     const int ty = tile / p.ntx, tx = tile - ty * p.ntx;
-    backward_tile(p.sc, tx * BWD_TILE_W, ty * BWD_TILE_H, sm, L0, L1, L2, gl0, gl1, gl2);
+    backward_tile<PERSP>(p.sc, tx * BWD_TILE_W, ty * BWD_TILE_H, sm, L0, L1, L2, gl0, gl1, gl2);
   }
   if (p.sc.dlight && p.sc.mode == PIKO_SHADE_LAMBERT) bwd_flush_light(sm, p.sc.dlight, gl0, gl1, gl2);
 }
@@ -40,6 +41,7 @@ struct PixelBwdParams {
   const float* color;
   const float* normal;
   const float* light;
+  const float* invw;
   const unsigned long long* key;
   const float4* dl_drgba;
   float* dcolor;
@@ -51,6 +53,7 @@ struct PixelBwdParams {
 constexpr int PIX_THREADS = 256;
 constexpr int PIX_VALS = 18;  // per pixel: 3 vertices x (3 colour + 3 normal)
 
+template <bool PERSP>
 __global__ void __launch_bounds__(PIX_THREADS) k_backward_pixel(PixelBwdParams p) {
   __shared__ float sval[PIX_THREADS / 32][PIX_VALS][32];
   __shared__ float sred[PIX_THREADS / 32][3];
@@ -91,7 +94,9 @@ __global__ void __launch_bounds__(PIX_THREADS) k_backward_pixel(PixelBwdParams p
       const long long w1 = (long long)(s.X0 - s.X2) * (Py - s.Y2) - (long long)(s.Y0 - s.Y2) * (Px - s.X2);
       const long long w2 = (long long)(s.X1 - s.X0) * (Py - s.Y0) - (long long)(s.Y1 - s.Y0) * (Px - s.X0);
       const float fA = (float)s.A;
-      const float b[3] = {__fdiv_rn((float)w0, fA), __fdiv_rn((float)w1, fA), __fdiv_rn((float)w2, fA)};
+      float b[3] = {__fdiv_rn((float)w0, fA), __fdiv_rn((float)w1, fA), __fdiv_rn((float)w2, fA)};
+      if (PERSP)
+        perspective_bary(b[0], b[1], b[2], __ldg(p.invw + vid[0]), __ldg(p.invw + vid[1]), __ldg(p.invw + vid[2]));
       const float4 g = __ldg(p.dl_drgba + i);
       if (p.mode == PIKO_SHADE_GOURAUD) {
 #pragma unroll
@@ -187,9 +192,13 @@ int backward_grid(int tiles, int num_sms) {
   int& per_sm = per_sm_of[dev & 63];
   if (per_sm == 0) {
     int v = 0;
-    if (cudaFuncSetAttribute(k_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BwdSmem)) !=
+    // both instances share the launch bounds and the shared-memory size
+    if (cudaFuncSetAttribute(k_backward<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BwdSmem)) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_backward, BWD_THREADS, sizeof(BwdSmem)) != cudaSuccess ||
+        cudaFuncSetAttribute(k_backward<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BwdSmem)) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_backward<false>, BWD_THREADS, sizeof(BwdSmem)) !=
+            cudaSuccess ||
         v < 1)
       v = 1;
     per_sm = v;
@@ -204,8 +213,8 @@ int backward_grid(int tiles, int num_sms) {
 using namespace piko;
 
 int piko_backward_launch(int W, int H, int mode, int unclamped, int T, int V, const int* tris, const int4* vtx,
-                         const float* color,
-                         const float* normal, const float* light, const unsigned long long* key,
+                         const float* color, const float* normal, const float* light, const float* invw,
+                         const unsigned long long* key,
                          const float* dl_drgba, float* dcolor, float* dnormal, float* dlight, int num_sms,
                          cudaStream_t s) {
   const long long npix = (long long)W * H;
@@ -213,24 +222,30 @@ int piko_backward_launch(int W, int H, int mode, int unclamped, int T, int V, co
     // more than one triangle per four pixels: triangles of a few pixels
     PixelBwdParams p;
     p.W = W; p.H = H; p.mode = mode; p.unclamped = unclamped; p.T = T; p.V = V;
-    p.tris = tris; p.vtx = vtx; p.color = color; p.normal = normal; p.light = light;
+    p.tris = tris; p.vtx = vtx; p.color = color; p.normal = normal; p.light = light; p.invw = invw;
     p.key = key; p.dl_drgba = reinterpret_cast<const float4*>(dl_drgba);
     p.dcolor = dcolor; p.dnormal = dnormal; p.dlight = dlight;
     long long blocks = (npix + PIX_THREADS - 1) / PIX_THREADS;
     if (blocks > (long long)num_sms * 4) blocks = (long long)num_sms * 4;
     if (blocks < 1) blocks = 1;
-    k_backward_pixel<<<(int)blocks, PIX_THREADS, 0, s>>>(p);
+    if (invw)
+      k_backward_pixel<true><<<(int)blocks, PIX_THREADS, 0, s>>>(p);
+    else
+      k_backward_pixel<false><<<(int)blocks, PIX_THREADS, 0, s>>>(p);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
   }
   BackwardParams p;
   BwdScene& c = p.sc;
   c.W = W; c.H = H; c.mode = mode; c.unclamped = unclamped; c.T = T; c.V = V;
-  c.tris = tris; c.vtx = vtx; c.color = color; c.normal = normal; c.light = light;
+  c.tris = tris; c.vtx = vtx; c.color = color; c.normal = normal; c.light = light; c.invw = invw;
   c.key = key; c.dl = reinterpret_cast<const float4*>(dl_drgba);
   c.dcolor = dcolor; c.dnormal = dnormal; c.dlight = dlight;
   p.ntx = (W + BWD_TILE_W - 1) / BWD_TILE_W;
   p.ntiles = p.ntx * ((H + BWD_TILE_H - 1) / BWD_TILE_H);
   const int blocks = backward_grid(p.ntiles, num_sms);
-  k_backward<<<blocks, BWD_THREADS, sizeof(BwdSmem), s>>>(p);
+  if (invw)
+    k_backward<true><<<blocks, BWD_THREADS, sizeof(BwdSmem), s>>>(p);
+  else
+    k_backward<false><<<blocks, BWD_THREADS, sizeof(BwdSmem), s>>>(p);
   return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }

@@ -334,6 +334,7 @@ __device__ void load_tile_scene(const BatchParams& b, int s, TileScene& t) {
   t.normal = d.normal;
   t.light = d.light;
   t.vdot = b.vdot + d.vtx_base;
+  t.invw = nullptr;  // batches interpolate in screen space
   t.key_out = d.key_out;
   t.rgba_out = d.rgba_out;
   t.gnorm_out = d.gnorm_out;
@@ -458,6 +459,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 1024 / BWD_THREADS) k_batch_backw
     BwdScene c;
     c.W = d.g.W; c.H = d.g.H; c.mode = d.mode; c.unclamped = 0; c.T = d.T; c.V = d.V;
     c.tris = d.tris; c.vtx = b.vtx + d.vtx_base; c.color = d.color; c.normal = d.normal; c.light = d.light;
+    c.invw = nullptr;  // batches interpolate in screen space
     c.key = d.key_out; c.dl = d.dl; c.dcolor = d.dcolor; c.dnormal = d.dnormal; c.dlight = d.dlight;
     float L0 = 0.f, L1 = 0.f, L2 = 0.f;
     if (c.mode == PIKO_SHADE_LAMBERT) {
@@ -607,8 +609,8 @@ int batch_prepare(BatchState*& bs, int num_sms, const piko_scene* scenes, int n,
     x.g.nbx = (s.width + bw - 1) / bw; x.g.nby = (s.height + bh - 1) / bh;
     x.V = s.num_vertices; x.T = s.num_triangles; x.mode = s.shade_mode; x.schedule = sched;
     x.vtx_base = (int)tv; x.tri_base = (int)tt; x.bin_base = (int)tb; x.pix_base = 0;
-    tile_layout(s.num_triangles, bw * bh, s.shade_mode, s.color != nullptr, 255, x.slot_bits, x.nslots, x.rec_stride,
-                slots_hint);
+    tile_layout(s.num_triangles, bw * bh, s.shade_mode, s.color != nullptr, false, 255, x.slot_bits, x.nslots,
+                x.rec_stride, slots_hint);
     x.pos = reinterpret_cast<const float4*>(s.pos);
     x.tris = s.tris; x.mvp = s.mvp; x.color = s.color; x.normal = s.normal; x.light = s.light_dir;
     x.key_out = reinterpret_cast<unsigned long long*>(f.key);

@@ -59,6 +59,7 @@ struct BwdScene {
   const float* color;
   const float* normal;
   const float* light;
+  const float* invw;  // 1 / clip w per vertex: perspective-correct attributes (NULL: screen-space)
   const unsigned long long* key;
   const float4* dl;
   float* dcolor;
@@ -134,6 +135,8 @@ __device__ __forceinline__ void bwd_add_term(const BwdScene& sc, const int* r, i
 // One tile with its top-left pixel (x0, y0).  Entered and left with a clear
 // hash table (bwd_clear once per CTA before the first tile); blockDim.x must
 // be BWD_THREADS.  gl* collect this thread's share of dL/dL.
+// PERSP: perspective-correct barycentrics (sc.invw set).
+template <bool PERSP = false>
 __device__ __forceinline__ void backward_tile(const BwdScene& sc, int x0, int y0, BwdSmem& sm, float L0, float L1,
                                               float L2, float& gl0, float& gl1, float& gl2) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -225,7 +228,9 @@ __device__ __forceinline__ void backward_tile(const BwdScene& sc, int x0, int y0
     const long long w2 = (long long)(X1 - X0) * (Py - Y0) - (long long)(Y1 - Y0) * (Px - X0);
     const long long w0 = A - w1 - w2;  // the three edge functions sum to A
     const float rA = __int_as_float(r[RB_T]);
-    const float b[3] = {(float)w0 * rA, (float)w1 * rA, (float)w2 * rA};
+    float b[3] = {(float)w0 * rA, (float)w1 * rA, (float)w2 * rA};
+    if (PERSP)
+      perspective_bary(b[0], b[1], b[2], __ldg(sc.invw + vid[0]), __ldg(sc.invw + vid[1]), __ldg(sc.invw + vid[2]));
     const float4 g = __ldg(sc.dl + o);
     if (sc.mode == PIKO_SHADE_GOURAUD) {
 #pragma unroll

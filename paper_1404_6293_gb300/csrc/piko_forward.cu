@@ -15,10 +15,11 @@ namespace piko {
 // ======================================================================
 // Vertex stage
 // ======================================================================
+template <bool INVW>
 __global__ void __launch_bounds__(256) k_vertex(int W, int H, int V, const float4* __restrict__ pos,
                                                 const float* __restrict__ mvp, int4* __restrict__ vtx,
                                                 const float* __restrict__ normal, const float* __restrict__ light,
-                                                float* __restrict__ vdot) {
+                                                float* __restrict__ vdot, float* __restrict__ invw) {
   pdl_launch_dependents();  // the count pass may be scheduled; it waits for this grid before reading
   __shared__ float m[16];
   const bool has_m = mvp != nullptr;
@@ -35,17 +36,30 @@ __global__ void __launch_bounds__(256) k_vertex(int W, int H, int V, const float
     if (vdot) vdot[i] = __ldg(normal + 3 * (size_t)i) * L0 + __ldg(normal + 3 * (size_t)i + 1) * L1 +
                         __ldg(normal + 3 * (size_t)i + 2) * L2;
     // one 16-byte load per vertex, coalesced across the warp
-    vtx[i] = snap_vertex(__ldg(pos + i), has_m ? m : nullptr, fW, fH);
+    if (INVW) {
+      float w;
+      vtx[i] = snap_vertex(__ldg(pos + i), has_m ? m : nullptr, fW, fH, &w);
+      // 1 / clip w for perspective-correct attributes (unused when w <= 0:
+      // the vertex culls every triangle it belongs to)
+      invw[i] = w > 0.0f ? __fdiv_rn(1.0f, w) : 0.0f;
+    } else {
+      vtx[i] = snap_vertex(__ldg(pos + i), has_m ? m : nullptr, fW, fH);
+    }
   }
 }
 
 void launch_vertex(int W, int H, int V, const float* pos, const float* mvp, int4* vtx, const float* normal,
-                   const float* light, float* vdot, int num_sms, cudaStream_t s) {
+                   const float* light, float* vdot, float* invw, int num_sms, cudaStream_t s) {
   if (V <= 0) return;
   // one vertex per thread: every load is in flight at once
   (void)num_sms;
   const int blocks = (V + 255) / 256;
-  k_vertex<<<blocks, 256, 0, s>>>(W, H, V, reinterpret_cast<const float4*>(pos), mvp, vtx, normal, light, vdot);
+  if (invw)
+    k_vertex<true><<<blocks, 256, 0, s>>>(W, H, V, reinterpret_cast<const float4*>(pos), mvp, vtx, normal, light, vdot,
+                                          invw);
+  else
+    k_vertex<false><<<blocks, 256, 0, s>>>(W, H, V, reinterpret_cast<const float4*>(pos), mvp, vtx, normal, light,
+                                           vdot, nullptr);
 }
 
 // ======================================================================

@@ -164,6 +164,16 @@ __device__ __forceinline__ unsigned depth_of(long long w1, long long w2, const T
   return (unsigned)(s.Z0 + q);
 }
 
+// Perspective-correct barycentrics from screen-space ones:
+// b'_i = (b_i / w_i) / sum_j (b_j / w_j), given 1/w_i.
+__device__ __forceinline__ void perspective_bary(float& b0, float& b1, float& b2, float iw0, float iw1, float iw2) {
+  const float q0 = b0 * iw0, q1 = b1 * iw1, q2 = b2 * iw2;
+  const float r = __fdiv_rn(1.0f, q0 + q1 + q2);
+  b0 = q0 * r;
+  b1 = q1 * r;
+  b2 = q2 * r;
+}
+
 // ------------------------------------------------------------ vertex stage
 // ((m0*x + m1*y) + m2*z) + m3*w, every operation rounded, no contraction
 __device__ __forceinline__ float mvp_row(const float* m, float4 p) {
@@ -175,8 +185,9 @@ __device__ __forceinline__ float mvp_row(const float* m, float4 p) {
 }
 
 // Transform (m may be NULL for the identity), divide, viewport, 16.8 snap:
-// {X, Y, Z, 1}, or all zero for a vertex that culls its triangles.
-__device__ __forceinline__ int4 snap_vertex(float4 p, const float* m, float fW, float fH) {
+// {X, Y, Z, 1}, or all zero for a vertex that culls its triangles.  *clip_w
+// (when given) receives the clip-space w.
+__device__ __forceinline__ int4 snap_vertex(float4 p, const float* m, float fW, float fH, float* clip_w = nullptr) {
   float c0 = p.x, c1 = p.y, c2 = p.z, c3 = p.w;
   if (m) {
     c0 = mvp_row(m + 0, p);
@@ -184,6 +195,7 @@ __device__ __forceinline__ int4 snap_vertex(float4 p, const float* m, float fW, 
     c2 = mvp_row(m + 8, p);
     c3 = mvp_row(m + 12, p);
   }
+  if (clip_w) *clip_w = c3;
   int4 o = make_int4(0, 0, 0, 0);
   if (c3 > 0.0f) {
     const float nx = __fdiv_rn(c0, c3), ny = __fdiv_rn(c1, c3), nz = __fdiv_rn(c2, c3);
@@ -232,6 +244,7 @@ struct ProcessParams {
   const float* normal;
   const float* light;
   const float* vdot;  // n_v . L per vertex (Lambert)
+  const float* invw;  // 1 / clip w per vertex: perspective-correct attributes (NULL: screen-space)
   const unsigned* bin_off;
   const unsigned* bin_tris;
   unsigned long long* key_out;
@@ -245,7 +258,7 @@ struct ProcessParams {
 // Lambert term is linear in the interpolated normal, so per-vertex dots
 // interpolate to the same value).
 void launch_vertex(int W, int H, int V, const float* pos, const float* mvp, int4* vtx, const float* normal,
-                   const float* light, float* vdot, int num_sms, cudaStream_t s);
+                   const float* light, float* vdot, float* invw, int num_sms, cudaStream_t s);
 // Count pass and scan (two launches): bin_count holds 2 * nbins counters
 // (single-bin and multi-bin entries), zero between frames; the scan turns
 // them into CSR offsets and scatter cursors (capacity: entries the bin lists

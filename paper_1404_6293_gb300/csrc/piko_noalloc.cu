@@ -135,7 +135,7 @@ extern "C" int piko_raster_forward_noalloc(const piko_scene* s, piko_framebuffer
   }
   const bool lambert = s->shade_mode == PIKO_SHADE_LAMBERT;
   launch_vertex(g.W, g.H, s->num_vertices, s->pos, s->mvp, vtx, lambert ? s->normal : nullptr, s->light_dir,
-                lambert ? vdot : nullptr, num_sms, st);
+                lambert ? vdot : nullptr, nullptr, num_sms, st);
   launch_setup_count(g, s->num_triangles, s->tris, s->num_vertices, vtx, rect, bin_count, status, 0, num_sms, st);
   launch_scan(nbins, bin_count, bin_off, cursor, (unsigned long long)PIKO_NOALLOC_MAX_BIN_ENTRIES, status, chunk_state,
               ++g_scan_epoch, st);
@@ -158,6 +158,7 @@ extern "C" int piko_raster_forward_noalloc(const piko_scene* s, piko_framebuffer
   p.normal = s->normal;
   p.light = s->light_dir;
   p.vdot = vdot;
+  p.invw = nullptr;  // screen-space attributes only
   p.bin_off = bin_off;
   p.bin_tris = bin_tris;
   p.key_out = reinterpret_cast<unsigned long long*>(fb->key);

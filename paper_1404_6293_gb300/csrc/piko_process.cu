@@ -24,6 +24,7 @@ __host__ __device__ inline TileScene scene_of(const ProcessParams& p) {
   sc.normal = p.normal;
   sc.light = p.light;
   sc.vdot = p.vdot;
+  sc.invw = p.invw;
   sc.key_out = p.key_out;
   sc.rgba_out = p.rgba_out;
   sc.gnorm_out = p.gnorm_out;
@@ -38,14 +39,15 @@ __host__ __device__ inline TileScene scene_of(const ProcessParams& p) {
 // loops for occupancy (about 120 registers uncapped); the one-CTA-per-tile
 // instance fits 64 registers without spilling.
 // One instance per schedule (SCHED = PIKO_SCHED_*), so that each carries
-// only its own tile loop, and per value of the work-counter option (STATS),
-// so that the counters hold no registers when they are off.  The scene is
+// only its own tile loop, per value of the work-counter option (STATS), so
+// that the counters hold no registers when they are off, and per attribute
+// interpolation (PERSP: perspective-correct).  The scene is
 // read in place from the grid-constant parameter block.
 struct ProcessLaunch {
   ProcessParams p;
   TileScene sc;
 };
-template <int SCHED, bool STATS>
+template <int SCHED, bool STATS, bool PERSP>
 __global__ void __maxnreg__(PIKO_PROCESS_MAXNREG) k_process(const __grid_constant__ ProcessLaunch pl) {
   const ProcessParams& p = pl.p;
   extern __shared__ __align__(16) unsigned long long smem[];
@@ -84,7 +86,7 @@ __global__ void __maxnreg__(PIKO_PROCESS_MAXNREG) k_process(const __grid_constan
     }
     if (tile >= p.ntiles) break;
     const unsigned beg = __ldg(p.bin_off + tile), end = __ldg(p.bin_off + tile + 1);
-    process_tile<STATS>(sc, tile, beg, end, p.bin_tris, sm, big_base, st);
+    process_tile<STATS, PERSP>(sc, tile, beg, end, p.bin_tris, sm, big_base, st);
   }
   if (STATS) {  // one atomic per warp: same-address atomics from every thread serialise
     for (int o = 16; o > 0; o >>= 1) {
@@ -103,8 +105,8 @@ __global__ void __maxnreg__(PIKO_PROCESS_MAXNREG) k_process(const __grid_constan
 // ---------------------------------------------------------------- host side
 static void layout(ProcessParams& p, int threads) {
   (void)threads;
-  tile_layout(p.num_triangles, 1 << (p.g.bshift_x + p.g.bshift_y), p.mode, p.color != nullptr, 511, p.slot_bits,
-              p.nslots, p.rec_stride, p.slots_hint);
+  tile_layout(p.num_triangles, 1 << (p.g.bshift_x + p.g.bshift_y), p.mode, p.color != nullptr, p.invw != nullptr, 511,
+              p.slot_bits, p.nslots, p.rec_stride, p.slots_hint);
 }
 
 static size_t smem_bytes(const ProcessParams& p, int threads) {
@@ -113,15 +115,16 @@ static size_t smem_bytes(const ProcessParams& p, int threads) {
 
 using ProcessKernel = void (*)(ProcessLaunch);
 
-template <bool STATS>
+template <bool STATS, bool PERSP>
 static ProcessKernel process_kernel_of(int schedule) {
-  if (schedule == PIKO_SCHED_DYNAMIC) return k_process<PIKO_SCHED_DYNAMIC, STATS>;
-  if (schedule == PIKO_SCHED_HARDWARE) return k_process<PIKO_SCHED_HARDWARE, STATS>;
-  return k_process<PIKO_SCHED_STATIC, STATS>;
+  if (schedule == PIKO_SCHED_DYNAMIC) return k_process<PIKO_SCHED_DYNAMIC, STATS, PERSP>;
+  if (schedule == PIKO_SCHED_HARDWARE) return k_process<PIKO_SCHED_HARDWARE, STATS, PERSP>;
+  return k_process<PIKO_SCHED_STATIC, STATS, PERSP>;
 }
 
 static ProcessKernel process_kernel(const ProcessParams& p) {
-  return p.stats ? process_kernel_of<true>(p.schedule) : process_kernel_of<false>(p.schedule);
+  if (p.invw) return p.stats ? process_kernel_of<true, true>(p.schedule) : process_kernel_of<false, true>(p.schedule);
+  return p.stats ? process_kernel_of<true, false>(p.schedule) : process_kernel_of<false, false>(p.schedule);
 }
 
 cudaError_t process_occupancy(const ProcessParams& p0, int threads, int* blocks_per_sm) {

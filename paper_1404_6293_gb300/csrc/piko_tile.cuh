@@ -39,6 +39,7 @@ struct TileScene {
   const float* normal;
   const float* light;
   const float* vdot;
+  const float* invw;  // 1 / clip w per vertex, or NULL for screen-space attributes
   unsigned long long* key_out;
   float4* rgba_out;
   uint2* gnorm_out;
@@ -62,15 +63,18 @@ struct TileStats {
   unsigned long long tests, frags, shaded;
 };
 
-// record words: 0..5 X0 Y0 X1 Y1 X2 Y2 (oriented), 6 = 1/A (float), then attributes
+// record words: 0..5 X0 Y0 X1 Y1 X2 Y2 (oriented), 6 = 1/A (float), then the
+// attributes, then (perspective-correct attributes only) 1/w of the three
+// vertices
 constexpr int R_RA = 6;
 constexpr int R_ATTR = 7;
 
-__device__ __forceinline__ int rec_attr_count(int mode, bool has_color) {
+__host__ __device__ __forceinline__ int rec_attr_count(int mode, bool has_color) {
   if (mode == PIKO_SHADE_GOURAUD) return 9;              // c0 c1 c2
   if (mode == PIKO_SHADE_LAMBERT) return has_color ? 12 : 3;  // d0 d1 d2 (n_i . L) [+ c0 c1 c2]
   return 18;                                             // n0 n1 n2 c0 c1 c2
 }
+
 
 // ---------------------------------------------------------------- raster
 template <typename I>
@@ -291,10 +295,16 @@ __device__ __forceinline__ void rec_bary(const int* r, int x, int y, float& b0, 
   b0 = 1.0f - b1 - b2;
 }
 
+// PERSP: perspective-correct barycentrics (the record holds the vertices' 1/w)
+template <bool PERSP>
 __device__ __forceinline__ void shade_from_record(const TileScene& p, const int* r, int x, int y, size_t o) {
   float b0, b1, b2;
   rec_bary(r, x, y, b0, b1, b2);
   const float* a = reinterpret_cast<const float*>(r + R_ATTR);
+  if (PERSP) {
+    const float* iw = a + rec_attr_count(p.mode, p.color != nullptr);
+    perspective_bary(b0, b1, b2, iw[0], iw[1], iw[2]);
+  }
   if (p.mode == PIKO_SHADE_GOURAUD) {
     if (p.rgba_out)
       p.rgba_out[o] = make_float4(b0 * a[0] + b1 * a[3] + b2 * a[6], b0 * a[1] + b1 * a[4] + b2 * a[7],
@@ -327,6 +337,7 @@ __device__ __forceinline__ void shade_from_record(const TileScene& p, const int*
 }
 
 // Fallback for winners without a record: everything re-read from global memory.
+template <bool PERSP>
 __device__ __forceinline__ void shade_from_global(const TileScene& p, unsigned t, int x, int y, size_t o) {
   TriSetup s;
   setup_triangle(__ldg(p.tris + 3 * (size_t)t), __ldg(p.tris + 3 * (size_t)t + 1), __ldg(p.tris + 3 * (size_t)t + 2),
@@ -335,7 +346,8 @@ __device__ __forceinline__ void shade_from_global(const TileScene& p, unsigned t
   const long long w1 = (long long)(s.X0 - s.X2) * (Py - s.Y2) - (long long)(s.Y0 - s.Y2) * (Px - s.X2);
   const long long w2 = (long long)(s.X1 - s.X0) * (Py - s.Y0) - (long long)(s.Y1 - s.Y0) * (Px - s.X0);
   const float rA = approx_rcp((float)s.A);
-  const float b1 = (float)w1 * rA, b2 = (float)w2 * rA, b0 = 1.0f - b1 - b2;
+  float b1 = (float)w1 * rA, b2 = (float)w2 * rA, b0 = 1.0f - b1 - b2;
+  if (PERSP) perspective_bary(b0, b1, b2, __ldg(p.invw + s.v0), __ldg(p.invw + s.v1), __ldg(p.invw + s.v2));
   float c0 = 0.80f, c1 = 0.75f, c2 = 0.65f;
   if (p.color) {
     const float* q0 = p.color + 3 * (size_t)s.v0;
@@ -365,12 +377,18 @@ __device__ __forceinline__ void shade_from_global(const TileScene& p, unsigned t
   if (p.rgba_out) p.rgba_out[o] = make_float4(c0 * d, c1 * d, c2 * d, 1.0f);
 }
 
-// Fills the shared-memory record of one bin entry.
+// Fills the shared-memory record of one bin entry (PERSP: with 1/w).
+template <bool PERSP>
 __device__ __forceinline__ void fill_record(const TileScene& p, const TriSetup& s, int* r) {
   r[0] = s.X0; r[1] = s.Y0; r[2] = s.X1; r[3] = s.Y1; r[4] = s.X2; r[5] = s.Y2;
   r[R_RA] = __float_as_int(approx_rcp((float)s.A));
   float* a = reinterpret_cast<float*>(r + R_ATTR);
   const int v[3] = {s.v0, s.v1, s.v2};
+  if (PERSP) {
+    float* iw = a + rec_attr_count(p.mode, p.color != nullptr);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) iw[j] = __ldg(p.invw + v[j]);
+  }
   if (p.mode == PIKO_SHADE_LAMBERT) {
 #pragma unroll
     for (int j = 0; j < 3; ++j) a[j] = __ldg(p.vdot + v[j]);
@@ -410,7 +428,9 @@ __device__ __forceinline__ void load_setup(const TileScene& p, unsigned t, TriSe
 // Process one tile: tile is the scene-local tile index, [beg, end) its range
 // in bin_tris.  Called by every thread of the CTA (nt threads, a power of
 // two); contains CTA barriers.  big_base tracks the large-triangle ring.
-template <bool STATS>
+// PERSP: perspective-correct attributes (p.invw set); one kernel instance
+// per value so that the screen-space path carries none of it.
+template <bool STATS, bool PERSP = false>
 __device__ __forceinline__ void process_tile(const TileScene& p, int tile, unsigned beg, unsigned end,
                                              const unsigned* __restrict__ bin_tris, const TileSmem& sm,
                                              unsigned& big_base, TileStats& st) {
@@ -430,7 +450,7 @@ __device__ __forceinline__ void process_tile(const TileScene& p, int tile, unsig
       const unsigned slot = (i - beg) < (unsigned)p.nslots ? (i - beg) : no_slot;
       TriSetup s;
       load_setup(p, t, s);
-      if (slot != no_slot) fill_record(p, s, sm.srec + slot * p.rec_stride);
+      if (slot != no_slot) fill_record<PERSP>(p, s, sm.srec + slot * p.rec_stride);
       const int minX = min(s.X0, min(s.X1, s.X2)), maxX = max(s.X0, max(s.X1, s.X2));
       const int minY = min(s.Y0, min(s.Y1, s.Y2)), maxY = max(s.Y0, max(s.Y1, s.Y2));
       int px0, px1, py0, py1;
@@ -501,9 +521,9 @@ __device__ __forceinline__ void process_tile(const TileScene& p, int tile, unsig
     p.key_out[o] = ((unsigned long long)z << 32) | t;
     if (STATS) ++st.shaded;
     if (slot != no_slot)
-      shade_from_record(p, sm.srec + slot * p.rec_stride, x, y, o);
+      shade_from_record<PERSP>(p, sm.srec + slot * p.rec_stride, x, y, o);
     else
-      shade_from_global(p, t, x, y, o);
+      shade_from_global<PERSP>(p, t, x, y, o);
   }
   __syncthreads();
 }
@@ -514,8 +534,9 @@ __device__ __forceinline__ void process_tile(const TileScene& p, int tile, unsig
 // (0: as many as allowed) sizes the record area: shared memory taken by
 // records is taken from L1, which serves the kernel's gathers, so records
 // are sized for the tiles' typical entry count rather than the largest.
-inline void tile_layout(int num_triangles, int bin_px, int mode, bool has_color, int max_slots, int& slot_bits,
-                        int& nslots, int& rec_stride, int want_slots = 0) {
+// persp adds the three vertices' 1/w (perspective-correct attributes).
+inline void tile_layout(int num_triangles, int bin_px, int mode, bool has_color, bool persp, int max_slots,
+                        int& slot_bits, int& nslots, int& rec_stride, int want_slots = 0) {
   int id_bits = 1;
   while (id_bits < 32 && (1LL << id_bits) <= (long long)num_triangles) ++id_bits;
   slot_bits = 40 - id_bits < 16 ? 40 - id_bits : 16;
@@ -523,8 +544,7 @@ inline void tile_layout(int num_triangles, int bin_px, int mode, bool has_color,
   if (want_slots > 0 && want_slots < want) want = want_slots;
   const int cap = (1 << slot_bits) - 1;
   nslots = want < cap ? want : cap;
-  const int attrs = mode == PIKO_SHADE_GOURAUD ? 9 : (mode == PIKO_SHADE_LAMBERT ? (has_color ? 12 : 3) : 18);
-  rec_stride = R_ATTR + attrs;
+  rec_stride = R_ATTR + rec_attr_count(mode, has_color) + (persp ? 3 : 0);
   if ((rec_stride & 1) == 0) ++rec_stride;
 }
 

@@ -594,6 +594,8 @@ def run_extra(args):
         dl = torch.zeros_like(ds.light_dir)
         bins, scheds = [(args.bins, args.bins)] * nv, ["dynamic" if args.schedule == "hardware" else args.schedule] * nv
         rb = Rasterizer(W, H, args.bins, args.bins)
+        if args.perspective:
+            rb.set_option(L.PIKO_OPT_PERSPECTIVE, 1)
         rb.forward_batch(views, fbs, bins, scheds)
         assert rb.status()[0] == 0
         rb.set_option(L.PIKO_OPT_CHECK_CAPACITY, 0)
@@ -648,7 +650,8 @@ def run_extra(args):
                                 "bin": [args.bins, args.bins], "schedule": scheds[0],
                                 "how": "the 64 views as one forward_batch and one backward_batch, each replayed "
                                        "from a CUDA graph",
-                                "l2": "flushed between steps (256 MiB write)"},
+                                "l2": "flushed between steps (256 MiB write)",
+                                **({"attributes": "perspective-correct"} if args.perspective else {})},
                      "forward_ms": float(fwd.mean()), "backward_ms": float(bwd.mean()),
                      "covered_pixels": covered,
                      "roofline": {"kernel": "backward (64 views, incl. loss gradient)", "bound": "hbm",
@@ -661,10 +664,10 @@ def run_extra(args):
             sv = S.Scene(W, H, sph.pos, sph.tris, color=sph.color, normal=sph.normal, mvp=mvps[0],
                          light_dir=sph.light_dir, shade_mode=sph.shade_mode)
             key, _ = oracle.raster_bbox(sv, threads=len(os.sched_getaffinity(0)))
-            rgba = oracle.shade(sv, key)
+            rgba = oracle.shade(sv, key, perspective=args.perspective)
             gg = np.zeros((H, W, 4))
             gg[..., :3] = 2 * (rgba[..., :3] - tgt[0].cpu().numpy()[..., :3])
-            oracle.backward(sv, key, gg)
+            oracle.backward(sv, key, gg, perspective=args.perspective)
             dt = time.perf_counter() - t0
             line["cpu_baseline"] = {"value": sph.num_triangles / dt / 1e6, "unit": UNIT,
                                     "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
@@ -835,7 +838,7 @@ def main():
                          "of the bin-size x schedule sweep at 16x16)")
     ap.add_argument("--threads", type=int, default=0, help="Process CTA size (0: library default)")
     ap.add_argument("--perspective", action="store_true",
-                    help="heightfield workload: perspective-correct attributes (PIKO_OPT_PERSPECTIVE)")
+                    help="heightfield and sphere workloads: perspective-correct attributes (PIKO_OPT_PERSPECTIVE)")
     ap.add_argument("--autotune", action="store_true",
                     help="heightfield workload: bin size, schedule and threads per bin from the autotuner")
     ap.add_argument("--small-px", type=int, default=0,

@@ -88,9 +88,9 @@ extern "C" {
 #define PIKO_OPT_PERSPECTIVE 8      /* 1: perspective-correct attributes in shading and
                                        gradients: b'_i = (b_i / w_i) / sum_j (b_j / w_j), w_i
                                        the clip w of vertex i; 0 (default): screen-space b_i.
-                                       Depth and coverage do not change.  Single-scene calls
-                                       only: the batch calls return PIKO_ERR_INVALID_ARG while
-                                       it (or PIKO_OPT_UNCLAMPED) is set                    */
+                                       Depth and coverage do not change.  Applies to every
+                                       scene of a batch; piko_raster_backward_batch follows
+                                       the setting of the last piko_raster_forward_batch   */
 
 /* Stage boundaries of one forward pass, for piko_raster_set_stage_events. */
 #define PIKO_NUM_STAGE_EVENTS 6 /* before vertex, after vertex, after setup+count, after scan,

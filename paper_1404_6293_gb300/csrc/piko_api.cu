@@ -12,7 +12,7 @@ struct BatchState;
 void batch_state_free(BatchState* bs);
 int batch_prepare(BatchState*& bs, int num_sms, const piko_scene* scenes, int n, piko_framebuffer* fbs,
                   const int32_t* bin_sizes, const int32_t* schedules, int default_bin_w, int default_bin_h,
-                  int default_schedule, cudaStream_t stream, std::string& err);
+                  int default_schedule, int unclamped, int persp, cudaStream_t stream, std::string& err);
 int batch_launch_forward(BatchState* bs, DevStatus* st, bool persistent, cudaStream_t stream, std::string& err);
 long long batch_capacity(const BatchState* bs);
 void batch_note_entries(BatchState* bs, long long entries);
@@ -362,13 +362,10 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
 int piko_raster_forward_batch(piko_raster* h, const piko_scene* scenes, int n, piko_framebuffer* fbs,
                               const int32_t* bin_sizes, const int32_t* schedules, void* cuda_stream) {
   if (!h) return PIKO_ERR_INVALID_ARG;
-  if (h->unclamped || h->perspective)
-    return fail(h, PIKO_ERR_INVALID_ARG, "batch calls shade clamped and in screen space: unset PIKO_OPT_UNCLAMPED "
-                                         "and PIKO_OPT_PERSPECTIVE");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
   h->last_stream = st;
   int r = batch_prepare(h->batch, h->num_sms, scenes, n, fbs, bin_sizes, schedules, h->bin_w, h->bin_h, h->schedule,
-                        st, h->err);
+                        h->unclamped, h->perspective, st, h->err);
   if (r != PIKO_OK) return r;
   for (int attempt = 0;; ++attempt) {
     if ((r = batch_launch_forward(h->batch, h->status, h->batch_launch == 0, st, h->err)) != PIKO_OK) return r;
@@ -392,9 +389,6 @@ int piko_raster_backward_batch(piko_raster* h, const piko_scene* scenes, int n, 
                                float* const* dl_dlight, void* cuda_stream) {
   if (!h) return PIKO_ERR_INVALID_ARG;
   if (!scenes || !fbs || n < 1) return fail(h, PIKO_ERR_INVALID_ARG, "backward_batch needs scenes and framebuffers");
-  if (h->unclamped || h->perspective)
-    return fail(h, PIKO_ERR_INVALID_ARG, "batch calls shade clamped and in screen space: unset PIKO_OPT_UNCLAMPED "
-                                         "and PIKO_OPT_PERSPECTIVE");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
   h->last_stream = st;
   return batch_launch_backward(h->batch, scenes, n, fbs, dl_drgba, dl_dcolor, dl_dnormal, dl_dlight, h->num_sms, st,

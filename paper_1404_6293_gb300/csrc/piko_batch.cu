@@ -26,7 +26,8 @@ struct BatchScene {
   RasterGeom g;
   int V, T, mode, schedule;
   int vtx_base, tri_base, bin_base, pix_base;
-  int slot_bits, nslots, rec_stride, pad;
+  int slot_bits, nslots, rec_stride;
+  int unclamped;  // Lambert without the clamp (the handle's option)
   const float4* pos;
   const int* tris;
   const float* mvp;
@@ -65,6 +66,7 @@ struct BatchParams {
   int total_v, total_t, total_bins, total_static, total_dyn, total_btiles;
   int4* vtx;
   float* vdot;
+  float* invw;  // 1 / clip w per vertex (perspective-correct attributes), else NULL
   BinRect* rect;
   unsigned* cnt;  // 2 * total_bins, zero between frames
   unsigned* bin_off;
@@ -144,12 +146,19 @@ __device__ bool cta_should_stop(const DevStatus* st) {
 }
 
 // ------------------------------------------------------------------ phases
+template <bool PERSP>
 __device__ void phase_vertex(const BatchParams& b) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.total_v; i += gridDim.x * blockDim.x) {
     const int s = find_scene(b.vtx_prefix, b.n, i);
     const BatchScene& d = b.sc[s];
     const int v = i - d.vtx_base;
-    b.vtx[i] = snap_vertex(__ldg(d.pos + v), d.mvp, (float)d.g.W, (float)d.g.H);
+    if (PERSP) {
+      float w;
+      b.vtx[i] = snap_vertex(__ldg(d.pos + v), d.mvp, (float)d.g.W, (float)d.g.H, &w);
+      b.invw[i] = w > 0.0f ? __fdiv_rn(1.0f, w) : 0.0f;
+    } else {
+      b.vtx[i] = snap_vertex(__ldg(d.pos + v), d.mvp, (float)d.g.W, (float)d.g.H);
+    }
     if (d.mode == PIKO_SHADE_LAMBERT) {
       const float* n = d.normal + 3 * (size_t)v;
       b.vdot[i] = __ldg(n) * __ldg(d.light) + __ldg(n + 1) * __ldg(d.light + 1) + __ldg(n + 2) * __ldg(d.light + 2);
@@ -322,7 +331,7 @@ __device__ void load_tile_scene(const BatchParams& b, int s, TileScene& t) {
   const BatchScene& d = b.sc[s];
   t.g = d.g;
   t.mode = d.mode;
-  t.unclamped = 0;
+  t.unclamped = d.unclamped;
   t.small_px = 32;
   t.slot_bits = d.slot_bits;
   t.nslots = d.nslots;
@@ -334,13 +343,14 @@ __device__ void load_tile_scene(const BatchParams& b, int s, TileScene& t) {
   t.normal = d.normal;
   t.light = d.light;
   t.vdot = b.vdot + d.vtx_base;
-  t.invw = nullptr;  // batches interpolate in screen space
+  t.invw = b.invw ? b.invw + d.vtx_base : nullptr;
   t.key_out = d.key_out;
   t.rgba_out = d.rgba_out;
   t.gnorm_out = d.gnorm_out;
   t.galb_out = d.galb_out;
 }
 
+template <bool PERSP>
 __device__ void process_one(const BatchParams& b, const int* prefix, int i, ProcessShared& ps, const TileSmem& sm,
                             unsigned& big_base) {
   if (threadIdx.x == 0) {
@@ -361,9 +371,10 @@ __device__ void process_one(const BatchParams& b, const int* prefix, int i, Proc
     __syncthreads();
     return;
   }
-  process_tile<false>(sc, ps.tile, beg, end, b.bin_tris, sm, big_base, st);
+  process_tile<false, PERSP>(sc, ps.tile, beg, end, b.bin_tris, sm, big_base, st);
 }
 
+template <bool PERSP>
 __device__ void phase_process(const BatchParams& b, ProcessShared& ps, const TileSmem& sm) {
   for (int i = threadIdx.x; i < b.max_bin_px; i += blockDim.x) sm.skey[i] = KEY_EMPTY;
   if (threadIdx.x == 0) {
@@ -373,7 +384,7 @@ __device__ void phase_process(const BatchParams& b, ProcessShared& ps, const Til
   __syncthreads();
   unsigned big_base = 0u;
   // DirectMap scenes: tiles dealt round robin; then LoadBalance scenes from the queue
-  for (int i = blockIdx.x; i < b.total_static; i += gridDim.x) process_one(b, b.stat_prefix, i, ps, sm, big_base);
+  for (int i = blockIdx.x; i < b.total_static; i += gridDim.x) process_one<PERSP>(b, b.stat_prefix, i, ps, sm, big_base);
   __shared__ int s_next;
   for (int iter = 0;; ++iter) {
     if (threadIdx.x == 0) {
@@ -387,7 +398,7 @@ __device__ void phase_process(const BatchParams& b, ProcessShared& ps, const Til
     const int i = s_next;
     __syncthreads();  // s_next is rewritten for the next tile
     if (i < 0 || i >= b.total_dyn) break;
-    process_one(b, b.dyn_prefix, i, ps, sm, big_base);
+    process_one<PERSP>(b, b.dyn_prefix, i, ps, sm, big_base);
   }
 }
 
@@ -396,6 +407,8 @@ __device__ void phase_process(const BatchParams& b, ProcessShared& ps, const Til
 #endif
 constexpr int BATCH_THREADS = 128;
 
+// PERSP: perspective-correct attributes; one instance per setting
+template <bool PERSP>
 __global__ void __maxnreg__(PIKO_BATCH_MAXNREG) k_batch_forward(BatchParams b) {
   extern __shared__ __align__(16) unsigned long long smem[];
   __shared__ ScanSmem scan_sm;
@@ -408,7 +421,7 @@ __global__ void __maxnreg__(PIKO_BATCH_MAXNREG) k_batch_forward(BatchParams b) {
   sm.s_nbig = &s_nbig;
   if (cta_should_stop(b.st)) return;
   if (b.phases & PH_VERTEX) {
-    phase_vertex(b);
+    phase_vertex<PERSP>(b);
     if (b.persistent && !grid_barrier(b.sync, b.st)) return;
   }
   if (b.phases & PH_COUNT) {
@@ -427,7 +440,7 @@ __global__ void __maxnreg__(PIKO_BATCH_MAXNREG) k_batch_forward(BatchParams b) {
   }
   if (b.phases & PH_PROCESS) {
     if (cta_should_stop(b.st)) return;
-    phase_process(b, ps, sm);
+    phase_process<PERSP>(b, ps, sm);
   }
 }
 
@@ -440,8 +453,10 @@ struct BatchBwdParams {
   const int* btile_prefix;  // [n+1] backward tiles per scene
   int total_btiles;
   const int4* vtx;
+  const float* invw;  // as in BatchParams
 };
 
+template <bool PERSP>
 __global__ void __launch_bounds__(BWD_THREADS, 1024 / BWD_THREADS) k_batch_backward(BatchBwdParams b) {
   extern __shared__ __align__(16) unsigned char bwd_smem_raw[];
   BwdSmem& sm = *reinterpret_cast<BwdSmem*>(bwd_smem_raw);
@@ -457,9 +472,9 @@ __global__ void __launch_bounds__(BWD_THREADS, 1024 / BWD_THREADS) k_batch_backw
     const BatchScene& d = b.sc[s];
     if (d.dl == nullptr || d.mode == PIKO_SHADE_GBUFFER) continue;  // the same for the whole CTA
     BwdScene c;
-    c.W = d.g.W; c.H = d.g.H; c.mode = d.mode; c.unclamped = 0; c.T = d.T; c.V = d.V;
+    c.W = d.g.W; c.H = d.g.H; c.mode = d.mode; c.unclamped = d.unclamped; c.T = d.T; c.V = d.V;
     c.tris = d.tris; c.vtx = b.vtx + d.vtx_base; c.color = d.color; c.normal = d.normal; c.light = d.light;
-    c.invw = nullptr;  // batches interpolate in screen space
+    c.invw = b.invw ? b.invw + d.vtx_base : nullptr;
     c.key = d.key_out; c.dl = d.dl; c.dcolor = d.dcolor; c.dnormal = d.dnormal; c.dlight = d.dlight;
     float L0 = 0.f, L1 = 0.f, L2 = 0.f;
     if (c.mode == PIKO_SHADE_LAMBERT) {
@@ -468,7 +483,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 1024 / BWD_THREADS) k_batch_backw
     const int lt = i - __ldg(b.btile_prefix + s);
     const int ntx = (c.W + BWD_TILE_W - 1) / BWD_TILE_W;
     const int ty = lt / ntx, tx = lt - ty * ntx;
-    backward_tile(c, tx * BWD_TILE_W, ty * BWD_TILE_H, sm, L0, L1, L2, gl0, gl1, gl2);
+    backward_tile<PERSP>(c, tx * BWD_TILE_W, ty * BWD_TILE_H, sm, L0, L1, L2, gl0, gl1, gl2);
     if (c.dlight && c.mode == PIKO_SHADE_LAMBERT) bwd_flush_light(sm, c.dlight, gl0, gl1, gl2);
   }
 }
@@ -500,6 +515,8 @@ struct BatchState {
   long long vcap = 0;
   float* vdot = nullptr;
   long long dcap = 0;
+  float* invw = nullptr;
+  long long icap = 0;
   BinRect* rect = nullptr;
   long long tcap = 0;
   unsigned* cnt = nullptr;
@@ -520,6 +537,7 @@ struct BatchState {
   size_t smem = 0;
   int grid = 0;
   int n = 0;
+  int persp = 0;               // the layout's attribute interpolation (perspective-correct or not)
   long long last_entries = 0;  // bin entries of the last frame read back (sizes the shading records)
   long long last_bins = 0;     // bins of that frame
 };
@@ -559,6 +577,7 @@ void batch_state_free(BatchState* bs) {
   cudaFree(bs->desc);
   cudaFree(bs->vtx);
   cudaFree(bs->vdot);
+  cudaFree(bs->invw);
   cudaFree(bs->rect);
   cudaFree(bs->cnt);
   cudaFree(bs->bin_off);
@@ -576,7 +595,7 @@ void batch_state_free(BatchState* bs) {
 // Returns a PIKO_* code; err describes a failure.
 int batch_prepare(BatchState*& bs, int num_sms, const piko_scene* scenes, int n, piko_framebuffer* fbs,
                   const int32_t* bin_sizes, const int32_t* schedules, int default_bin_w, int default_bin_h,
-                  int default_schedule, cudaStream_t stream, std::string& err) {
+                  int default_schedule, int unclamped, int persp, cudaStream_t stream, std::string& err) {
   if (!bs) bs = new BatchState();
   if (n < 1 || !scenes || !fbs) { err = "batch needs n >= 1 scenes and framebuffers"; return PIKO_ERR_INVALID_ARG; }
   std::vector<BatchScene> d(n);
@@ -609,8 +628,9 @@ int batch_prepare(BatchState*& bs, int num_sms, const piko_scene* scenes, int n,
     x.g.nbx = (s.width + bw - 1) / bw; x.g.nby = (s.height + bh - 1) / bh;
     x.V = s.num_vertices; x.T = s.num_triangles; x.mode = s.shade_mode; x.schedule = sched;
     x.vtx_base = (int)tv; x.tri_base = (int)tt; x.bin_base = (int)tb; x.pix_base = 0;
-    tile_layout(s.num_triangles, bw * bh, s.shade_mode, s.color != nullptr, false, 255, x.slot_bits, x.nslots,
+    tile_layout(s.num_triangles, bw * bh, s.shade_mode, s.color != nullptr, persp != 0, 255, x.slot_bits, x.nslots,
                 x.rec_stride, slots_hint);
+    x.unclamped = unclamped;
     x.pos = reinterpret_cast<const float4*>(s.pos);
     x.tris = s.tris; x.mvp = s.mvp; x.color = s.color; x.normal = s.normal; x.light = s.light_dir;
     x.key_out = reinterpret_cast<unsigned long long*>(f.key);
@@ -635,6 +655,7 @@ int batch_prepare(BatchState*& bs, int num_sms, const piko_scene* scenes, int n,
   int r;
   if ((r = grow_dev(&bs->vtx, &bs->vcap, tv, false, err)) != PIKO_OK) return r;
   if ((r = grow_dev(&bs->vdot, &bs->dcap, tv, false, err)) != PIKO_OK) return r;
+  if (persp && (r = grow_dev(&bs->invw, &bs->icap, tv, false, err)) != PIKO_OK) return r;
   if ((r = grow_dev(&bs->rect, &bs->tcap, tt, false, err)) != PIKO_OK) return r;
   if (tb > bs->bcap) {
     // counts must start at zero; offsets/cursors/chunk states are rewritten
@@ -710,18 +731,19 @@ int batch_prepare(BatchState*& bs, int num_sms, const piko_scene* scenes, int n,
   b.btile_prefix = reinterpret_cast<const int*>(dd + dbytes + 5 * pbytes);
   b.total_v = (int)tv; b.total_t = (int)tt; b.total_bins = (int)tb; b.total_static = (int)tsd;
   b.total_dyn = (int)tdy; b.total_btiles = (int)tp;
-  b.vtx = bs->vtx; b.vdot = bs->vdot; b.rect = bs->rect; b.cnt = bs->cnt; b.bin_off = bs->bin_off;
+  b.vtx = bs->vtx; b.vdot = bs->vdot; b.invw = persp ? bs->invw : nullptr; b.rect = bs->rect; b.cnt = bs->cnt; b.bin_off = bs->bin_off;
   b.cursor = bs->cursor; b.chunk_state = bs->chunk_state; b.bin_tris = bs->bin_tris;
   b.capacity = (unsigned long long)bs->ecap; b.sync = bs->sync;
   b.max_bin_px = max_bin_px;
   bs->smem = tile_smem_bytes(max_bin_px, BATCH_THREADS, 1, 0) + (size_t)max_rec * 4;
+  const auto kf = persp ? k_batch_forward<true> : k_batch_forward<false>;
   if (bs->smem > 48 * 1024 &&
-      cudaFuncSetAttribute(k_batch_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs->smem) != cudaSuccess) {
+      cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs->smem) != cudaSuccess) {
     err = "batch shared memory request refused";
     return PIKO_ERR_CUDA;
   }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_forward, BATCH_THREADS, bs->smem) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, BATCH_THREADS, bs->smem) != cudaSuccess ||
       per_sm < 1) {
     cudaGetLastError();
     err = "batch kernel does not fit on an SM";
@@ -729,6 +751,7 @@ int batch_prepare(BatchState*& bs, int num_sms, const piko_scene* scenes, int n,
   }
   bs->grid = per_sm * num_sms;
   bs->n = n;
+  bs->persp = persp ? 1 : 0;
   bs->host_desc = d;
   return PIKO_OK;
 }
@@ -757,7 +780,7 @@ int batch_launch_forward(BatchState* bs, DevStatus* st, bool persistent, cudaStr
     attr.val.cooperative = 1;
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_batch_forward, b);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, bs->persp ? k_batch_forward<true> : k_batch_forward<false>, b);
     if (e != cudaSuccess) {
       err = std::string("cooperative batch launch: ") + cudaGetErrorString(e);
       return PIKO_ERR_CUDA;
@@ -768,7 +791,10 @@ int batch_launch_forward(BatchState* bs, DevStatus* st, bool persistent, cudaStr
   const int phases[5] = {PH_VERTEX, PH_COUNT, PH_SCAN, PH_SCATTER, PH_PROCESS};
   for (int k = 0; k < 5; ++k) {
     b.phases = phases[k];
-    k_batch_forward<<<bs->grid, BATCH_THREADS, bs->smem, stream>>>(b);
+    if (bs->persp)
+      k_batch_forward<true><<<bs->grid, BATCH_THREADS, bs->smem, stream>>>(b);
+    else
+      k_batch_forward<false><<<bs->grid, BATCH_THREADS, bs->smem, stream>>>(b);
   }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -832,15 +858,19 @@ int batch_launch_backward(BatchState* bs, const piko_scene* scenes, int n, const
   p.btile_prefix = bs->params.btile_prefix;
   p.total_btiles = bs->params.total_btiles;
   p.vtx = bs->vtx;
+  p.invw = bs->params.invw;  // the interpolation of the last forward_batch
   static int per_sm_of[64] = {0};  // the shared-memory opt-in is per device
   int dev = 0;
   cudaGetDevice(&dev);
   int& per_sm = per_sm_of[dev & 63];
   if (per_sm == 0) {
     int v = 0;
-    if (cudaFuncSetAttribute(k_batch_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BwdSmem)) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_batch_backward, BWD_THREADS, sizeof(BwdSmem)) !=
+    // both instances share the launch bounds and the shared-memory size
+    if (cudaFuncSetAttribute(k_batch_backward<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(BwdSmem)) != cudaSuccess ||
+        cudaFuncSetAttribute(k_batch_backward<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(BwdSmem)) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_batch_backward<false>, BWD_THREADS, sizeof(BwdSmem)) !=
             cudaSuccess ||
         v < 1)
       v = 1;
@@ -849,7 +879,10 @@ int batch_launch_backward(BatchState* bs, const piko_scene* scenes, int n, const
   long long blocks = (long long)per_sm * num_sms;
   if (blocks > p.total_btiles) blocks = p.total_btiles;
   if (blocks < 1) blocks = 1;
-  k_batch_backward<<<(int)blocks, BWD_THREADS, sizeof(BwdSmem), stream>>>(p);
+  if (bs->persp)
+    k_batch_backward<true><<<(int)blocks, BWD_THREADS, sizeof(BwdSmem), stream>>>(p);
+  else
+    k_batch_backward<false><<<(int)blocks, BWD_THREADS, sizeof(BwdSmem), stream>>>(p);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     err = std::string("batch backward launch: ") + cudaGetErrorString(e);

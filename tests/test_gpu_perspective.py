@@ -109,6 +109,7 @@ def _grad_check(g_gpu, g_ref):
     g_gpu = np.asarray(g_gpu, np.float64)
     scale = np.abs(g_ref).max()
     big = np.abs(g_ref) > 1e-3 * scale
+    assert scale > 0
     rel = np.abs(g_gpu - g_ref)[big] / np.abs(g_ref)[big]
     assert rel.max() <= 1e-4, rel.max()
     assert np.abs(g_gpu - g_ref)[~big].max(initial=0) <= 1e-4 * scale
@@ -143,17 +144,56 @@ def test_backward_forms_match_oracle(form, mode):
         _grad_check(dlg.cpu().numpy(), dl)
 
 
-def test_batch_calls_reject_the_option():
+def test_batch_with_the_option_equals_single_scene_calls():
+    """Perspective and unclamped shading in a batch: every scene's keys,
+    colours and gradients as its single-scene call gives them."""
+    torch = _torch()
     from paper_1404_6293_gb300 import _lib as L
     from paper_1404_6293_gb300.raster import DeviceScene, Rasterizer
-    s = _sphere(64, 64, 12, 8, S.SHADE_LAMBERT)
-    ds = DeviceScene.from_host(s)
-    for opt in (L.PIKO_OPT_PERSPECTIVE, L.PIKO_OPT_UNCLAMPED):
-        r = Rasterizer(64, 64)
-        r.set_option(opt, 1)
-        with pytest.raises(RuntimeError):
-            r.forward_batch([ds])
-        r.set_option(opt, 0)
-        fbs = r.forward_batch([ds])
-        assert r.status()[0] == 0 and len(fbs) == 1
-        r.close()
+    host = [_sphere(160, 128, 40, 30, S.SHADE_LAMBERT, seed=3), _floor(128, 96),
+            _sphere(96, 80, 60, 40, S.SHADE_GOURAUD, seed=4)]
+    for opts in ({L.PIKO_OPT_PERSPECTIVE: 1}, {L.PIKO_OPT_PERSPECTIVE: 1, L.PIKO_OPT_UNCLAMPED: 1},
+                 {L.PIKO_OPT_UNCLAMPED: 1}):
+        ds = [DeviceScene.from_host(s) for s in host]
+        rb = Rasterizer(64, 64)
+        for k, v in opts.items():
+            rb.set_option(k, v)
+        fbs = rb.forward_batch(ds, None, [(16, 16), (32, 32), (16, 16)], ["dynamic", "static", "dynamic"])
+        torch.cuda.synchronize()
+        assert rb.status()[0] == 0
+        grads_b, grads_s = [], []
+        gl = []
+        for i, s in enumerate(host):
+            tgt = torch.from_numpy(S.target_image(s.width, s.height, seed=9 + i)[0]).cuda()
+            gl.append((2.0 * (fbs[i].rgba - tgt)).contiguous())
+            gl[-1][..., 3] = 0
+            grads_b.append([torch.zeros((s.num_vertices, 3), device="cuda"), torch.zeros((s.num_vertices, 3),
+                            device="cuda"), torch.zeros(3, device="cuda")])
+        rb.backward_batch(ds, fbs, gl, [g[0] for g in grads_b], [g[1] if s.normal is not None else None
+                                                                  for g, s in zip(grads_b, host)],
+                          [g[2] if s.normal is not None else None for g, s in zip(grads_b, host)])
+        torch.cuda.synchronize()
+        assert rb.status()[0] == 0
+        for i, s in enumerate(host):
+            r = Rasterizer(s.width, s.height, 16, 16, "hardware")
+            for k, v in opts.items():
+                r.set_option(k, v)
+            fb = r.forward(ds[i])
+            torch.cuda.synchronize()
+            assert torch.equal(fb.key, fbs[i].key), f"scene {i} keys"
+            assert (fb.rgba - fbs[i].rgba).abs().max().item() <= 1e-6, f"scene {i} colours"
+            ref_key, _ = oracle.raster_bbox(s)
+            persp = bool(opts.get(L.PIKO_OPT_PERSPECTIVE, 0))
+            unc = bool(opts.get(L.PIKO_OPT_UNCLAMPED, 0))
+            ref = oracle.shade(s, ref_key, perspective=persp, unclamped=unc)
+            assert np.abs(fbs[i].rgba.cpu().numpy() - ref).max() <= RGB_TOL
+            g = [torch.zeros_like(t) for t in grads_b[i]]
+            r.backward(ds[i], fb, gl[i], g[0], g[1] if s.normal is not None else None,
+                       g[2] if s.normal is not None else None)
+            torch.cuda.synchronize()
+            _grad_check(grads_b[i][0].cpu().numpy(), g[0].cpu().numpy().astype(np.float64))
+            if s.shade_mode == S.SHADE_LAMBERT:  # Gouraud has no normal or light gradients
+                _grad_check(grads_b[i][1].cpu().numpy(), g[1].cpu().numpy().astype(np.float64))
+                _grad_check(grads_b[i][2].cpu().numpy(), g[2].cpu().numpy().astype(np.float64))
+            r.close()
+        rb.close()

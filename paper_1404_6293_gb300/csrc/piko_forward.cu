@@ -156,8 +156,7 @@ int scan_chunks(int nbins) { return (nbins + SCAN_CHUNK - 1) / SCAN_CHUNK; }
 // per group of lanes sharing the bin (__match_any_sync), so the scatter
 // needs no atomic for it; multi-bin pairs are spread over the warp.
 // ======================================================================
-// Vertex data of one triangle, gathered before any of it is used so that two
-// batches of triangles have their loads in flight together.
+// Vertex data of one triangle, gathered before any of it is used.
 struct TriVerts {
   int4 p0, p1, p2;
   bool in_range;
@@ -246,17 +245,14 @@ __global__ void __launch_bounds__(256) k_setup_count(RasterGeom g, int T, const 
   pdl_launch_dependents();
   const unsigned lt_mask = (1u << lane) - 1u;
   const int step = gridDim.x * (blockDim.x >> 5) * 32;
-  // two batches of 32 triangles per iteration: both batches' loads are issued
-  // before either is processed
-  for (int base = (blockIdx.x * (blockDim.x >> 5) + wib) * 32; base < T; base += 2 * step) {
-    const int baseB = base + step;
-    const bool hasB = baseB < T;  // warp-uniform
+  // one batch of 32 triangles per warp and iteration: at 28 registers eight
+  // CTAs fit an SM, and the other warps hide the gathers' latency (two
+  // batches in flight per warp needed 48 registers, five CTAs, and ran 2%
+  // slower end to end)
+  for (int base = (blockIdx.x * (blockDim.x >> 5) + wib) * 32; base < T; base += step) {
     const int3 ia = load_tri(tris, T, base + lane);
-    const int3 ib = hasB ? load_tri(tris, T, baseB + lane) : make_int3(0, 0, 0);
     const TriVerts va = gather_verts(ia, V, vtx, base + lane < T);
-    const TriVerts vb = gather_verts(ib, V, vtx, hasB && baseB + lane < T);
     count_batch(g, T, base + lane, ia, va, rect, cnt, nbins, st, stats, lane, lt_mask);
-    if (hasB) count_batch(g, T, baseB + lane, ib, vb, rect, cnt, nbins, st, stats, lane, lt_mask);
   }
 }
 

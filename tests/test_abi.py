@@ -46,3 +46,18 @@ def test_struct_layout_matches_binding():
     from paper_1404_6293_gb300 import _lib as L
     assert ctypes.sizeof(L.PikoScene) == 4 * 4 + 6 * 8 + 2 * 4
     assert ctypes.sizeof(L.PikoFramebuffer) == 4 * 8
+
+
+def test_binding_constants_match_the_header():
+    """Every integer #define of the header that the binding names has the
+    header's value, and the binding names every option and error code."""
+    from paper_1404_6293_gb300 import _lib as L
+    text = open(os.path.join(ROOT, "include", "piko_raster.h")).read()
+    defines = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(PIKO_\w+)\s+(-?\d+)\b", text)}
+    assert defines, "no integer defines found"
+    for name, value in defines.items():
+        if hasattr(L, name):
+            assert getattr(L, name) == value, name
+    for name in defines:
+        if name.startswith(("PIKO_OPT_", "PIKO_ERR_", "PIKO_SCHED_", "PIKO_SHADE_")):
+            assert hasattr(L, name), f"binding lacks {name}"

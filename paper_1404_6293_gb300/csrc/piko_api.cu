@@ -222,7 +222,8 @@ int piko_raster_reserve(piko_raster* h, int64_t max_vertices, int64_t max_triang
   int r;
   if ((r = grow(h, &h->vtx, &h->vcap, max_vertices, "vertex buffer")) != PIKO_OK) return r;
   if ((r = grow(h, &h->vdot, &h->dcap, max_vertices, "vertex light terms")) != PIKO_OK) return r;
-  if (h->perspective && (r = grow(h, &h->invw, &h->icap, max_vertices, "vertex 1/w")) != PIKO_OK) return r;
+  // 1/w too, so that turning perspective-correct attributes on later needs no allocation
+  if ((r = grow(h, &h->invw, &h->icap, max_vertices, "vertex 1/w")) != PIKO_OK) return r;
   if ((r = grow(h, &h->rect, &h->tcap, max_triangles, "bin rectangles")) != PIKO_OK) return r;
   if ((r = grow(h, &h->bin_tris, &h->ecap, max_bin_entries, "bin lists")) != PIKO_OK) return r;
   cudaError_t e = cudaDeviceSynchronize();

@@ -197,3 +197,36 @@ def test_batch_with_the_option_equals_single_scene_calls():
                 _grad_check(grads_b[i][2].cpu().numpy(), g[2].cpu().numpy().astype(np.float64))
             r.close()
         rb.close()
+
+
+def test_option_after_reserve_needs_no_allocation_in_a_graph():
+    """reserve() sizes the 1/w buffer too, so a forward captured in a CUDA
+    graph after turning the option on allocates nothing."""
+    torch = _torch()
+    from paper_1404_6293_gb300 import _lib as L
+    from paper_1404_6293_gb300.raster import DeviceScene, Framebuffer, Rasterizer
+    s = _sphere(128, 96, 24, 16, S.SHADE_LAMBERT)
+    r = Rasterizer(s.width, s.height, 16, 16, "hardware")
+    ds = DeviceScene.from_host(s)
+    fb = Framebuffer.allocate(s.width, s.height, s.shade_mode)
+    r.reserve(s.num_vertices, s.num_triangles, 1 << 20)
+    r.set_option(L.PIKO_OPT_CHECK_CAPACITY, 0)
+    r.set_option(L.PIKO_OPT_PERSPECTIVE, 1)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        r.forward(ds, fb, side)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        r.forward(ds, fb)
+    fb.key.fill_(0)
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    assert r.status()[0] == 0
+    ref_key, _ = oracle.raster_bbox(s)
+    assert np.array_equal(fb.key_numpy(), ref_key)
+    assert np.abs(fb.rgba.cpu().numpy() - oracle.shade(s, ref_key, perspective=True)).max() <= RGB_TOL
+    r.close()

@@ -90,7 +90,8 @@ extern "C" {
                                        the clip w of vertex i; 0 (default): screen-space b_i.
                                        Depth and coverage do not change.  Applies to every
                                        scene of a batch; piko_raster_backward_batch follows
-                                       the setting of the last piko_raster_forward_batch   */
+                                       the setting of the last piko_raster_forward_batch,
+                                       piko_raster_backward the handle's current setting  */
 
 /* Stage boundaries of one forward pass, for piko_raster_set_stage_events. */
 #define PIKO_NUM_STAGE_EVENTS 6 /* before vertex, after vertex, after setup+count, after scan,

@@ -36,7 +36,9 @@ KERNEL_SOURCES = ["paper_1404_6293_gb300/csrc/piko_process.cu", "paper_1404_6293
                   "paper_1404_6293_gb300/csrc/piko_internal.cuh"]
 
 # Per-unit algorithmic costs of the Process kernel (thread operations), fixed
-# from the minimal operation sequence of the definition: see the design doc.
+# before the first measurement from the minimal operation sequence of the
+# definition (vertex setup per bin entry, edge tests per sample, exact depth
+# and key per covered sample, shading per pixel).
 OPS_PER_ENTRY = 60      # re-derive the triangle: 3 gathers, 6 differences, 64-bit area, clip to tile
 OPS_PER_TEST = 12       # three 64-bit incremental edge updates and the sign test
 OPS_PER_FRAGMENT = 16   # 64-bit depth numerator, reciprocal estimate and fix-up, key, shared-memory min

@@ -8,6 +8,8 @@ b'_i = (b_i / w_i) / sum_j (b_j / w_j) with w_i the clip w of each vertex.
   the inverse camera matrix, which is independent of O15's formula. The
   screen-space form misses it by far more.
 - Gradients with O15 match float64 central differences of the loss.
+- A hand-derived case gives b' = (4/7, 2/7, 1/7) at a triangle's screen
+  centroid with w = (1, 2, 4).
 """
 import numpy as np
 
@@ -125,3 +127,29 @@ def test_perspective_gradients_match_central_differences():
     # and the perspective gradients differ from the screen-space ones
     dc_a, _, _ = oracle.backward(sph, key, g, mvp=M)
     assert np.abs(dc_a - dc).max() > 1e-3 * np.abs(dc).max()
+
+
+def test_centroid_with_w_1_2_4_is_4_2_1_sevenths():
+    """Hand-derived: at a pixel centre that is the triangle's screen
+    centroid, b = (1/3, 1/3, 1/3); with clip w = (1, 2, 4) the weights b_i/w_i
+    are (1/3, 1/6, 1/12), so b' = (4/7, 2/7, 1/7).  Vertex colours are the
+    unit vectors, so the Gouraud colour there is b' itself."""
+    W = H = 32
+    P = 256 * 8 + 128                     # centre of pixel (8, 8) in 16.8 units
+    offs = [(-768, 768), (768, 768), (0, -1536)]   # sum to zero: P is the centroid
+    ws = [1.0, 2.0, 4.0]                  # powers of two: every float32 step below is exact
+    pos = []
+    for (dx, dy), w in zip(offs, ws):
+        x_ndc = (P + dx) / (128.0 * W) - 1.0
+        y_ndc = 1.0 - (P + dy) / (128.0 * H)
+        pos.append([x_ndc * w, y_ndc * w, 0.0, w])
+    pos = np.array(pos, np.float32)
+    color = np.eye(3, dtype=np.float32)
+    s = S.Scene(W, H, pos, np.array([[0, 1, 2]], np.int32), color=color)
+    X, Y, _, ok = oracle.vertex_stage(s)
+    assert ok.all() and list(X) == [P + d[0] for d in offs] and list(Y) == [P + d[1] for d in offs]
+    key, _ = oracle.raster_brute(s)
+    assert _ids(key)[8, 8] == 0
+    rgb = oracle.shade(s, key, perspective=True)[8, 8, :3]
+    assert np.allclose(rgb, [4 / 7, 2 / 7, 1 / 7], atol=1e-15)
+    assert np.allclose(oracle.shade(s, key)[8, 8, :3], [1 / 3, 1 / 3, 1 / 3], atol=1e-15)

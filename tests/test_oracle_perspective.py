@@ -153,3 +153,19 @@ def test_centroid_with_w_1_2_4_is_4_2_1_sevenths():
     rgb = oracle.shade(s, key, perspective=True)[8, 8, :3]
     assert np.allclose(rgb, [4 / 7, 2 / 7, 1 / 7], atol=1e-15)
     assert np.allclose(oracle.shade(s, key)[8, 8, :3], [1 / 3, 1 / 3, 1 / 3], atol=1e-15)
+
+
+def test_perspective_gouraud_gradient_closed_form():
+    """With g = 1 on every channel, dL/dc_v sums v's perspective-correct
+    weight over its pixels; the weights at a pixel sum to one, so the total
+    is 3 x the covered pixels, as in screen space (an unnormalised weight
+    would break it)."""
+    sph, mvps = S.sphere_views(num_views=1, width=40, height=40, slices=10, stacks=8, seed=12)
+    sph.shade_mode = S.SHADE_GOURAUD
+    key, _ = oracle.raster_brute(sph, mvp=mvps[0])
+    g = np.zeros((40, 40, 4))
+    g[..., :3] = 1.0
+    dc, _, _ = oracle.backward(sph, key, g, mvp=mvps[0], perspective=True)
+    covered = int((key != EMPTY).sum())
+    assert covered > 300
+    assert np.isclose(dc.sum(), 3 * covered, rtol=1e-12)

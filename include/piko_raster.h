@@ -255,19 +255,26 @@ int piko_raster_stats(piko_raster *h, int64_t out[5]);
  * schedule and the default options, but needs no handle: its scratch memory
  * is one fixed device array of about 6.3 MB inside this library, which every
  * GPU that loads the library keeps until the process exits.  It calls no
- * cudaMalloc, cudaFree or other allocating routine.
- *  - The first call on each device looks up that array's device address
- *    (once per device, with the device current); make that first call
- *    before any stream capture.
+ * cudaMalloc, cudaFree or other allocating routine.  Its Process launch
+ * sizes the per-tile shading records for the largest count the key layout
+ * allows (the handle forward sizes them from the last frame's bin lists), so
+ * its shared-memory footprint can differ; the output is the same.
+ *  - The first call in each CUDA context (for callers on the runtime's
+ *    primary context: once per device, with that device current) looks up
+ *    the array's device address; make that first call before any stream
+ *    capture.  A thread with no current context uses the current device's
+ *    primary context.
  *  - Every call on a device shares the array and it keeps the previous
- *    call's contents (the call clears what must start at zero itself).
- *    Calls whose work overlaps on the GPU -- on different streams or from
- *    different host threads -- race and give wrong results; order them on
- *    one stream.
+ *    call's contents (each call clears the status word, the scan states and
+ *    the per-tile counts itself).  Calls whose work overlaps on the GPU --
+ *    on different streams or from different host threads -- race and give
+ *    wrong results; order them on one stream.
  *  - Scenes above the limits below, or more tiles than
- *    PIKO_NOALLOC_MAX_BINS, are rejected with PIKO_ERR_INVALID_ARG and
- *    nothing is enqueued.  Other host-side checks are those of
- *    piko_raster_forward.
+ *    PIKO_NOALLOC_MAX_BINS, are rejected with PIKO_ERR_INVALID_ARG.  When
+ *    a host-side argument check fails nothing is enqueued; the other
+ *    host-side checks are those of piko_raster_forward.  A CUDA error while
+ *    enqueuing returns PIKO_ERR_CUDA, possibly after part of the work was
+ *    enqueued.
  *  - status_out (a device int32, may be NULL) receives PIKO_OK or the first
  *    device-side condition when the pass finishes: PIKO_ERR_OVERFLOW if the
  *    bin lists need more than PIKO_NOALLOC_MAX_BIN_ENTRIES entries (the

@@ -14,6 +14,8 @@
 // triangles, PIKO_NOALLOC_MAX_BINS tiles and PIKO_NOALLOC_MAX_BIN_ENTRIES
 // (triangle, tile) pairs; about 6.3 MB of device memory that every GPU which
 // loads this library keeps until the process exits.
+#include <cuda.h>
+
 #include <atomic>
 #include <mutex>
 
@@ -26,16 +28,20 @@ namespace {
 constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 // layout of the scratch array
+// The scan's chunk states sit directly before the per-tile counts so that
+// one memset clears both at the start of every call.
+constexpr int MAX_CHUNKS = 64;
 constexpr size_t OFF_STATUS = 0;
 constexpr size_t OFF_VTX = align256(OFF_STATUS + sizeof(DevStatus));
 constexpr size_t OFF_VDOT = align256(OFF_VTX + sizeof(int4) * PIKO_NOALLOC_MAX_VERTICES);
 constexpr size_t OFF_RECT = align256(OFF_VDOT + sizeof(float) * PIKO_NOALLOC_MAX_VERTICES);
-constexpr size_t OFF_COUNT = align256(OFF_RECT + sizeof(BinRect) * PIKO_NOALLOC_MAX_TRIANGLES);
+constexpr size_t OFF_CHUNKS = align256(OFF_RECT + sizeof(BinRect) * PIKO_NOALLOC_MAX_TRIANGLES);
+constexpr size_t OFF_COUNT = OFF_CHUNKS + sizeof(unsigned long long) * MAX_CHUNKS;
 constexpr size_t OFF_OFFS = align256(OFF_COUNT + sizeof(unsigned) * 2 * PIKO_NOALLOC_MAX_BINS);
 constexpr size_t OFF_CURSOR = align256(OFF_OFFS + sizeof(unsigned) * (PIKO_NOALLOC_MAX_BINS + 1));
-constexpr size_t OFF_CHUNKS = align256(OFF_CURSOR + sizeof(unsigned) * PIKO_NOALLOC_MAX_BINS);
-constexpr size_t OFF_ENTRIES = align256(OFF_CHUNKS + sizeof(unsigned long long) * 64);
-static_assert(PIKO_NOALLOC_MAX_BINS / 2048 + 1 <= 64, "scan chunk states (2048 bins each) must fit");
+constexpr size_t OFF_ENTRIES = align256(OFF_CURSOR + sizeof(unsigned) * PIKO_NOALLOC_MAX_BINS);
+static_assert(PIKO_NOALLOC_MAX_BINS / 2048 + 1 <= MAX_CHUNKS, "scan chunk states (2048 bins each) must fit");
+static_assert(OFF_COUNT % 256 == 0, "counts stay 256-byte aligned");
 constexpr size_t SCRATCH_BYTES = align256(OFF_ENTRIES + sizeof(unsigned) * (size_t)PIKO_NOALLOC_MAX_BIN_ENTRIES);
 
 // The one scratch buffer shared by every call on a device.  In host code this
@@ -43,29 +49,85 @@ constexpr size_t SCRATCH_BYTES = align256(OFF_ENTRIES + sizeof(unsigned) * (size
 // address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 
-constexpr int MAX_DEVICES = 64;
-std::atomic<unsigned> g_scan_epoch{0};  // distinct per call: the scan's chunk states are never cleared
+std::atomic<unsigned> g_scan_epoch{0};
 std::mutex g_setup_lock;
-unsigned char* g_scratch_addr[MAX_DEVICES] = {};
 
-// Looks up the device address of the scratch array for the current device,
-// once per device.
-int scratch_for_current_device(unsigned char** out) {
+// The array's device address belongs to the module instance of one CUDA
+// context: the primary context of a device normally, but a caller may run
+// in a context of its own (cuCtxCreate), and cudaDeviceReset replaces the
+// primary context.  So the address is cached per context, keyed by the
+// context's unique id (cuCtxGetId: never reused within a process), and
+// looked up again for a context not seen before.  The two driver calls are
+// reached through the runtime's entry-point query, so the library does not
+// link the driver library directly.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+constexpr int MAX_CONTEXTS = 64;
+struct CtxScratch {
+  unsigned long long ctx_id;
+  unsigned char* addr;
+};
+CtxScratch g_ctx_cache[MAX_CONTEXTS] = {};
+int g_ctx_count = 0, g_ctx_next = 0;
+
+bool driver_entry_points() {
+  if (g_ctx_get_current && g_ctx_get_id) return true;
+  cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = cudaDriverEntryPointSymbolNotFound;
+  void* f1 = nullptr;
+  void* f2 = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+      cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+      q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+    cudaGetLastError();
+    return false;
+  }
+  g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+  g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f2);
+  return true;
+}
+
+// Device address of the scratch array in the current context.  The first
+// call in a context (once per device for callers on the primary context)
+// looks it up with cudaGetSymbolAddress; later calls reuse it.
+int scratch_for_current_context(unsigned char** out) {
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
     cudaGetLastError();
     return PIKO_ERR_CUDA;
   }
   std::lock_guard<std::mutex> lock(g_setup_lock);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+  if (!driver_entry_points()) return PIKO_ERR_CUDA;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return PIKO_ERR_CUDA;
+  if (!ctx) {
+    // no context is current on this thread yet: the runtime would use the
+    // device's primary context, so make that one current and key on it
+    if (cudaSetDevice(dev) != cudaSuccess) {
       cudaGetLastError();
       return PIKO_ERR_CUDA;
     }
-    g_scratch_addr[dev] = static_cast<unsigned char*>(p);
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return PIKO_ERR_CUDA;
   }
-  *out = g_scratch_addr[dev];
+  if (g_ctx_get_id(ctx, &id) != CUDA_SUCCESS) return PIKO_ERR_CUDA;
+  for (int i = 0; i < g_ctx_count; ++i)
+    if (g_ctx_cache[i].ctx_id == id) {
+      *out = g_ctx_cache[i].addr;
+      return PIKO_OK;
+    }
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+    cudaGetLastError();
+    return PIKO_ERR_CUDA;
+  }
+  // a context that is gone keeps its entry until the ring wraps; ids are
+  // never reused, so a stale entry is never matched
+  CtxScratch& slot = g_ctx_count < MAX_CONTEXTS ? g_ctx_cache[g_ctx_count++] : g_ctx_cache[g_ctx_next++ % MAX_CONTEXTS];
+  slot.ctx_id = id;
+  slot.addr = static_cast<unsigned char*>(p);
+  *out = slot.addr;
   return PIKO_OK;
 }
 
@@ -81,7 +143,7 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 extern "C" int piko_raster_forward_noalloc(const piko_scene* s, piko_framebuffer* fb, int bin_w, int bin_h,
                                            int schedule, int32_t* status_out, void* cuda_stream) {
-  // ---- host-side checks: nothing is enqueued when one fails
+  // ---- host-side argument checks: nothing is enqueued when one fails
   if (!s || !fb || !fb->key) return PIKO_ERR_INVALID_ARG;
   if (s->width < 1 || s->height < 1 || s->width > 32767 || s->height > 32767) return PIKO_ERR_INVALID_ARG;
   if (!valid_bin(bin_w) || !valid_bin(bin_h)) return PIKO_ERR_INVALID_ARG;
@@ -101,7 +163,7 @@ extern "C" int piko_raster_forward_noalloc(const piko_scene* s, piko_framebuffer
   if (s->shade_mode == PIKO_SHADE_GBUFFER && (!fb->gbuf_normal || !fb->gbuf_albedo)) return PIKO_ERR_INVALID_ARG;
 
   unsigned char* base = nullptr;
-  int r = scratch_for_current_device(&base);
+  int r = scratch_for_current_context(&base);
   if (r != PIKO_OK) return r;
   int dev = 0, num_sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -126,10 +188,13 @@ extern "C" int piko_raster_forward_noalloc(const piko_scene* s, piko_framebuffer
   const int nbins = nbx * nby;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
 
-  // The array keeps whatever the previous call left in it: the status word
-  // and the per-tile counts must start at zero.
+  // The array keeps whatever the previous call left in it: the status word,
+  // the scan's chunk states and the per-tile counts must start at zero.  A
+  // cleared chunk state reads as "not published", so no state left by an
+  // earlier call (with more tiles, or an epoch tag that has wrapped) can be
+  // taken for this call's.
   if (cudaMemsetAsync(status, 0, sizeof(DevStatus), st) != cudaSuccess ||
-      cudaMemsetAsync(bin_count, 0, sizeof(unsigned) * 2 * nbins, st) != cudaSuccess) {
+      cudaMemsetAsync(chunk_state, 0, (OFF_COUNT - OFF_CHUNKS) + sizeof(unsigned) * 2 * nbins, st) != cudaSuccess) {
     cudaGetLastError();
     return PIKO_ERR_CUDA;
   }

@@ -609,3 +609,63 @@ def test_power_law_and_sphere_generators():
     sph, mvps = S.sphere_views(num_views=4)
     assert sph.num_vertices == 199 * 250 + 2 and sph.num_triangles == 99_500
     assert mvps.shape == (4, 16)
+
+
+# ------------------------------------------------- O12 G-buffer layout, O13 loss
+def test_gbuffer_words_hand_derived_4x4():
+    """G-buffer output layout (normal + 0, albedo + alpha 1, empty pixels all
+    zero) and binary16 words against values derived by hand."""
+    with open(os.path.join(GOLDEN, "gbuffer_4x4.json")) as f:
+        g = json.load(f)
+    s = fixed_scene(4, 4, g["verts_fixed"], g["tris"], color=g["albedo"], normal=g["normal"], mode=2)
+    key, st = oracle.raster_brute(s)
+    assert st == 0
+    gn, ga = oracle.shade(s, key)
+    assert gn.dtype == np.uint16 and ga.dtype == np.uint16 and gn.shape == (4, 4, 4)
+    for j in range(4):
+        for i in range(4):
+            k = f"{i},{j}"
+            if k in g["normal_words"]:
+                assert gn[j, i].tolist() == g["normal_words"][k], k
+                assert ga[j, i].tolist() == g["albedo_words"][k], k
+            else:
+                assert key[j, i] == EMPTY, k
+                assert gn[j, i].tolist() == [0, 0, 0, 0] and ga[j, i].tolist() == [0, 0, 0, 0], k
+
+
+def _loss_scene(mode, color, normal=None, light=None):
+    with open(os.path.join(GOLDEN, "gbuffer_4x4.json")) as f:
+        g = json.load(f)
+    return fixed_scene(4, 4, g["verts_fixed"], g["tris"], color=color, normal=normal, mode=mode, light=light)
+
+
+def test_loss_closed_form_gouraud_one_triangle():
+    """One constant-colour triangle over six of 16 pixels: covered pixels
+    contribute |c - t|^2, empty ones |t|^2 over RGB; alpha never enters."""
+    c = np.array([0.5, 0.25, 1.0])
+    s = _loss_scene(0, np.tile(c, (4, 1)))
+    key, st = oracle.raster_brute(s)
+    assert st == 0 and int((key != EMPTY).sum()) == 6
+    target = np.zeros((4, 4, 4), np.float32)
+    target[..., 3] = 5.0                       # alpha of the target is ignored
+    target[key == EMPTY, :3] = 0.5             # empty pixels: rgb 0 against 0.5
+    # 6 * (0.25 + 0.0625 + 1) + 10 * 3 * 0.25 = 7.875 + 7.5
+    assert oracle.loss(s, key, target) == 15.375
+    target[key != EMPTY, :3] = c                # covered pixels exact: only the empty ones remain
+    assert oracle.loss(s, key, target) == 7.5
+
+
+def test_loss_closed_form_lambert_clamp():
+    """Lambert with n = (0, 0, 1), albedo R linear in x (0.125 + 0.25 i at
+    column i): L = (0, 0, 0.5) gives sum over covered (i, j) of
+    (0.5 (0.125 + 0.25 i))^2 = 0.25 (3 * 0.125^2 + 2 * 0.375^2 + 0.625^2) =
+    0.1796875; L = (0, 0, -0.5) clamps to 0 (loss 0) unless unclamped."""
+    col = np.array([[0.0, 0, 0], [1.0, 0, 0], [0, 0, 0], [0.0, 0, 0]])
+    nrm = np.tile([0.0, 0.0, 1.0], (4, 1))
+    target = np.zeros((4, 4, 4), np.float32)
+    s = _loss_scene(1, col, nrm, [0.0, 0.0, 0.5])
+    key, _ = oracle.raster_brute(s)
+    assert oracle.loss(s, key, target) == 0.1796875
+    s = _loss_scene(1, col, nrm, [0.0, 0.0, -0.5])
+    assert oracle.loss(s, key, target) == 0.0
+    assert oracle.loss(s, key, target, unclamped=True) == 0.1796875

@@ -62,8 +62,109 @@ def measured_peaks() -> dict:
         return {}
 
 
+class _NvmlLib:
+    """Read-only NVML queries through ctypes (libnvidia-ml ships with the
+    driver; no Python package needed)."""
+
+    SM = 1  # NVML_CLOCK_SM
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, torch_index: int):
+        import ctypes as C
+        self.C = C
+        lib = C.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.lib = lib
+        self.dev = C.c_void_p()
+        ok = False
+        try:
+            import torch
+            p = torch.cuda.get_device_properties(torch_index)
+            bus = "%08X:%02X:%02X.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+            ok = lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), C.byref(self.dev)) == 0
+        except Exception:
+            ok = False
+        if not ok and lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(torch_index), C.byref(self.dev)) != 0:
+            raise OSError("no NVML handle for the device")
+        self.get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = C.c_uint(0)
+        self.max_mhz = float(mx.value) if lib.nvmlDeviceGetMaxClockInfo(self.dev, self.SM, C.byref(mx)) == 0 else None
+
+    def sample(self):
+        C = self.C
+        mhz, mw, rs = C.c_uint(0), C.c_uint(0), C.c_ulonglong(0)
+        sm = float(mhz.value) if self.lib.nvmlDeviceGetClockInfo(self.dev, self.SM, C.byref(mhz)) == 0 else None
+        pw = mw.value / 1000.0 if self.lib.nvmlDeviceGetPowerUsage(self.dev, C.byref(mw)) == 0 else None
+        reasons = rs.value if self.get_reasons(self.dev, C.byref(rs)) == 0 else 0
+        return sm, pw, reasons
+
+
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled while the timed region runs."""
+    """SM clock, power and clock-event reasons sampled during the timed
+    regions.  NVML is polled in-process every ``period_ms`` on a background
+    thread (read-only queries), so that even a timed loop of a few
+    milliseconds gets samples; nvidia-smi (100 ms) is the fallback when NVML
+    cannot be loaded.  ``mark()`` returns a sample index; ``summary(a, b)``
+    summarises the samples taken between two marks."""
+
+    def __init__(self, index: int, period_ms: float = 0.5):
+        import threading
+        self.rows = []  # (t, sm_mhz, power_w, reasons set)
+        self.max_mhz = None
+        self.source = "nvml"
+        self._stop = threading.Event()
+        self._thread = None
+        try:
+            nv = _NvmlLib(index)
+            self.max_mhz = nv.max_mhz
+
+            def loop():
+                while not self._stop.is_set():
+                    sm, pw, rs = nv.sample()
+                    self.rows.append((time.perf_counter(), sm, pw,
+                                      {name for bit, name in nv.REASONS.items() if rs & bit}))
+                    time.sleep(period_ms * 1e-3)
+
+            self._thread = threading.Thread(target=loop, daemon=True)
+            self._thread.start()
+        except OSError:
+            self.source = "nvidia-smi"
+            self._smi = _SmiSampler(index)
+
+    def mark(self) -> int:
+        if self._thread is None:
+            return self._smi.mark()
+        return len(self.rows)
+
+    def summary(self, begin: int, end: int | None = None) -> dict:
+        if self._thread is None:
+            return self._smi.summary(begin, end)
+        rows = self.rows[begin:end]
+        sm = [r[1] for r in rows if r[1]]
+        pw = [r[2] for r in rows if r[2] is not None]
+        reasons = sorted(set().union(*[r[3] for r in rows])) if rows else []
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.max_mhz,
+                "sm_mhz_min": min(sm) if sm else None, "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(pw) if pw else None, "source": self.source}
+
+    def stop(self, first_line: int = 0) -> dict:
+        out = self.summary(first_line)
+        self.close()
+        return out
+
+    def close(self):
+        if self._thread is not None:
+            self._stop.set()
+            self._thread.join(timeout=2)
+        elif getattr(self, "_smi", None) is not None:
+            self._smi.close()
+
+
+class _SmiSampler:
+    """nvidia-smi clocks and throttle reasons every 100 ms (fallback)."""
 
     FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
               "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
@@ -79,27 +180,21 @@ class ClockSampler:
         except OSError:
             self.proc = None
 
-    def mark(self):
+    def _rows(self):
         self.out.flush()
         try:
-            return sum(1 for _ in open(self.out.name))
+            rows = [ln.strip().split(",") for ln in open(self.out.name)]
         except OSError:
-            return 0
+            return []
+        return [[c.strip() for c in r] for r in rows if len(r) == len(self.FIELDS)]
 
-    def stop(self, first_line: int = 0) -> dict | None:
-        if self.proc is None:
-            return None
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        self.out.flush()
-        rows = [ln.strip().split(",") for ln in open(self.out.name)][first_line:]
-        os.unlink(self.out.name)
-        rows = [[c.strip() for c in r] for r in rows if len(r) == len(self.FIELDS)]
+    def mark(self):
+        return len(self._rows())
+
+    def summary(self, begin, end=None) -> dict:
+        rows = self._rows()[begin:end]
         if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "source": "nvidia-smi"}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         reasons = set()
@@ -109,8 +204,20 @@ class ClockSampler:
                 if v.lower() in ("active", "1", "yes"):
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(rows),
+                "reasons": sorted(reasons), "samples": len(rows), "source": "nvidia-smi",
                 "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
+
+    def close(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        try:
+            os.unlink(self.out.name)
+        except OSError:
+            pass
 
 
 def max_over_ranks(x: float, dist=None, device="cpu") -> float:
@@ -140,37 +247,94 @@ def workload(args):
     return scene, cfg
 
 
-def cpu_baseline(scene, seconds: float, perspective: bool = False) -> dict:
-    """The oracle as it stands: bounding-box loop on all host cores + float64 shading."""
-    import oracle
+# ---------------------------------------------------------------- CPU side
+def host_cpu() -> dict:
+    """Host cores this process may use and the CPU model (lscpu, else /proc/cpuinfo)."""
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.TimeoutExpired):
+        pass
+    if not model:
+        try:
+            info = open("/proc/cpuinfo").read().splitlines()
+            for ln in info:
+                if ln.lower().startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+            if not model:
+                impl = next((ln.split(":")[1].strip() for ln in info if ln.startswith("CPU implementer")), "?")
+                part = next((ln.split(":")[1].strip() for ln in info if ln.startswith("CPU part")), "?")
+                model = f"CPU implementer {impl}, part {part}"
+        except OSError:
+            model = "unknown"
+    return {"cores": cores, "cpu_model": model}
+
+
+def _repeat(fn, seconds: float):
+    """Runs fn() until ``seconds`` have passed (at least once): (reps, seconds per rep)."""
     reps, t0 = 0, time.perf_counter()
     while True:
-        key, _ = oracle.raster_bbox(scene, threads=cores)
-        oracle.shade(scene, key, perspective=perspective)
+        fn()
         reps += 1
         if time.perf_counter() - t0 >= seconds:
             break
-    dt = (time.perf_counter() - t0) / reps
-    return {"value": scene.num_triangles / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{reps} full frame(s) of the same workload: bounding-box oracle on {cores} threads "
-                      f"plus float64 shading, {dt:.2f} s per frame"}
+    return reps, (time.perf_counter() - t0) / reps
+
+
+def _band(scene, n):
+    """The scene with only its first n triangles (same vertices, camera and shading)."""
+    import dataclasses
+
+    import numpy as np
+    return dataclasses.replace(scene, tris=np.ascontiguousarray(scene.tris[:n]))
+
+
+def oracle_frame_fn(scene, threads, perspective=False, extra=None):
+    import oracle
+
+    def fn():
+        key, _ = oracle.raster_bbox(scene, threads=threads)
+        out = oracle.shade(scene, key, perspective=perspective)
+        if extra is not None:
+            extra(key, out)
+    return fn
+
+
+def cpu_baseline(scene, seconds: float, perspective: bool = False, single_seconds: float = 3.0,
+                 extra=None, what: str = "bounding-box oracle plus float64 shading") -> dict:
+    """The oracle as it stands, on the host cores: full frames on every core
+    (row bands), and a band of the triangles on one thread."""
+    hc = host_cpu()
+    cores = hc["cores"]
+    reps, dt = _repeat(oracle_frame_fn(scene, cores, perspective, extra), seconds)
+    T = scene.num_triangles
+    # single thread: a leading band of the triangles, sized from a probe
+    n = max(1, T // 64)
+    t0 = time.perf_counter()
+    oracle_frame_fn(_band(scene, n), 1, perspective, extra)()
+    t1 = max(time.perf_counter() - t0, 1e-6)
+    n = int(max(1, min(T, n * single_seconds / t1)))
+    r1, d1 = _repeat(oracle_frame_fn(_band(scene, n), 1, perspective, extra), single_seconds)
+    return {"value": T / dt / 1e6, "unit": UNIT, "cores": cores, "cpu_model": hc["cpu_model"], "kind": "oracle",
+            "sample": f"{reps} full frame(s): {what} on {cores} threads, {dt:.3f} s per frame",
+            "single_thread": {"value": n / d1 / 1e6, "unit": UNIT, "cores": 1,
+                              "sample": f"first {n} of {T} triangles per frame, {r1} frame(s), {what} on one "
+                                        f"thread, {d1:.3f} s per frame"}}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    import numpy as np
-
     import oracle
-    from paper_1404_6293_gb300 import scenes as S
     scene, cfg = workload(args)
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
-
-    def sub(n):
-        return S.Scene(scene.width, scene.height, scene.pos, np.ascontiguousarray(scene.tris[:n]),
-                       normal=scene.normal, mvp=scene.mvp, light_dir=scene.light_dir, shade_mode=scene.shade_mode)
+    cores = host_cpu()["cores"]
 
     def step(sc):
         key, _ = oracle.raster_bbox(sc, threads=cores)
@@ -179,11 +343,11 @@ def run_reference(args):
     # size the per-step sample so that warm-up plus timed steps stay near two minutes
     n = scene.num_triangles // 32
     t0 = time.perf_counter()
-    step(sub(n))
+    step(_band(scene, n))
     t1 = time.perf_counter() - t0
     budget = 120.0 / max(1, args.steps + args.warmup)
     n = int(max(2000, min(scene.num_triangles, n * budget / max(t1, 1e-6))))
-    sc = sub(n)
+    sc = _band(scene, n)
     for _ in range(args.warmup):
         step(sc)
     times = []
@@ -203,6 +367,130 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ---------------------------------------------------------------- GPU side
+class Ctx:
+    """What every measurement shares: stream, L2 flush buffer, peaks, clocks."""
+
+    def __init__(self, clocks):
+        import torch
+        self.torch = torch
+        self.stream = torch.cuda.current_stream()
+        self.flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        self.peaks = measured_peaks()
+        self.hbm = float(self.peaks.get("hbm_gbs", 6800.0))
+        self.n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        self.clocks = clocks
+
+    def event(self):
+        e = self.torch.cuda.Event(enable_timing=True)
+        e.record(self.stream)  # creates the underlying CUDA event
+        return e
+
+    def f_mhz(self, clk) -> float:
+        return (clk or {}).get("sm_mhz") or float(self.peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1470.0))
+
+    def alu_peak(self, clk) -> float:
+        """Thread-ops/s of the SMs at the sampled clock, in Gop/s."""
+        return self.n_sm * ALU_OPS_PER_SM_CLK * self.f_mhz(clk) * 1e6 / 1e9
+
+
+def time_forward(ctx, r, ds, fb, K, W, stages=True):
+    """Per-step forward times (ms, CUDA events around each step on the
+    launching stream, L2 flushed between steps) and, in a second loop, the
+    per-stage times from the library's stage events."""
+    import numpy as np
+    torch = ctx.torch
+    for _ in range(W):
+        ctx.flush.zero_()
+        r.forward(ds, fb)
+    ev = [(ctx.event(), ctx.event()) for _ in range(K)]
+    torch.cuda.synchronize()
+    for k in range(K):
+        ctx.flush.zero_()
+        ev[k][0].record(ctx.stream)
+        r.forward(ds, fb)
+        ev[k][1].record(ctx.stream)
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    stage_ms = None
+    if stages:
+        from paper_1404_6293_gb300 import _lib as L
+        sev = [[ctx.event() for _ in range(L.PIKO_NUM_STAGE_EVENTS)] for _ in range(K)]
+        torch.cuda.synchronize()
+        for k in range(K):
+            ctx.flush.zero_()
+            r.set_stage_events(sev[k])
+            r.forward(ds, fb)
+        torch.cuda.synchronize()
+        r.set_stage_events(None)
+        stage_ms = np.array([[sev[k][i].elapsed_time(sev[k][i + 1]) for i in range(L.PIKO_NUM_STAGE_EVENTS - 1)]
+                             for k in range(K)])
+    return step_ms, stage_ms
+
+
+def size_and_count(r, ds, fb):
+    """One forward that sizes the bin lists, then one with the work counters:
+    (stats, covered pixels).  Leaves the capacity check off and the counters off."""
+    from paper_1404_6293_gb300 import _lib as L
+    r.forward(ds, fb)
+    code, _ = r.status()
+    if code != 0:
+        raise RuntimeError(f"forward status {code}")
+    r.set_option(L.PIKO_OPT_CHECK_CAPACITY, 0)
+    r.set_option(L.PIKO_OPT_STATS, 1)
+    r.forward(ds, fb)
+    stats = r.stats()
+    r.set_option(L.PIKO_OPT_STATS, 0)
+    return stats, int((fb.key != -1).sum().item())
+
+
+def process_roofline(ctx, scene, stats, proc_ms, clk, traffic=None) -> dict:
+    """Roofline of the Process kernel: algorithmic bytes (4 B per bin entry,
+    12 B of indices per binned triangle, 16 B per snapped vertex, 12 B per
+    vertex per attribute array, 24 B per pixel written) at the measured HBM
+    copy bandwidth, against algorithmic thread-ops at the sampled SM clock."""
+    V = scene.num_vertices
+    attr = 12 * V * ((scene.normal is not None) + (scene.color is not None))
+    bytes_proc = (4 * stats["bin_entries"] + 12 * stats["binned_triangles"] + 16 * V + attr
+                  + 24 * scene.width * scene.height)
+    ops_proc = (OPS_PER_ENTRY * stats["bin_entries"] + OPS_PER_TEST * stats["samples_tested"]
+                + OPS_PER_FRAGMENT * stats["fragments"] + OPS_PER_SHADE[scene.shade_mode] * stats["shaded"])
+    alu_peak = ctx.alu_peak(clk)
+    t_hbm = bytes_proc / (ctx.hbm * 1e9)
+    t_alu = ops_proc / (alu_peak * 1e9)
+    if t_alu >= t_hbm:
+        achieved = ops_proc / (proc_ms * 1e-3) / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gop/s",
+                "frac": achieved / alu_peak, "traffic": traffic,
+                "peak_note": f"{ctx.n_sm} SMs x 128 thread-ops/clk x {ctx.f_mhz(clk):.0f} MHz sampled SM clock"}
+    else:
+        achieved = bytes_proc / (proc_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": ctx.hbm, "unit": "GB/s", "frac": achieved / ctx.hbm,
+                "traffic": traffic, "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs)"}
+    roof.update({"kernel": "k_process", "kernel_ms": proc_ms, "algorithmic_bytes": bytes_proc,
+                 "algorithmic_ops": ops_proc, "t_hbm_us": t_hbm * 1e6, "t_alu_us": t_alu * 1e6,
+                 "sm_mhz_used": ctx.f_mhz(clk),
+                 "frac_at_2070mhz": max(t_hbm, ops_proc / (ctx.n_sm * 128 * 2070e6)) / (proc_ms * 1e-3)})
+    return roof
+
+
+def headline_traffic(args):
+    """ncu DRAM bytes per Process launch, when the committed record matches
+    these kernel sources and this launch configuration."""
+    try:
+        with open(PROFILE_TRAFFIC) as f:
+            prof = json.load(f)
+        bin_px = args.bins * args.bins
+        launch = {"bins": args.bins, "schedule": args.schedule,
+                  "threads": args.threads or (64 if bin_px <= 64 else (128 if bin_px <= 256 else 256)),
+                  "perspective": bool(args.perspective)}
+        if prof.get("kernel_hash") == kernel_hash() and prof.get("launch") == launch:
+            return prof.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
 
 
 def run_ours(args):
@@ -252,196 +540,49 @@ def run_ours(args):
         cfg["small_tri_pixels"] = args.small_px
     ds = DeviceScene.from_host(scene)
     fb = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode)
-    r.forward(ds, fb)  # sizes the bin lists (capacity check on)
-    code, need = r.status()
-    if code != 0:
-        raise RuntimeError(f"forward status {code}")
-    r.set_option(L.PIKO_OPT_CHECK_CAPACITY, 0)
-    r.set_option(L.PIKO_OPT_STATS, 1)
-    r.forward(ds, fb)
-    stats = r.stats()
-    r.set_option(L.PIKO_OPT_STATS, 0)
-    covered = int((fb.key != -1).sum().item())
+    stats, covered = size_and_count(r, ds, fb)
 
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    clocks = ClockSampler(torch.cuda.current_device() if world == 1 else local)
-    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(torch.cuda.current_device())
+    ctx = Ctx(clocks)
+    stream = ctx.stream
     for _ in range(args.warmup):
-        flush.zero_()
+        ctx.flush.zero_()
         r.forward(ds, fb)
     K = args.steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    for a, b in ev:
-        a.record(stream)
-        b.record(stream)
+    ev = [(ctx.event(), ctx.event()) for _ in range(K)]
     barrier()
-    first_clock_line = clocks.mark()
+    mark0 = clocks.mark()
     wall0 = time.perf_counter()
     for k in range(K):
-        flush.zero_()
+        ctx.flush.zero_()
         ev[k][0].record(stream)
         r.forward(ds, fb)
         ev[k][1].record(stream)
     barrier()
     wall = time.perf_counter() - wall0
-    clk = clocks.stop(first_clock_line)
+    mark1 = clocks.mark()
     code, _ = r.status()
     if code != 0:
         raise RuntimeError(f"status {code} after the timed loop")
     step_ms = [a.elapsed_time(b) for a, b in ev]
     # per-stage times in a separate loop: events between the stages would
     # break the launch overlap the timed loop has
-    Ks = min(K, 500)
-    sev = [[torch.cuda.Event(enable_timing=True) for _ in range(L.PIKO_NUM_STAGE_EVENTS)] for _ in range(Ks)]
-    for row in sev:
-        for e in row:
-            e.record(stream)
+    _, stage_ms = time_forward(ctx, r, ds, fb, min(K, 500), 1)
     barrier()
-    for k in range(Ks):
-        flush.zero_()
-        r.set_stage_events(sev[k])
-        r.forward(ds, fb)
-    barrier()
-    stage_ms = np.array([[sev[k][i].elapsed_time(sev[k][i + 1]) for i in range(L.PIKO_NUM_STAGE_EVENTS - 1)]
-                         for k in range(Ks)])
+    mark2 = clocks.mark()
+    clk = clocks.summary(mark0, mark1)
+    clk_both = clocks.summary(mark0, mark2)  # the timed loop and the per-stage loop: same kernels
+    if not clk.get("sm_mhz"):
+        clk = dict(clk_both, note="no sample inside the timed loop alone; summary over the timed and stage loops")
+    clk["with_stage_loop"] = {k: clk_both.get(k) for k in ("sm_mhz", "samples", "reasons")}
     ms = max_over_ranks(float(np.sum(step_ms) / K), dist, "cuda")
     value = job_throughput(T, world, ms)
     shaded_gfrag = job_throughput(covered, world, ms, 1e9)
-
-    # ---------------------------------------------------------------- roofline
-    peaks = measured_peaks()
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
     proc_ms = float(stage_ms[:, 4].mean())
-    V = scene.num_vertices
-    attr = 12 * V * ((scene.normal is not None) + (scene.color is not None))
-    bytes_proc = (4 * stats["bin_entries"] + 12 * stats["binned_triangles"] + 16 * V + attr
-                  + 24 * scene.width * scene.height)
-    ops_proc = (OPS_PER_ENTRY * stats["bin_entries"] + OPS_PER_TEST * stats["samples_tested"]
-                + OPS_PER_FRAGMENT * stats["fragments"] + OPS_PER_SHADE[scene.shade_mode] * stats["shaded"])
-    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-    f_mhz = (clk or {}).get("sm_mhz") or float(peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1470.0))
-    alu_peak = n_sm * ALU_OPS_PER_SM_CLK * f_mhz * 1e6 / 1e9  # Gop/s
-    t_hbm = bytes_proc / (hbm * 1e9)
-    t_alu = ops_proc / (alu_peak * 1e9)
-    traffic = None
-    try:
-        with open(PROFILE_TRAFFIC) as f:
-            prof = json.load(f)
-        bin_px = args.bins * args.bins
-        launch = {"bins": args.bins, "schedule": args.schedule,
-                  "threads": args.threads or (64 if bin_px <= 64 else (128 if bin_px <= 256 else 256)),
-                  "perspective": bool(args.perspective)}
-        # counters apply only to the same kernel sources in the same launch configuration
-        if prof.get("kernel_hash") == kernel_hash() and prof.get("launch") == launch:
-            traffic = prof.get("dram_bytes_per_launch")
-    except (OSError, ValueError):
-        pass
-    if t_alu >= t_hbm:
-        achieved = ops_proc / (proc_ms * 1e-3) / 1e9
-        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gop/s",
-                "frac": achieved / alu_peak, "traffic": traffic,
-                "peak_note": f"{n_sm} SMs x 128 thread-ops/clk x {f_mhz:.0f} MHz measured SM clock"}
-    else:
-        achieved = bytes_proc / (proc_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": traffic, "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs)"}
-    roof.update({"kernel": "k_process", "kernel_ms": proc_ms, "algorithmic_bytes": bytes_proc,
-                 "algorithmic_ops": ops_proc, "t_hbm_us": t_hbm * 1e6, "t_alu_us": t_alu * 1e6,
-                 "frac_at_2070mhz": (max(t_hbm, ops_proc / (n_sm * 128 * 2070e6)) / (proc_ms * 1e-3)),
-                 "forward_frac": max(t_hbm, t_alu) / (ms * 1e-3)})
+    roof = process_roofline(ctx, scene, stats, proc_ms, clk, headline_traffic(args))
+    roof["forward_frac"] = max(roof["t_hbm_us"], roof["t_alu_us"]) * 1e-3 / ms
 
-    # ---------------------------------------------------------------- end to end
-    e2e = None
-    r.set_stage_events(None)
-    if not args.no_e2e:
-        names = [n for n in ("pos", "tris", "normal", "color", "mvp", "light_dir") if getattr(ds, n) is not None]
-        host_in = {n: getattr(ds, n).cpu().pin_memory() for n in names}
-        key_h = torch.empty_like(fb.key, device="cpu").pin_memory()
-        rgba_h = torch.empty_like(fb.rgba, device="cpu").pin_memory()
-        h2d = sum(t.numel() * t.element_size() for t in host_in.values())
-        d2h = key_h.numel() * 8 + rgba_h.numel() * 4
-        Ke = min(K, args.e2e_steps)
-        pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(Ke)]
-        for _ in range(3):
-            r.render_from_host(host_in, ds, fb, key_h, rgba_h)
-        barrier()
-        # one frame at a time (L2 flushed between frames, outside the events)
-        for k in range(Ke):
-            flush.zero_()
-            pairs[k][0].record(stream)
-            r.render_from_host(host_in, ds, fb, key_h, rgba_h)
-            pairs[k][1].record(stream)
-        barrier()
-        seq_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in pairs) / Ke, dist, "cuda")
-        # frames alternate over two handles and two streams, so frame k+1's
-        # host-to-device copy runs while frame k renders and copies back; every
-        # frame still copies all its inputs in and its key and RGBA out
-        nl = max(2, args.e2e_lanes)
-        lanes = [(r, ds, fb, key_h, rgba_h)]
-        for _ in range(nl - 1):
-            rr = Rasterizer(scene.width, scene.height, args.bins, args.bins, args.schedule)
-            if args.threads:
-                rr.set_option(L.PIKO_OPT_THREADS_PER_TILE, args.threads)
-            if args.perspective:
-                rr.set_option(L.PIKO_OPT_PERSPECTIVE, 1)
-            d = DeviceScene.from_host(scene)
-            f = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode)
-            rr.forward(d, f)
-            if rr.status()[0] != 0:
-                raise RuntimeError("status error sizing an end-to-end handle")
-            rr.set_option(L.PIKO_OPT_CHECK_CAPACITY, 0)
-            lanes.append((rr, d, f, torch.empty_like(key_h).pin_memory(), torch.empty_like(rgba_h).pin_memory()))
-        side = [torch.cuda.Stream() for _ in range(nl)]
-        for k in range(3 * nl):
-            rr, d, f, kh, rh = lanes[k % nl]
-            rr.render_from_host(host_in, d, f, kh, rh, stream=side[k % nl])
-        barrier()
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for sd in side:
-            sd.wait_stream(stream)
-        for k in range(Ke):
-            rr, d, f, kh, rh = lanes[k % nl]
-            rr.render_from_host(host_in, d, f, kh, rh, stream=side[k % nl])
-        for sd in side:
-            stream.wait_stream(sd)
-        e1.record(stream)
-        barrier()
-        e_ms = max_over_ranks(e0.elapsed_time(e1) / Ke, dist, "cuda")
-        # the same frames' copies alone, on the same lanes and streams: the
-        # floor that the end-to-end frames cannot go below
-        flush.zero_()
-        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        c0.record(stream)
-        for sd in side:
-            sd.wait_stream(stream)
-        for k in range(Ke):
-            rr, d, f, kh, rh = lanes[k % nl]
-            with torch.cuda.stream(side[k % nl]):
-                for n, t in host_in.items():
-                    getattr(d, n).copy_(t, non_blocking=True)
-                kh.copy_(f.key, non_blocking=True)
-                rh.copy_(f.rgba, non_blocking=True)
-        for sd in side:
-            stream.wait_stream(sd)
-        c1.record(stream)
-        barrier()
-        c_ms = max_over_ranks(c0.elapsed_time(c1) / Ke, dist, "cuda")
-        e2e = {"value": job_throughput(T, world, e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": e_ms, "steps": Ke,
-               "how": "Rasterizer.render_from_host per frame: pinned host -> device copies of every input, "
-                      f"forward, device -> host copies of key and RGBA; frames rotate over {nl} handles and "
-                      f"{nl} streams so copies overlap the other frames' work",
-               "sequential": {"value": job_throughput(T, world, seq_ms), "ms_per_step": seq_ms,
-                              "how": "one frame at a time on one stream, L2 flushed between frames"},
-               "copies_only": {"ms_per_step": c_ms, "gb_s": (h2d + d2h) / (c_ms * 1e6),
-                               "frac_of_e2e_time": c_ms / e_ms,
-                               "how": "the same frames' host<->device copies without the forward pass"}}
-        if any(ln[0].status()[0] != 0 for ln in lanes):
-            raise RuntimeError("status error after the end-to-end loop")
-        for ln in lanes[1:]:
-            ln[0].close()
+    e2e = None if args.no_e2e else measure_e2e(args, ctx, r, ds, fb, scene, world, dist, barrier)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -453,9 +594,20 @@ def run_ours(args):
             "wall_ms_incl_flush": 1e3 * wall / K,
             "roofline": roof, "clocks": clk, "e2e": e2e,
             "gpu_launches": 5 * K,
-            "parity": "depth/ID bit-exact vs the CPU oracle in tests/test_gpu_parity.py (same workload)"}
+            "parity": "depth/ID bit-exact vs the CPU oracle on this workload under every schedule "
+                      "(tests/test_gpu_full_size.py)"}
+    if rank == 0 and world == 1 and not args.no_configs:
+        line["bin_sweep"] = bin_sweep(args, ctx, scene, ds)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene, args.cpu_seconds, args.perspective)
+    if rank == 0 and world == 1 and not args.no_configs:
+        line["configs"] = {
+            "C1_random_256": measure_random256(args, ctx),
+            "C3_deferred_powerlaw_1080p": measure_deferred(args, ctx),
+            "C4_sphere_64_views": measure_sphere(args, ctx),
+            "C5_batch_256_scenes": measure_batch(args, ctx),
+        }
+    clocks.close()
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -464,225 +616,366 @@ def run_ours(args):
     return 0
 
 
-def _timed_steps(step, K, warmup, flush, stream):
+def measure_e2e(args, ctx, r, ds, fb, scene, world, dist, barrier) -> dict:
+    """The same metric through Rasterizer.render_from_host: pinned host ->
+    device copies of every input, the forward pass, device -> host copies of
+    key and RGBA, all inside the events."""
     import torch
-    for _ in range(warmup):
-        flush.zero_()
-        step(None)
+
+    from paper_1404_6293_gb300 import _lib as L
+    from paper_1404_6293_gb300.raster import DeviceScene, Framebuffer, Rasterizer
+    T = scene.num_triangles
+    stream = ctx.stream
+    K = args.steps
+    names = [n for n in ("pos", "tris", "normal", "color", "mvp", "light_dir") if getattr(ds, n) is not None]
+    host_in = {n: getattr(ds, n).cpu().pin_memory() for n in names}
+    key_h = torch.empty_like(fb.key, device="cpu").pin_memory()
+    rgba_h = torch.empty_like(fb.rgba, device="cpu").pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host_in.values())
+    d2h = key_h.numel() * 8 + rgba_h.numel() * 4
+    Ke = min(K, args.e2e_steps)
+    pairs = [(ctx.event(), ctx.event()) for _ in range(Ke)]
+    for _ in range(3):
+        r.render_from_host(host_in, ds, fb, key_h, rgba_h)
+    barrier()
+    # one frame at a time (L2 flushed between frames, outside the events)
+    for k in range(Ke):
+        ctx.flush.zero_()
+        pairs[k][0].record(stream)
+        r.render_from_host(host_in, ds, fb, key_h, rgba_h)
+        pairs[k][1].record(stream)
+    barrier()
+    seq_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in pairs) / Ke, dist, "cuda")
+    # frames rotate over several handles and streams, so frame k+1's
+    # host-to-device copy runs while frame k renders and copies back; every
+    # frame still copies all its inputs in and its key and RGBA out
+    nl = max(2, args.e2e_lanes)
+    lanes = [(r, ds, fb, key_h, rgba_h)]
+    for _ in range(nl - 1):
+        rr = Rasterizer(scene.width, scene.height, args.bins, args.bins, args.schedule)
+        if args.threads:
+            rr.set_option(L.PIKO_OPT_THREADS_PER_TILE, args.threads)
+        if args.perspective:
+            rr.set_option(L.PIKO_OPT_PERSPECTIVE, 1)
+        if args.small_px:
+            rr.set_option(L.PIKO_OPT_SMALL_TRI_PIXELS, args.small_px)
+        d = DeviceScene.from_host(scene)
+        f = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode)
+        rr.forward(d, f)
+        if rr.status()[0] != 0:
+            raise RuntimeError("status error sizing an end-to-end handle")
+        rr.set_option(L.PIKO_OPT_CHECK_CAPACITY, 0)
+        lanes.append((rr, d, f, torch.empty_like(key_h).pin_memory(), torch.empty_like(rgba_h).pin_memory()))
+    side = [torch.cuda.Stream() for _ in range(nl)]
+    for k in range(3 * nl):
+        rr, d, f, kh, rh = lanes[k % nl]
+        rr.render_from_host(host_in, d, f, kh, rh, stream=side[k % nl])
+    barrier()
+    ctx.flush.zero_()
+    e0, e1 = ctx.event(), ctx.event()
+    e0.record(stream)
+    for sd in side:
+        sd.wait_stream(stream)
+    for k in range(Ke):
+        rr, d, f, kh, rh = lanes[k % nl]
+        rr.render_from_host(host_in, d, f, kh, rh, stream=side[k % nl])
+    for sd in side:
+        stream.wait_stream(sd)
+    e1.record(stream)
+    barrier()
+    e_ms = max_over_ranks(e0.elapsed_time(e1) / Ke, dist, "cuda")
+    # the same frames' copies alone, on the same lanes and streams: the
+    # floor that the end-to-end frames cannot go below
+    ctx.flush.zero_()
+    c0, c1 = ctx.event(), ctx.event()
+    c0.record(stream)
+    for sd in side:
+        sd.wait_stream(stream)
+    for k in range(Ke):
+        rr, d, f, kh, rh = lanes[k % nl]
+        with torch.cuda.stream(side[k % nl]):
+            for n, t in host_in.items():
+                getattr(d, n).copy_(t, non_blocking=True)
+            kh.copy_(f.key, non_blocking=True)
+            rh.copy_(f.rgba, non_blocking=True)
+    for sd in side:
+        stream.wait_stream(sd)
+    c1.record(stream)
+    barrier()
+    c_ms = max_over_ranks(c0.elapsed_time(c1) / Ke, dist, "cuda")
+    if any(ln[0].status()[0] != 0 for ln in lanes):
+        raise RuntimeError("status error after the end-to-end loop")
+    for ln in lanes[1:]:
+        ln[0].close()
+    link = (h2d + d2h) / (c_ms * 1e6)
+    return {"value": job_throughput(T, world, e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": e_ms, "steps": Ke,
+            "how": "Rasterizer.render_from_host per frame: pinned host -> device copies of every input, "
+                   f"forward, device -> host copies of key and RGBA; frames rotate over {nl} handles and "
+                   f"{nl} streams so copies overlap the other frames' work",
+            "sequential": {"value": job_throughput(T, world, seq_ms), "ms_per_step": seq_ms,
+                           "how": "one frame at a time on one stream, L2 flushed between frames"},
+            "copies_only": {"ms_per_step": c_ms, "gb_s": link, "frac_of_e2e_time": c_ms / e_ms,
+                            "how": "the same frames' host<->device copies without the forward pass"},
+            "bound": {"kind": "host link", "link_gb_s_measured": link,
+                      "floor_ms": c_ms, "frac_of_floor": c_ms / e_ms,
+                      "note": "each frame moves its inputs in and its 8-byte key plus float32 RGBA out; the "
+                              "copies alone take copies_only.ms_per_step, which bounds this number"}}
+
+
+def bin_sweep(args, ctx, scene, ds) -> dict:
+    """Forward time of the headline workload at every bin size (8, 16, 32, 64)
+    under the hardware and dynamic schedules (the workload's bin-size sweep)."""
+    from paper_1404_6293_gb300 import _lib as L
+    from paper_1404_6293_gb300.raster import Framebuffer, Rasterizer
+    out = {}
+    K = args.steps
+    for b in (8, 16, 32, 64):
+        for sched in ("hardware", "dynamic"):
+            r = Rasterizer(scene.width, scene.height, b, b, sched)
+            if args.perspective:
+                r.set_option(L.PIKO_OPT_PERSPECTIVE, 1)
+            fb = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode)
+            stats, covered = size_and_count(r, ds, fb)
+            step_ms, stage_ms = time_forward(ctx, r, ds, fb, K, args.warmup)
+            ms = sum(step_ms) / K
+            out[f"{b}x{b} {sched}"] = {"ms_per_step": ms, "value": scene.num_triangles / (ms * 1e-3) / 1e6,
+                                       "process_ms": float(stage_ms[:, 4].mean()),
+                                       "bin_entries": stats["bin_entries"]}
+            r.close()
+    return out
+
+
+def measure_random256(args, ctx) -> dict:
+    """256x256, 1,000 random triangles of 40-px radius, Gouraud, 16x16 bins,
+    static schedule: a small frame, bound by launch latency."""
+    from paper_1404_6293_gb300 import scenes as S
+    from paper_1404_6293_gb300.raster import DeviceScene, Framebuffer, Rasterizer
+    scene = S.random_triangles()
+    r = Rasterizer(scene.width, scene.height, 16, 16, "static")
+    ds = DeviceScene.from_host(scene)
+    fb = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode)
+    stats, covered = size_and_count(r, ds, fb)
+    K = args.steps
+    m0 = ctx.clocks.mark()
+    step_ms, stage_ms = time_forward(ctx, r, ds, fb, K, args.warmup)
+    clk = ctx.clocks.summary(m0)
+    if r.status()[0] != 0:
+        raise RuntimeError("status error in the 256x256 loop")
+    ms = sum(step_ms) / K
+    proc_ms = float(stage_ms[:, 4].mean())
+    rec = {"workload": "random triangles 256x256, 1,000 triangles of 40-px radius, Gouraud, 16x16 bins, static",
+           "value": scene.num_triangles / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms,
+           "shaded_gfrag_s": covered / (ms * 1e-3) / 1e9,
+           "rasterized_gfrag_s": stats["fragments"] / (ms * 1e-3) / 1e9,
+           "stage_ms": {n: float(stage_ms[:, i].mean()) for i, n in
+                        enumerate(["vertex", "setup_count", "scan", "scatter", "process"])},
+           "work": {**stats, "covered_pixels": covered},
+           "roofline": process_roofline(ctx, scene, stats, proc_ms, clk), "clocks": clk, "gpu_launches": 5 * K,
+           "parity": "keys bit-exact, colour <= 1e-5 vs the oracle (tests/test_gpu_parity.py)"}
+    if not args.no_cpu_baseline:
+        import oracle
+        cb = cpu_baseline(scene, args.config_cpu_seconds, single_seconds=1.0)
+        t0 = time.perf_counter()
+        key, _ = oracle.raster_brute(scene)
+        oracle.shade(scene, key)
+        dt = time.perf_counter() - t0
+        cb["brute_force_single_thread"] = {"value": scene.num_triangles / dt / 1e6, "unit": UNIT,
+                                           "sample": f"one full frame, every pixel against every triangle on "
+                                                     f"one thread, {dt:.3f} s"}
+        rec["cpu_baseline"] = cb
+    r.close()
+    return rec
+
+
+def measure_deferred(args, ctx) -> dict:
+    """Power-law 1080p (500k triangles, area pdf ~ a^-2), G-buffer forward
+    then the 64-point-light pass."""
+    import numpy as np
+    import torch
+
+    from paper_1404_6293_gb300 import scenes as S
+    from paper_1404_6293_gb300 import _lib as L
+    from paper_1404_6293_gb300.raster import DeviceScene, Framebuffer, Rasterizer
+    scene = S.power_law_triangles()
+    lights = torch.from_numpy(S.point_lights(scene.width, scene.height, 64)).cuda()
+    bins = args.deferred_bins
+    r = Rasterizer(scene.width, scene.height, bins, bins, args.deferred_schedule)
+    ds = DeviceScene.from_host(scene)
+    fb = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode)
+    out = torch.empty((scene.height, scene.width, 4), dtype=torch.float32, device="cuda")
+    stats, covered = size_and_count(r, ds, fb)
+    K = args.steps
+    for _ in range(args.warmup):
+        ctx.flush.zero_()
+        r.forward(ds, fb)
+        r.deferred_light(fb, lights, out)
+    recs = []
     torch.cuda.synchronize()
-    records = []
+    m0 = ctx.clocks.mark()
     for _ in range(K):
-        flush.zero_()
-        marks = {}
-        step(marks)
-        records.append(marks)
+        ctx.flush.zero_()
+        st = [ctx.event() for _ in range(L.PIKO_NUM_STAGE_EVENTS)]
+        end = ctx.event()
+        r.set_stage_events(st)
+        r.forward(ds, fb)
+        r.deferred_light(fb, lights, out)
+        end.record(ctx.stream)
+        recs.append((st, end))
     torch.cuda.synchronize()
-    return records
+    clk = ctx.clocks.summary(m0)
+    if r.status()[0] != 0:
+        raise RuntimeError("status error in the deferred loop")
+    fwd = np.array([s[0].elapsed_time(s[5]) for s, _ in recs])
+    light = np.array([s[5].elapsed_time(e) for s, e in recs])
+    proc = np.array([s[4].elapsed_time(s[5]) for s, _ in recs])
+    ms = float((fwd + light).mean())
+    lt = float(light.mean()) * 1e-3
+    light_ops = 30 * covered * 64
+    alu_peak = ctx.alu_peak(clk)
+    light_bytes = scene.width * scene.height * (8 + 8 + 8 + 16)
+    rec = {"workload": "power-law 1920x1080, 500k triangles (area pdf ~ a^-2 on 1 px .. 1/4 screen), G-buffer "
+                       f"+ 64 point lights, {bins}x{bins} bins, {args.deferred_schedule}",
+           "value": scene.num_triangles / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms,
+           "shaded_gfrag_s": covered / (ms * 1e-3) / 1e9,
+           "rasterized_gfrag_s": stats["fragments"] / (ms * 1e-3) / 1e9,
+           "forward_ms": float(fwd.mean()), "process_ms": float(proc.mean()), "light_pass_ms": float(light.mean()),
+           "light_gpixlights_s": covered * 64 / lt / 1e9, "work": {**stats, "covered_pixels": covered},
+           "roofline": process_roofline(ctx, scene, stats, float(proc.mean()), clk),
+           "light_roofline": {"kernel": "k_deferred_light", "bound": "alu", "achieved": light_ops / lt / 1e9,
+                              "peak": alu_peak, "unit": "Gop/s", "frac": light_ops / lt / 1e9 / alu_peak,
+                              "hbm_frac": light_bytes / lt / 1e9 / ctx.hbm,
+                              "ops": "30 thread-ops per (covered pixel, light)"},
+           "clocks": clk, "gpu_launches": 6 * K,
+           "parity": "keys bit-exact, G-buffer within one binary16 step, light pass <= 1e-5 vs the oracle "
+                     "(tests/test_gpu_parity.py, tests/test_gpu_full_size.py)"}
+    if not args.no_cpu_baseline:
+        import oracle
+        lt_host = lights.cpu().numpy()
+
+        def light_pass(key, g):
+            oracle.light_pass(key, g[0], g[1], lt_host)
+        rec["cpu_baseline"] = cpu_baseline(scene, args.config_cpu_seconds, extra=light_pass, single_seconds=2.0,
+                                           what="bounding-box oracle, float64 G-buffer and 64-light pass")
+    r.close()
+    return rec
 
 
-def run_extra(args):
-    """Measurements of the other rows of the hot path (one GPU, rank 0):
-    deferred: power-law 1080p G-buffer forward + 64-light pass;
-    sphere: 64 views of a 99.5k-triangle sphere, forward + L2-loss backward."""
+def measure_sphere(args, ctx) -> dict:
+    """64 views at 512x512 of a 99.5k-triangle sphere, forward + L2-loss
+    backward (colour, normal, light): one forward_batch and one
+    backward_batch, each replayed from a CUDA graph."""
+    import dataclasses
+
     import numpy as np
     import torch
 
     from paper_1404_6293_gb300 import _lib as L
     from paper_1404_6293_gb300 import scenes as S
     from paper_1404_6293_gb300.raster import DeviceScene, Framebuffer, Rasterizer
+    stream = ctx.stream
+    sph, mvps = S.sphere_views(num_views=64)
+    W = H = 512
+    nv = 64
+    ds = DeviceScene.from_host(sph)
+    mv = torch.from_numpy(mvps).cuda()
+    views = [dataclasses.replace(ds, mvp=mv[v]) for v in range(nv)]
+    tgt = torch.from_numpy(S.target_image(W, H, seed=1240, views=nv)).cuda()
+    key_all = torch.empty((nv, H, W), dtype=torch.int64, device="cuda")
+    rgba_all = torch.empty((nv, H, W, 4), dtype=torch.float32, device="cuda")
+    g_all = torch.empty_like(rgba_all)
+    fbs = [Framebuffer(key_all[v], rgba_all[v]) for v in range(nv)]
+    gviews = [g_all[v] for v in range(nv)]
+    dc = torch.zeros_like(ds.color)
+    dn = torch.zeros_like(ds.normal)
+    dl = torch.zeros_like(ds.light_dir)
+    bins, scheds = [(16, 16)] * nv, ["dynamic"] * nv
+    rb = Rasterizer(W, H, 16, 16)
+    if args.perspective:
+        rb.set_option(L.PIKO_OPT_PERSPECTIVE, 1)
+    rb.forward_batch(views, fbs, bins, scheds)
+    assert rb.status()[0] == 0
+    rb.set_option(L.PIKO_OPT_CHECK_CAPACITY, 0)
+    covered = int((key_all != -1).sum().item())
 
-    torch.cuda.set_device(0)
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    peaks = measured_peaks()
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
-    def ev():
-        e = torch.cuda.Event(enable_timing=True)
-        e.record(stream)  # creates the underlying CUDA event
-        return e
-    clocks = ClockSampler(0)
-    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
-
-    if args.workload == "deferred":
-        scene = S.power_law_triangles()
-        lights = torch.from_numpy(S.point_lights(scene.width, scene.height, 64)).cuda()
-        r = Rasterizer(scene.width, scene.height, args.bins, args.bins, args.schedule)
-        if args.small_px:
-            r.set_option(L.PIKO_OPT_SMALL_TRI_PIXELS, args.small_px)
-        if args.threads:
-            r.set_option(L.PIKO_OPT_THREADS_PER_TILE, args.threads)
-        ds = DeviceScene.from_host(scene)
-        fb = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode)
-        out = torch.empty((scene.height, scene.width, 4), dtype=torch.float32, device="cuda")
-        r.forward(ds, fb)
-        assert r.status()[0] == 0
-        r.set_option(L.PIKO_OPT_CHECK_CAPACITY, 0)
-        r.set_option(L.PIKO_OPT_STATS, 1)
-        r.forward(ds, fb)
-        stats = r.stats()
-        r.set_option(L.PIKO_OPT_STATS, 0)
-        covered = int((fb.key != -1).sum().item())
-
-        def step(m):
-            if m is None:
-                r.forward(ds, fb)
-                r.deferred_light(fb, lights, out)
-                return
-            m["stage"] = [ev() for _ in range(L.PIKO_NUM_STAGE_EVENTS)]
-            m["light_end"] = ev()
-            r.set_stage_events(m["stage"])
-            r.forward(ds, fb)
-            r.deferred_light(fb, lights, out)
-            m["light_end"].record(stream)
-
-        mark = clocks.mark()
-        recs = _timed_steps(step, args.steps, args.warmup, flush, stream)
-        clk = clocks.stop(mark)
-        assert r.status()[0] == 0
-        fwd = np.array([m["stage"][0].elapsed_time(m["stage"][5]) for m in recs])
-        light = np.array([m["stage"][5].elapsed_time(m["light_end"]) for m in recs])
-        proc = np.array([m["stage"][4].elapsed_time(m["stage"][5]) for m in recs])
-        ms = float((fwd + light).mean())
-        light_ops = 30 * covered * 64
-        alu_peak = n_sm * 128 * ((clk or {}).get("sm_mhz") or 1470.0) * 1e6 / 1e9
-        light_bytes = scene.width * scene.height * (8 + 8 + 8 + 16)
-        lt = float(light.mean()) * 1e-3
-        line.update({"value": scene.num_triangles / (ms * 1e-3) / 1e6, "ms_per_step": ms, "dtype": "int64+f32",
-                     "config": {"workload": "power-law 1920x1080, 500k triangles, G-buffer + 64 point lights",
-                                "bin": [args.bins, args.bins], "schedule": args.schedule,
-                                "l2": "flushed between steps (256 MiB write)",
-                                **({"small_tri_pixels": args.small_px} if args.small_px else {}),
-                                **({"threads_per_tile": args.threads} if args.threads else {})},
-                     "forward_ms": float(fwd.mean()), "process_ms": float(proc.mean()),
-                     "light_pass_ms": float(light.mean()),
-                     "light_gpixlights_s": covered * 64 / lt / 1e9, "work": {**stats, "covered_pixels": covered},
-                     "roofline": {"kernel": "k_deferred_light", "bound": "alu" if light_ops / (alu_peak * 1e9) >
-                                  light_bytes / (hbm * 1e9) else "hbm",
-                                  "achieved": light_ops / lt / 1e9, "peak": alu_peak, "unit": "Gop/s",
-                                  "frac": light_ops / lt / 1e9 / alu_peak, "traffic": None,
-                                  "hbm_frac": light_bytes / lt / 1e9 / hbm},
-                     "clocks": clk, "gpu_launches": 6 * args.steps})
-        if not args.no_cpu_baseline:
-            import oracle
-            t0 = time.perf_counter()
-            key, _ = oracle.raster_bbox(scene, threads=len(os.sched_getaffinity(0)))
-            gn, ga = oracle.shade(scene, key)
-            oracle.light_pass(key, gn, ga, lights.cpu().numpy())
-            dt = time.perf_counter() - t0
-            line["cpu_baseline"] = {"value": scene.num_triangles / dt / 1e6, "unit": UNIT,
-                                    "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-                                    "sample": f"one full frame: bounding-box oracle, float64 G-buffer and light pass, {dt:.2f} s"}
-    elif args.workload == "sphere":
-        # the 64 views as one batch (scenes sharing the mesh, one camera each):
-        # forward_batch, one loss-gradient op over all views, backward_batch
-        # accumulating into the mesh's gradients; replayed from CUDA graphs
-        import dataclasses
-        sph, mvps = S.sphere_views(num_views=64)
-        W = H = 512
-        nv = 64
-        ds = DeviceScene.from_host(sph)
-        mv = torch.from_numpy(mvps).cuda()
-        views = [dataclasses.replace(ds, mvp=mv[v]) for v in range(nv)]
-        tgt = torch.from_numpy(S.target_image(W, H, seed=1240, views=nv)).cuda()
-        key_all = torch.empty((nv, H, W), dtype=torch.int64, device="cuda")
-        rgba_all = torch.empty((nv, H, W, 4), dtype=torch.float32, device="cuda")
-        g_all = torch.empty_like(rgba_all)
-        fbs = [Framebuffer(key_all[v], rgba_all[v]) for v in range(nv)]
-        gviews = [g_all[v] for v in range(nv)]
-        dc = torch.zeros_like(ds.color)
-        dn = torch.zeros_like(ds.normal)
-        dl = torch.zeros_like(ds.light_dir)
-        bins, scheds = [(args.bins, args.bins)] * nv, ["dynamic" if args.schedule == "hardware" else args.schedule] * nv
-        rb = Rasterizer(W, H, args.bins, args.bins)
-        if args.perspective:
-            rb.set_option(L.PIKO_OPT_PERSPECTIVE, 1)
+    def fwd_pass():
         rb.forward_batch(views, fbs, bins, scheds)
-        assert rb.status()[0] == 0
-        rb.set_option(L.PIKO_OPT_CHECK_CAPACITY, 0)
-        covered = int((key_all != -1).sum().item())
 
-        def fwd_pass():
-            rb.forward_batch(views, fbs, bins, scheds)
+    def bwd_pass():
+        dc.zero_(); dn.zero_(); dl.zero_()
+        torch.sub(rgba_all, tgt, out=g_all).mul_(2.0)
+        g_all[..., 3] = 0.0
+        rb.backward_batch(views, fbs, gviews, [dc] * nv, [dn] * nv, [dl] * nv)
 
-        def bwd_pass():
-            dc.zero_(); dn.zero_(); dl.zero_()
-            torch.sub(rgba_all, tgt, out=g_all).mul_(2.0)
-            g_all[..., 3] = 0.0
-            rb.backward_batch(views, fbs, gviews, [dc] * nv, [dn] * nv, [dl] * nv)
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            fwd_pass(); bwd_pass()
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    gf, gb = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gf):
+        fwd_pass()
+    with torch.cuda.graph(gb):
+        bwd_pass()
+    torch.cuda.synchronize()
+    K = args.steps
+    for _ in range(args.warmup):
+        ctx.flush.zero_()
+        gf.replay(); gb.replay()
+    evs = [(ctx.event(), ctx.event(), ctx.event()) for _ in range(K)]
+    torch.cuda.synchronize()
+    m0 = ctx.clocks.mark()
+    for s, f, e in evs:
+        ctx.flush.zero_()
+        s.record(stream)
+        gf.replay()
+        f.record(stream)
+        gb.replay()
+        e.record(stream)
+    torch.cuda.synchronize()
+    clk = ctx.clocks.summary(m0)
+    assert rb.status()[0] == 0
+    fwd = np.array([s.elapsed_time(f) for s, f, _ in evs])
+    bwd = np.array([f.elapsed_time(e) for _, f, e in evs])
+    ms = float((fwd + bwd).mean())
+    T = nv * sph.num_triangles
+    V = sph.num_vertices
+    bw_bytes = nv * W * H * (8 + 16) + V * (16 + 12 * 2) + nv * V * 12 * 2
+    bt = float(bwd.mean()) * 1e-3
+    rec = {"workload": "sphere 99.5k triangles, 64 views 512x512, forward + L2-loss backward (colour, normal, light)",
+           "value": T / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms,
+           "shaded_gfrag_s": covered / (ms * 1e-3) / 1e9,
+           "how": "the 64 views as one forward_batch and one backward_batch (16x16 bins, dynamic), each "
+                  "replayed from a CUDA graph; the backward includes the loss gradient",
+           "forward_ms": float(fwd.mean()), "backward_ms": float(bwd.mean()), "covered_pixels": covered,
+           "roofline": {"kernel": "backward (64 views, incl. loss gradient)", "bound": "hbm",
+                        "achieved": bw_bytes / bt / 1e9, "peak": ctx.hbm, "unit": "GB/s",
+                        "frac": bw_bytes / bt / 1e9 / ctx.hbm, "traffic": None,
+                        "bytes": "24 B per pixel (key, dL/dRGBA) + 40 B per vertex read + 24 B per vertex per view "
+                                 "of gradient updates"},
+           "clocks": clk, "gpu_launches": 2 * K,
+           "parity": "keys bit-exact, colour <= 1e-5, gradients <= 1e-4 rel vs the oracle on every view "
+                     "(tests/test_gpu_full_size.py)"}
+    if not args.no_cpu_baseline:
+        import oracle
+        sv = S.Scene(W, H, sph.pos, sph.tris, color=sph.color, normal=sph.normal, mvp=mvps[0],
+                     light_dir=sph.light_dir, shade_mode=sph.shade_mode)
+        tg0 = tgt[0].cpu().numpy()
 
-        side = torch.cuda.Stream()
-        side.wait_stream(stream)
-        with torch.cuda.stream(side):
-            for _ in range(2):
-                fwd_pass(); bwd_pass()
-        stream.wait_stream(side)
-        torch.cuda.synchronize()
-        gf, gb = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
-        with torch.cuda.graph(gf):
-            fwd_pass()
-        with torch.cuda.graph(gb):
-            bwd_pass()
-        torch.cuda.synchronize()
-
-        def step(m):
-            if m is not None:
-                m["s"] = ev(); m["f"] = ev(); m["e"] = ev()
-                m["s"].record(stream)
-            gf.replay()
-            if m is not None:
-                m["f"].record(stream)
-            gb.replay()
-            if m is not None:
-                m["e"].record(stream)
-
-        mark = clocks.mark()
-        recs = _timed_steps(step, args.steps, args.warmup, flush, stream)
-        clk = clocks.stop(mark)
-        assert rb.status()[0] == 0
-        fwd = np.array([m["s"].elapsed_time(m["f"]) for m in recs])
-        bwd = np.array([m["f"].elapsed_time(m["e"]) for m in recs])
-        ms = float((fwd + bwd).mean())
-        T = nv * sph.num_triangles
-        bw_bytes = nv * W * H * (8 + 16) + sph.num_vertices * (16 + 12 * 2) + nv * sph.num_vertices * 12 * 2
-        bt = float(bwd.mean()) * 1e-3
-        line.update({"value": T / (ms * 1e-3) / 1e6, "ms_per_step": ms, "dtype": "int64+f32",
-                     "config": {"workload": "sphere 99.5k triangles, 64 views 512x512, forward + L2 backward",
-                                "bin": [args.bins, args.bins], "schedule": scheds[0],
-                                "how": "the 64 views as one forward_batch and one backward_batch, each replayed "
-                                       "from a CUDA graph",
-                                "l2": "flushed between steps (256 MiB write)",
-                                **({"attributes": "perspective-correct"} if args.perspective else {})},
-                     "forward_ms": float(fwd.mean()), "backward_ms": float(bwd.mean()),
-                     "covered_pixels": covered,
-                     "roofline": {"kernel": "backward (64 views, incl. loss gradient)", "bound": "hbm",
-                                  "achieved": bw_bytes / bt / 1e9, "peak": hbm, "unit": "GB/s",
-                                  "frac": bw_bytes / bt / 1e9 / hbm, "traffic": None},
-                     "clocks": clk, "gpu_launches": 2})
-        if not args.no_cpu_baseline:
-            import oracle
-            t0 = time.perf_counter()
-            sv = S.Scene(W, H, sph.pos, sph.tris, color=sph.color, normal=sph.normal, mvp=mvps[0],
-                         light_dir=sph.light_dir, shade_mode=sph.shade_mode)
-            key, _ = oracle.raster_bbox(sv, threads=len(os.sched_getaffinity(0)))
-            rgba = oracle.shade(sv, key, perspective=args.perspective)
+        def backward(key, rgba):
             gg = np.zeros((H, W, 4))
-            gg[..., :3] = 2 * (rgba[..., :3] - tgt[0].cpu().numpy()[..., :3])
+            gg[..., :3] = 2 * (rgba[..., :3] - tg0[..., :3])
             oracle.backward(sv, key, gg, perspective=args.perspective)
-            dt = time.perf_counter() - t0
-            line["cpu_baseline"] = {"value": sph.num_triangles / dt / 1e6, "unit": UNIT,
-                                    "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-                                    "sample": f"one view: bounding-box oracle, float64 shading and gradients, {dt:.2f} s"}
-    elif args.workload == "batch":
-        line.update(run_batch(args, clocks))
-    else:
-        raise SystemExit(f"unknown workload {args.workload}")
-    print(json.dumps(line), flush=True)
-    return 0
+        rec["cpu_baseline"] = cpu_baseline(sv, args.config_cpu_seconds, args.perspective, extra=backward,
+                                           single_seconds=2.0,
+                                           what="bounding-box oracle, float64 shading and gradients, one view")
+    rb.close()
+    return rec
 
 
-def run_batch(args, clocks) -> dict:
+def measure_batch(args, ctx) -> dict:
     """256 scenes (1k-200k triangles, 256^2-1024^2): plain per-scene loop of
     forward + backward (16x16 bins, static) against the autotuned batch,
     forward_batch + backward_batch replayed from one CUDA graph."""
@@ -694,8 +987,7 @@ def run_batch(args, clocks) -> dict:
     from paper_1404_6293_gb300.autotune import Autotuner
     from paper_1404_6293_gb300.raster import DeviceScene, Framebuffer, Rasterizer
 
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = ctx.stream
     host = S.scene_batch(args.batch_scenes)
     ds = [DeviceScene.from_host(s) for s in host]
     n = len(ds)
@@ -764,75 +1056,146 @@ def run_batch(args, clocks) -> dict:
     assert rb.status()[0] == 0
     rb.set_option(L.PIKO_OPT_CHECK_CAPACITY, 0)
 
-    def batched_step():
-        dc_b.zero_(); dn_b.zero_(); dl_b.zero_()
+    def batched_fwd():
         rb.forward_batch(ds, fbs_b, bins, scheds)
+
+    def batched_bwd():
+        dc_b.zero_(); dn_b.zero_(); dl_b.zero_()
         torch.sub(rgba_b, target, out=g_all).mul_(2.0)
         g_all[:, 3] = 0.0
         rb.backward_batch(ds, fbs_b, gviews, dcv_b, dnv_b, dlv_b)
 
     for _ in range(2):
-        batched_step()
+        batched_fwd(); batched_bwd()
     torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        batched_step()
+    gf, gb = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gf):
+        batched_fwd()
+    with torch.cuda.graph(gb):
+        batched_bwd()
     torch.cuda.synchronize()
 
-    def timed(fn, K, W):
+    def timed(steps, K, W):
+        """Mean ms of each part of a step (events between the parts)."""
         for _ in range(W):
-            flush.zero_()
-            fn()
+            ctx.flush.zero_()
+            for f in steps:
+                f()
         torch.cuda.synchronize()
-        tot = 0.0
+        tot = [0.0] * len(steps)
         for _ in range(K):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            fn()
-            b.record(stream)
-            b.synchronize()
-            tot += a.elapsed_time(b)
-        return tot / K
+            ctx.flush.zero_()
+            ev = [ctx.event() for _ in range(len(steps) + 1)]
+            ev[0].record(stream)
+            for j, f in enumerate(steps):
+                f()
+                ev[j + 1].record(stream)
+            ev[-1].synchronize()
+            for j in range(len(steps)):
+                tot[j] += ev[j].elapsed_time(ev[j + 1])
+        return [t / K for t in tot]
 
-    mark = clocks.mark()
-    ms_plain = timed(plain_step, args.steps, args.warmup)
-    ms_batch = timed(graph.replay, args.steps, args.warmup)
-    clk = clocks.stop(mark)
+    m0 = ctx.clocks.mark()
+    ms_plain = sum(timed([plain_step], args.steps, args.warmup))
+    m1 = ctx.clocks.mark()
+    f_ms, b_ms = timed([gf.replay, gb.replay], args.steps, args.warmup)
+    ms_batch = f_ms + b_ms
+    clk = ctx.clocks.summary(m1)
+    clk["plain_loop"] = {k: v for k, v in ctx.clocks.summary(m0, m1).items() if k in ("sm_mhz", "samples", "reasons")}
     assert rb.status()[0] == 0
     same_keys = bool(torch.equal(key_p, key_b))
     gdiff = max(float((dc_p - dc_b).abs().max()), float((dn_p - dn_b).abs().max()), float((dl_p - dl_b).abs().max()))
     gscale = max(float(dc_p.abs().max()), float(dn_p.abs().max()), float(dl_p.abs().max()))
+    covered = int((key_b != -1).sum().item())
     n_static = sum(1 for x in scheds if x == "static")
-    return {"value": T / (ms_batch * 1e-3) / 1e6, "ms_per_step": ms_batch, "dtype": "int64+f32",
-            "config": {"workload": f"{n} scenes, 1k-200k triangles, 256^2-1024^2, random + heightfield, "
-                                   "forward + L2 backward", "scenes": n, "triangles": T, "pixels": P,
-                       "l2": "flushed between steps (256 MiB write)"},
-            "plain": {"value": T / (ms_plain * 1e-3) / 1e6, "ms_per_step": ms_plain,
-                      "how": "per-scene piko_raster_forward then piko_raster_backward, 16x16 static"},
-            "batched": {"value": T / (ms_batch * 1e-3) / 1e6, "ms_per_step": ms_batch,
-                        "how": ("forward_batch (one persistent cooperative launch)" if args.batch_launch == "persistent"
-                                else "forward_batch (one launch per phase)") + " + loss gradient + "
-                               "backward_batch, replayed from one CUDA graph",
-                        "autotune_s": tune_s, "static_scenes": n_static,
-                        "bins_used": sorted(set(f"{a}x{b}" for a, b in bins)),
-                        "autotune": {"choice": tune_report["choice"], "classes": tune_report["classes"],
-                                     "per_class_forward_ms": tune_report["per_class_ms"],
-                                     "best_uniform_forward_ms": tune_report["best_uniform_ms"],
-                                     "uniform_forward_ms": {f"{u['bin'][0]}x{u['bin'][1]} {u['schedule']}": u["ms"]
-                                                            for u in tune_report["uniform"]}}},
-            "speedup_batched_over_plain": ms_plain / ms_batch,
-            "parity": {"keys_bit_identical_plain_vs_batched": same_keys, "grad_max_abs_diff": gdiff,
-                       "grad_scale": gscale},
-            "clocks": clk, "gpu_launches": (2 if args.batch_launch == "persistent" else 6) * args.steps,
-            "gpu_launches_plain": 7 * n * args.steps}
+    # must-move bytes of the batched backward: 24 B per pixel (key and dL/dRGBA
+    # read), per vertex 16 B position + 12 B colour + 12 B normal read and two
+    # gradient arrays of 12 B read and written
+    nrm = sum(1 for s in host if s.normal is not None)
+    bw_bytes = P * 24 + VT * (16 + 12 + 12 + 48)
+    rec = {"workload": f"{n} scenes, 1k-200k triangles (log-uniform), 256^2-1024^2, random + heightfield, "
+                       "forward + L2 backward",
+           "value": T / (ms_batch * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms_batch,
+           "scenes": n, "triangles": T, "pixels": P, "scenes_with_normals": nrm,
+           "shaded_gfrag_s": covered / (ms_batch * 1e-3) / 1e9,
+           "plain": {"value": T / (ms_plain * 1e-3) / 1e6, "ms_per_step": ms_plain,
+                     "how": "per-scene piko_raster_forward then piko_raster_backward, 16x16 static"},
+           "batched": {"value": T / (ms_batch * 1e-3) / 1e6, "ms_per_step": ms_batch,
+                       "forward_ms": f_ms, "backward_ms": b_ms,
+                       "how": ("forward_batch (one persistent cooperative launch)" if args.batch_launch ==
+                               "persistent" else "forward_batch (one launch per phase)") + " and loss gradient + "
+                              "backward_batch, each replayed from a CUDA graph",
+                       "autotune_s": tune_s, "static_scenes": n_static,
+                       "bins_used": sorted(set(f"{a}x{b}" for a, b in bins)),
+                       "autotune": {"choice": tune_report["choice"], "classes": tune_report["classes"],
+                                    "per_class_forward_ms": tune_report["per_class_ms"],
+                                    "best_uniform_forward_ms": tune_report["best_uniform_ms"],
+                                    "uniform_forward_ms": {f"{u['bin'][0]}x{u['bin'][1]} {u['schedule']}": u["ms"]
+                                                           for u in tune_report["uniform"]}}},
+           "speedup_batched_over_plain": ms_plain / ms_batch,
+           "roofline": {"kernel": "k_batch_backward (with the loss gradient)", "bound": "hbm",
+                        "achieved": bw_bytes / (b_ms * 1e-3) / 1e9, "peak": ctx.hbm, "unit": "GB/s",
+                        "frac": bw_bytes / (b_ms * 1e-3) / 1e9 / ctx.hbm, "traffic": None,
+                        "algorithmic_bytes": bw_bytes},
+           "parity": {"keys_bit_identical_plain_vs_batched": same_keys, "grad_max_abs_diff": gdiff,
+                      "grad_scale": gscale,
+                      "oracle": "every scene's keys bit-exact and colour <= 1e-5 vs the oracle "
+                                "(tests/test_gpu_full_size.py)"},
+           "clocks": clk, "gpu_launches": (2 if args.batch_launch == "persistent" else 6) * args.steps,
+           "gpu_launches_plain": 7 * n * args.steps}
+    if not args.no_cpu_baseline:
+        import oracle
+        hc = host_cpu()
+        # a bounded sample: whole scenes in order until the time budget is spent
+        t0 = time.perf_counter()
+        done_t = 0
+        k = 0
+        while k < n and time.perf_counter() - t0 < args.config_cpu_seconds:
+            sc = host[k]
+            key, _ = oracle.raster_bbox(sc, threads=hc["cores"])
+            rgba = oracle.shade(sc, key)
+            tg = target[po[k]:po[k + 1]].view(sc.height, sc.width, 4).cpu().numpy()
+            gg = np.zeros((sc.height, sc.width, 4))
+            gg[..., :3] = 2 * (rgba[..., :3] - tg[..., :3])
+            oracle.backward(sc, key, gg)
+            done_t += sc.num_triangles
+            k += 1
+        dt = time.perf_counter() - t0
+        rec["cpu_baseline"] = {"value": done_t / dt / 1e6, "unit": UNIT, "cores": hc["cores"],
+                               "cpu_model": hc["cpu_model"], "kind": "oracle",
+                               "sample": f"the first {k} of {n} scenes ({done_t} triangles): bounding-box oracle, "
+                                         f"float64 shading and gradients on {hc['cores']} threads, {dt:.2f} s"}
+    for h in handles.values():
+        h.close()
+    rb.close()
+    return rec
+
+
+def run_single_workload(args):
+    """One of the other configurations as the line's value (for profiling
+    and sweeps); the default run attaches them all under ``configs``."""
+    import torch
+    torch.cuda.set_device(0)
+    clocks = ClockSampler(0)
+    ctx = Ctx(clocks)
+    fn = {"random256": measure_random256, "deferred": measure_deferred, "sphere": measure_sphere,
+          "batch": measure_batch}[args.workload]
+    rec = fn(args, ctx)
+    clocks.close()
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic",
+            "dtype": "int64+f32", "config": {"workload": rec.pop("workload"),
+                                             "l2": "flushed between steps (256 MiB write)"}}
+    line.update(rec)
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3000)
-    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--bins", type=int, default=16)
     ap.add_argument("--schedule", default="hardware", choices=["static", "dynamic", "hardware"],
@@ -846,25 +1209,32 @@ def main():
     ap.add_argument("--small-px", type=int, default=0,
                     help="largest box (pixels inside a tile) one thread rasterizes; larger boxes take a warp "
                          "(0: library default)")
+    ap.add_argument("--deferred-bins", type=int, default=16)
+    ap.add_argument("--deferred-schedule", default="hardware", choices=["static", "dynamic", "hardware"])
     ap.add_argument("--batch-scenes", type=int, default=256)
     ap.add_argument("--batch-bins", type=int, default=0, help="batch workload: one square bin size for all scenes "
                     "instead of the autotuner's choice (0: autotune)")
     ap.add_argument("--batch-schedule", default="dynamic", choices=["static", "dynamic"])
     ap.add_argument("--batch-launch", default="persistent", choices=["persistent", "per-phase"],
                     help="batch workload: one cooperative launch, or one launch per phase (for launch lists)")
-    ap.add_argument("--workload", default="heightfield", choices=["heightfield", "deferred", "sphere", "batch"],
-                    help="heightfield: the headline line; the others measure further rows of the path")
+    ap.add_argument("--workload", default="heightfield",
+                    choices=["heightfield", "random256", "deferred", "sphere", "batch"],
+                    help="heightfield: the headline line (with every other configuration under 'configs'); "
+                         "the others: that configuration alone as the line")
+    ap.add_argument("--no-configs", action="store_true", help="headline line only (no bin sweep, no other configs)")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-lanes", type=int, default=3, help="handles/streams the end-to-end frames rotate over")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--config-cpu-seconds", type=float, default=4.0,
+                    help="oracle time budget (all cores) of each further configuration's cpu_baseline")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         sys.exit(run_reference(args))
-    sys.exit(run_ours(args) if args.workload == "heightfield" else run_extra(args))
+    sys.exit(run_ours(args) if args.workload == "heightfield" else run_single_workload(args))
 
 
 if __name__ == "__main__":

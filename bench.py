@@ -62,105 +62,120 @@ def measured_peaks() -> dict:
         return {}
 
 
-class _NvmlLib:
-    """Read-only NVML queries through ctypes (libnvidia-ml ships with the
-    driver; no Python package needed)."""
-
-    SM = 1  # NVML_CLOCK_SM
-    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
-               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
-
-    def __init__(self, torch_index: int):
-        import ctypes as C
-        self.C = C
-        lib = C.CDLL("libnvidia-ml.so.1")
-        if lib.nvmlInit_v2() != 0:
-            raise OSError("nvmlInit failed")
-        self.lib = lib
-        self.dev = C.c_void_p()
-        ok = False
-        try:
-            import torch
-            p = torch.cuda.get_device_properties(torch_index)
-            bus = "%08X:%02X:%02X.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
-            ok = lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), C.byref(self.dev)) == 0
-        except Exception:
-            ok = False
-        if not ok and lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(torch_index), C.byref(self.dev)) != 0:
-            raise OSError("no NVML handle for the device")
-        self.get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
-            lib.nvmlDeviceGetCurrentClocksThrottleReasons
-        mx = C.c_uint(0)
-        self.max_mhz = float(mx.value) if lib.nvmlDeviceGetMaxClockInfo(self.dev, self.SM, C.byref(mx)) == 0 else None
-
-    def sample(self):
-        C = self.C
-        mhz, mw, rs = C.c_uint(0), C.c_uint(0), C.c_ulonglong(0)
-        sm = float(mhz.value) if self.lib.nvmlDeviceGetClockInfo(self.dev, self.SM, C.byref(mhz)) == 0 else None
-        pw = mw.value / 1000.0 if self.lib.nvmlDeviceGetPowerUsage(self.dev, C.byref(mw)) == 0 else None
-        reasons = rs.value if self.get_reasons(self.dev, C.byref(rs)) == 0 else 0
-        return sm, pw, reasons
+_NVML_SAMPLER = r"""
+import ctypes as C, sys, time
+index, bus, period, out = int(sys.argv[1]), sys.argv[2], float(sys.argv[3]), sys.argv[4]
+lib = C.CDLL("libnvidia-ml.so.1")
+if lib.nvmlInit_v2() != 0:
+    sys.exit(3)
+dev = C.c_void_p()
+if not (bus and lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), C.byref(dev)) == 0):
+    if lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(index), C.byref(dev)) != 0:
+        sys.exit(4)
+reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or lib.nvmlDeviceGetCurrentClocksThrottleReasons
+mx = C.c_uint(0)
+mxv = mx.value if lib.nvmlDeviceGetMaxClockInfo(dev, 1, C.byref(mx)) == 0 else 0
+mhz, mw, rs = C.c_uint(0), C.c_uint(0), C.c_ulonglong(0)
+with open(out, "w", buffering=1) as f:
+    f.write("max,%d\n" % mxv)
+    while True:
+        sm = mhz.value if lib.nvmlDeviceGetClockInfo(dev, 1, C.byref(mhz)) == 0 else 0
+        pw = mw.value if lib.nvmlDeviceGetPowerUsage(dev, C.byref(mw)) == 0 else 0
+        r = rs.value if reasons_fn(dev, C.byref(rs)) == 0 else 0
+        f.write("%.6f,%d,%d,%d\n" % (time.monotonic(), sm, pw, r))
+        time.sleep(period)
+"""
 
 
 class ClockSampler:
     """SM clock, power and clock-event reasons sampled during the timed
-    regions.  NVML is polled in-process every ``period_ms`` on a background
-    thread (read-only queries), so that even a timed loop of a few
-    milliseconds gets samples; nvidia-smi (100 ms) is the fallback when NVML
-    cannot be loaded.  ``mark()`` returns a sample index; ``summary(a, b)``
-    summarises the samples taken between two marks."""
+    regions.  A child process polls NVML (read-only queries through ctypes;
+    libnvidia-ml ships with the driver) every ``period_ms`` and stamps each
+    sample with the system monotonic clock, so that even a timed loop of a
+    few milliseconds gets samples and the sampling takes no time from this
+    process; nvidia-smi (100 ms) is the fallback when NVML cannot be loaded.
+    ``mark()`` returns a time; ``summary(a, b)`` summarises the samples taken
+    between two marks."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
     def __init__(self, index: int, period_ms: float = 0.5):
-        import threading
-        self.rows = []  # (t, sm_mhz, power_w, reasons set)
-        self.max_mhz = None
         self.source = "nvml"
-        self._stop = threading.Event()
-        self._thread = None
+        self._smi = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.out.close()
+        bus = ""
         try:
-            nv = _NvmlLib(index)
-            self.max_mhz = nv.max_mhz
-
-            def loop():
-                while not self._stop.is_set():
-                    sm, pw, rs = nv.sample()
-                    self.rows.append((time.perf_counter(), sm, pw,
-                                      {name for bit, name in nv.REASONS.items() if rs & bit}))
-                    time.sleep(period_ms * 1e-3)
-
-            self._thread = threading.Thread(target=loop, daemon=True)
-            self._thread.start()
-        except OSError:
+            import torch
+            p = torch.cuda.get_device_properties(index)
+            bus = "%08X:%02X:%02X.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+        except Exception:
+            bus = ""
+        self.proc = subprocess.Popen([sys.executable, "-c", _NVML_SAMPLER, str(index), bus, str(period_ms * 1e-3),
+                                      self.out.name], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        # wait for the first sample (or for the child to give up)
+        t0 = time.monotonic()
+        while time.monotonic() - t0 < 10.0:
+            if self.proc.poll() is not None or len(self._rows()[1]) > 0:
+                break
+            time.sleep(0.01)
+        if not self._rows()[1]:
+            self._kill()
             self.source = "nvidia-smi"
             self._smi = _SmiSampler(index)
 
-    def mark(self) -> int:
-        if self._thread is None:
-            return self._smi.mark()
-        return len(self.rows)
+    def _rows(self):
+        mx, rows = None, []
+        try:
+            for ln in open(self.out.name):
+                parts = ln.strip().split(",")
+                if parts[0] == "max" and len(parts) == 2:
+                    mx = float(parts[1]) or None
+                elif len(parts) == 4:
+                    rows.append((float(parts[0]), float(parts[1]), float(parts[2]) / 1000.0, int(parts[3])))
+        except (OSError, ValueError):
+            pass
+        return mx, rows
 
-    def summary(self, begin: int, end: int | None = None) -> dict:
-        if self._thread is None:
+    def mark(self):
+        if self._smi is not None:
+            return self._smi.mark()
+        return time.monotonic()
+
+    def summary(self, begin, end=None) -> dict:
+        if self._smi is not None:
             return self._smi.summary(begin, end)
-        rows = self.rows[begin:end]
-        sm = [r[1] for r in rows if r[1]]
-        pw = [r[2] for r in rows if r[2] is not None]
-        reasons = sorted(set().union(*[r[3] for r in rows])) if rows else []
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.max_mhz,
+        mx, rows = self._rows()
+        rows = [r for r in rows if r[0] >= begin and (end is None or r[0] <= end)]
+        sm = [r[1] for r in rows if r[1] > 0]
+        pw = [r[2] for r in rows if r[2] > 0]
+        reasons = sorted({name for r in rows for bit, name in self.REASONS.items() if r[3] & bit})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
                 "sm_mhz_min": min(sm) if sm else None, "reasons": reasons, "samples": len(rows),
                 "power_w_max": max(pw) if pw else None, "source": self.source}
 
-    def stop(self, first_line: int = 0) -> dict:
+    def stop(self, first_line=0) -> dict:
         out = self.summary(first_line)
         self.close()
         return out
 
+    def _kill(self):
+        if self.proc is not None and self.proc.poll() is None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
     def close(self):
-        if self._thread is not None:
-            self._stop.set()
-            self._thread.join(timeout=2)
-        elif getattr(self, "_smi", None) is not None:
+        self._kill()
+        if self._smi is not None:
             self._smi.close()
+        try:
+            os.unlink(self.out.name)
+        except OSError:
+            pass
 
 
 class _SmiSampler:
@@ -592,6 +607,7 @@ def run_ours(args):
                          enumerate(["vertex", "setup_count", "scan", "scatter", "process"])},
             "work": {**stats, "covered_pixels": covered},
             "wall_ms_incl_flush": 1e3 * wall / K,
+            "step_ms_min": float(np.min(step_ms)), "step_ms_median": float(np.median(step_ms)),
             "roofline": roof, "clocks": clk, "e2e": e2e,
             "gpu_launches": 5 * K,
             "parity": "depth/ID bit-exact vs the CPU oracle on this workload under every schedule "

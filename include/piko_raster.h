@@ -92,6 +92,18 @@ extern "C" {
                                        scene of a batch; piko_raster_backward_batch follows
                                        the setting of the last piko_raster_forward_batch,
                                        piko_raster_backward the handle's current setting  */
+#define PIKO_OPT_WAIT_BUDGET 9      /* how long a device-side wait (scan look-back, batch grid
+                                       barrier) may spin before it gives up, records
+                                       PIKO_ERR_TIMEOUT and lets the frame's later phases
+                                       skip their work: value x 1000 SM clock cycles,
+                                       1..1000000 (default 40000, about 20 ms)              */
+#define PIKO_OPT_TEST_WITHHOLD 10   /* test hook for the bounded waits; faults nothing.
+                                       Bit 0: scan chunk 0 does not publish its prefix, so
+                                       chunk 1's look-back runs out (needs more than 2048
+                                       tiles).  Bit 1: in a persistent batch, CTA 0 does not
+                                       arrive at the first grid barrier, so every CTA's wait
+                                       runs out.  The frame then reports PIKO_ERR_TIMEOUT
+                                       and writes no output.  Default 0                    */
 
 /* Stage boundaries of one forward pass, for piko_raster_set_stage_events. */
 #define PIKO_NUM_STAGE_EVENTS 6 /* before vertex, after vertex, after setup+count, after scan,

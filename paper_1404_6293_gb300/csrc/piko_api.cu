@@ -13,7 +13,8 @@ void batch_state_free(BatchState* bs);
 int batch_prepare(BatchState*& bs, int num_sms, const piko_scene* scenes, int n, piko_framebuffer* fbs,
                   const int32_t* bin_sizes, const int32_t* schedules, int default_bin_w, int default_bin_h,
                   int default_schedule, int unclamped, int persp, cudaStream_t stream, std::string& err);
-int batch_launch_forward(BatchState* bs, DevStatus* st, bool persistent, cudaStream_t stream, std::string& err);
+int batch_launch_forward(BatchState* bs, DevStatus* st, bool persistent, cudaStream_t stream, std::string& err,
+                         long long wait_budget, int withhold);
 long long batch_capacity(const BatchState* bs);
 void batch_note_entries(BatchState* bs, long long entries);
 int batch_grow_entries(BatchState* bs, long long need, std::string& err);
@@ -38,6 +39,8 @@ struct piko_raster {
   int small_px = 32;
   int stats = 0;
   int batch_launch = 0;  // 0 persistent cooperative, 1 one launch per phase
+  long long wait_budget = 40000000;  // clock cycles a device-side wait may take (PIKO_OPT_WAIT_BUDGET)
+  int withhold = 0;                  // test hooks (PIKO_OPT_TEST_WITHHOLD)
   BatchState* batch = nullptr;
   cudaEvent_t stage_ev[PIKO_NUM_STAGE_EVENTS] = {};
   bool use_stage_ev = false;
@@ -205,6 +208,14 @@ int piko_raster_set_option(piko_raster* h, int key, int value) {
       if (value != 0 && value != 1) return fail(h, PIKO_ERR_INVALID_ARG, "perspective must be 0 or 1");
       h->perspective = value;
       return PIKO_OK;
+    case PIKO_OPT_WAIT_BUDGET:
+      if (value < 1 || value > 1000000) return fail(h, PIKO_ERR_INVALID_ARG, "wait budget must be 1..1000000 kcycles");
+      h->wait_budget = (long long)value * 1000;
+      return PIKO_OK;
+    case PIKO_OPT_TEST_WITHHOLD:
+      if (value < 0 || value > 3) return fail(h, PIKO_ERR_INVALID_ARG, "withhold must be 0..3");
+      h->withhold = value;
+      return PIKO_OK;
     case PIKO_OPT_SMALL_TRI_PIXELS:
       if (value < 0 || value > 4096) return fail(h, PIKO_ERR_INVALID_ARG, "small-triangle pixels out of range");
       h->small_px = value;
@@ -300,7 +311,7 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
     launch_setup_count(h->g, T, s->tris, V, h->vtx, h->rect, h->bin_count, h->status, h->stats, h->num_sms, st);
     if (ev) cudaEventRecord(h->stage_ev[2], st);
     launch_scan(h->nbins, h->bin_count, h->bin_off, h->cursor, (unsigned long long)h->ecap, h->status,
-                h->chunk_state, ++h->scan_epoch, st);
+                h->chunk_state, ++h->scan_epoch, st, h->wait_budget, h->withhold);
     if (ev) cudaEventRecord(h->stage_ev[3], st);
     if (!h->check_capacity) break;
     cudaError_t e = cudaMemcpyAsync(h->h_needed, &h->status->needed, sizeof(unsigned long long),
@@ -369,7 +380,9 @@ int piko_raster_forward_batch(piko_raster* h, const piko_scene* scenes, int n, p
                         h->unclamped, h->perspective, st, h->err);
   if (r != PIKO_OK) return r;
   for (int attempt = 0;; ++attempt) {
-    if ((r = batch_launch_forward(h->batch, h->status, h->batch_launch == 0, st, h->err)) != PIKO_OK) return r;
+    if ((r = batch_launch_forward(h->batch, h->status, h->batch_launch == 0, st, h->err, h->wait_budget,
+                                  h->withhold)) != PIKO_OK)
+      return r;
     if (!h->check_capacity) return PIKO_OK;
     cudaError_t e = cudaMemcpyAsync(h->h_needed, &h->status->needed, sizeof(unsigned long long),
                                     cudaMemcpyDeviceToHost, st);

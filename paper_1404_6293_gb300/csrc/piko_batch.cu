@@ -80,6 +80,8 @@ struct BatchParams {
   int phases;      // PH_* to run in this launch
   int persistent;  // grid barriers between phases
   int max_bin_px;
+  long long wait_budget;  // clock cycles a device-side wait may take before PIKO_ERR_TIMEOUT
+  int withhold;           // test hooks: TEST_WITHHOLD_* bits (piko_scan.cuh)
 };
 
 // largest s with prefix[s] <= i (prefix[n] > i)
@@ -109,20 +111,22 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
 // Grid barrier of a co-resident grid.  Returns false (for every thread of
 // the CTA) when the frame must stop: a wait ran out of its budget or an
 // earlier phase recorded a condition that makes later phases unsafe.
-__device__ bool grid_barrier(BatchSync* sync, DevStatus* st) {
+// skip_arrival (a test hook) makes this CTA wait without arriving, so that
+// every CTA's wait runs out.
+__device__ bool grid_barrier(BatchSync* sync, DevStatus* st, long long budget, bool skip_arrival = false) {
   __shared__ int s_go;
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned gen = ld_acquire_u32(&sync->gen);
     __threadfence();
-    if (atomicAdd(&sync->count, 1u) == gridDim.x - 1) {
+    if (!skip_arrival && atomicAdd(&sync->count, 1u) == gridDim.x - 1) {
       sync->count = 0u;
       __threadfence();
       st_release_u32(&sync->gen, gen + 1u);
     } else {
       const long long t0 = clock64();
       while (ld_acquire_u32(&sync->gen) == gen) {
-        if (clock64() - t0 > WAIT_BUDGET_CYCLES) {
+        if (clock64() - t0 > budget) {
           record_error(st, PIKO_ERR_TIMEOUT);
           break;
         }
@@ -283,7 +287,7 @@ __device__ void phase_scan(const BatchParams& b, ScanSmem& sm) {
     const int chunk = sm.chunk;
     if (chunk < 0 || chunk >= nchunks) break;
     scan_chunk(chunk, nchunks, b.total_bins, b.cnt, b.bin_off, b.cursor, b.capacity, b.st, b.chunk_state, b.epoch,
-               sm, &b.sync->dyn_head);
+               sm, &b.sync->dyn_head, b.wait_budget, b.withhold);
     __syncthreads();  // sm.chunk is rewritten for the next ticket
   }
 }
@@ -422,21 +426,22 @@ __global__ void __maxnreg__(PIKO_BATCH_MAXNREG) k_batch_forward(BatchParams b) {
   if (cta_should_stop(b.st)) return;
   if (b.phases & PH_VERTEX) {
     phase_vertex<PERSP>(b);
-    if (b.persistent && !grid_barrier(b.sync, b.st)) return;
+    const bool skip = (b.withhold & TEST_WITHHOLD_BARRIER) && blockIdx.x == 0;
+    if (b.persistent && !grid_barrier(b.sync, b.st, b.wait_budget, skip)) return;
   }
   if (b.phases & PH_COUNT) {
     if (blockIdx.x == 0 && threadIdx.x == 0) b.st->scan_ticket = 0u;  // the scan runs after a barrier
     phase_count(b);
-    if (b.persistent && !grid_barrier(b.sync, b.st)) return;
+    if (b.persistent && !grid_barrier(b.sync, b.st, b.wait_budget)) return;
   }
   if (b.phases & PH_SCAN) {
     phase_scan(b, scan_sm);
-    if (b.persistent && !grid_barrier(b.sync, b.st)) return;
+    if (b.persistent && !grid_barrier(b.sync, b.st, b.wait_budget)) return;
   }
   if (b.phases & PH_SCATTER) {
     if (cta_should_stop(b.st)) return;
     phase_scatter(b);
-    if (b.persistent && !grid_barrier(b.sync, b.st)) return;
+    if (b.persistent && !grid_barrier(b.sync, b.st, b.wait_budget)) return;
   }
   if (b.phases & PH_PROCESS) {
     if (cta_should_stop(b.st)) return;
@@ -757,9 +762,12 @@ int batch_prepare(BatchState*& bs, int num_sms, const piko_scene* scenes, int n,
 }
 
 // Launches the forward phases; persistent = one cooperative launch.
-int batch_launch_forward(BatchState* bs, DevStatus* st, bool persistent, cudaStream_t stream, std::string& err) {
+int batch_launch_forward(BatchState* bs, DevStatus* st, bool persistent, cudaStream_t stream, std::string& err,
+                         long long wait_budget, int withhold) {
   BatchParams b = bs->params;
   b.st = st;
+  b.wait_budget = wait_budget;
+  b.withhold = withhold;
   b.capacity = (unsigned long long)bs->ecap;
   b.bin_tris = bs->bin_tris;
   b.epoch = ++bs->epoch;

@@ -132,7 +132,8 @@ constexpr int SCAN_CHUNK = SCAN_THREADS * SCAN_PER;
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan(int nbins, unsigned* __restrict__ cnt,
                                                        unsigned* __restrict__ bin_off, unsigned* __restrict__ cursor,
                                                        unsigned long long capacity, DevStatus* st,
-                                                       unsigned long long* __restrict__ chunk_state, unsigned epoch) {
+                                                       unsigned long long* __restrict__ chunk_state, unsigned epoch,
+                                                       long long wait_budget, int withhold) {
   __shared__ ScanSmem sm;
   pdl_wait();  // counts and the ticket reset of the count pass
   pdl_launch_dependents();
@@ -141,7 +142,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(int nbins, unsigned* __re
   const int chunk = sm.chunk;
   const int nchunks = (nbins + SCAN_CHUNK - 1) / SCAN_CHUNK;
   if (chunk >= nchunks) return;  // only with a corrupted ticket; the count pass resets it every frame
-  scan_chunk(chunk, nchunks, nbins, cnt, bin_off, cursor, capacity, st, chunk_state, epoch, sm, &st->queue_head);
+  scan_chunk(chunk, nchunks, nbins, cnt, bin_off, cursor, capacity, st, chunk_state, epoch, sm, &st->queue_head,
+             wait_budget, withhold);
   // one CTA per chunk: every ticket was taken before the last chunk's
   // look-back ended, so the last chunk may reset the ticket
   if (chunk == nchunks - 1 && threadIdx.x == 0) st->scan_ticket = 0u;
@@ -278,9 +280,10 @@ void launch_setup_count(const RasterGeom& g, int T, const int* tris, int V, cons
 }
 
 void launch_scan(int nbins, unsigned* bin_count, unsigned* bin_off, unsigned* cursor, unsigned long long capacity,
-                 DevStatus* st, unsigned long long* chunk_state, unsigned epoch, cudaStream_t s) {
+                 DevStatus* st, unsigned long long* chunk_state, unsigned epoch, cudaStream_t s, long long wait_budget,
+                 int withhold) {
   launch_pdl(k_scan, scan_chunks(nbins), SCAN_THREADS, 0, s, nbins, bin_count, bin_off, cursor, capacity, st,
-             chunk_state, epoch);
+             chunk_state, epoch, wait_budget, withhold);
 }
 
 // ======================================================================

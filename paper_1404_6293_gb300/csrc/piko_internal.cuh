@@ -266,9 +266,12 @@ void launch_vertex(int W, int H, int V, const float* pos, const float* mvp, int4
 void launch_setup_count(const RasterGeom& g, int T, const int* tris, int V, const int4* vtx,
                         BinRect* rect, unsigned* bin_count, DevStatus* st, int stats, int num_sms, cudaStream_t s);
 // chunk_state: scan_chunks(nbins) words, zero at allocation; epoch must
-// differ between consecutive scans on the same state array.
+// differ between consecutive scans on the same state array.  wait_budget:
+// clock cycles a look-back wait may take before PIKO_ERR_TIMEOUT; withhold:
+// test hook bits (piko_scan.cuh).
 void launch_scan(int nbins, unsigned* bin_count, unsigned* bin_off, unsigned* cursor, unsigned long long capacity,
-                 DevStatus* st, unsigned long long* chunk_state, unsigned epoch, cudaStream_t s);
+                 DevStatus* st, unsigned long long* chunk_state, unsigned epoch, cudaStream_t s,
+                 long long wait_budget = 40000000, int withhold = 0);
 int scan_chunks(int nbins);
 void launch_scatter(const RasterGeom& g, int T, const BinRect* rect, const unsigned* bin_off, unsigned* cursor,
                     unsigned* bin_tris, unsigned long long capacity, DevStatus* st, int num_sms, cudaStream_t s);

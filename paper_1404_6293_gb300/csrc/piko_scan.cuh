@@ -9,8 +9,11 @@
 //   bits 63..62 kind (1 aggregate, 2 inclusive prefix), 61..46 epoch, 45..0 value.
 // off[b] = entries of all earlier bins; the scatter cursor of a bin starts
 // after its single-bin part; both count arrays are zeroed for the next frame.
-// A look-back wait is bounded by a clock budget; on expiry the scan records
-// PIKO_ERR_TIMEOUT and the frame's later stages skip their work.
+// A look-back wait is bounded by a clock budget (wait_budget cycles, by
+// default WAIT_BUDGET_CYCLES); on expiry the scan records PIKO_ERR_TIMEOUT
+// and the frame's later stages skip their work.  TEST_WITHHOLD_SCAN in
+// `withhold` makes chunk 0 keep its state unpublished, so that the next
+// chunk's wait runs out: a test of that path, which faults nothing.
 #pragma once
 
 #include "piko_internal.cuh"
@@ -21,6 +24,9 @@ constexpr int SCAN_PER = 8;
 constexpr unsigned long long SCAN_KIND_AGG = 1ull << 62, SCAN_KIND_PREFIX = 2ull << 62;
 constexpr unsigned long long SCAN_VALUE_MASK = (1ull << 46) - 1ull;
 constexpr long long WAIT_BUDGET_CYCLES = 40000000;  // ~20 ms at 2 GHz
+// test hooks (bits of the `withhold` argument)
+constexpr int TEST_WITHHOLD_SCAN = 1;     // scan chunk 0 does not publish its state
+constexpr int TEST_WITHHOLD_BARRIER = 2;  // batch CTA 0 does not arrive at the first grid barrier
 
 struct ScanSmem {
   unsigned long long warp_sums[32];
@@ -54,7 +60,8 @@ __device__ __forceinline__ void scan_chunk(int chunk, int nchunks, int nbins, un
                                            unsigned* __restrict__ bin_off, unsigned* __restrict__ cursor,
                                            unsigned long long capacity, DevStatus* st,
                                            unsigned long long* __restrict__ chunk_state, unsigned epoch, ScanSmem& sm,
-                                           unsigned* queue_to_reset) {
+                                           unsigned* queue_to_reset, long long wait_budget = WAIT_BUDGET_CYCLES,
+                                           int withhold = 0) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
   const unsigned long long tag = (unsigned long long)(epoch & 0xFFFFu) << 46;
   unsigned* __restrict__ multi = cnt + nbins;
@@ -88,7 +95,7 @@ __device__ __forceinline__ void scan_chunk(int chunk, int nchunks, int nbins, un
   if (tid == 0) {
     unsigned long long excl = 0;
     if (chunk == 0) {
-      st_release_u64(chunk_state, SCAN_KIND_PREFIX | tag | (agg & SCAN_VALUE_MASK));
+      if (!(withhold & TEST_WITHHOLD_SCAN)) st_release_u64(chunk_state, SCAN_KIND_PREFIX | tag | (agg & SCAN_VALUE_MASK));
     } else {
       st_release_u64(chunk_state + chunk, SCAN_KIND_AGG | tag | (agg & SCAN_VALUE_MASK));
       const long long t0 = clock64();
@@ -97,7 +104,7 @@ __device__ __forceinline__ void scan_chunk(int chunk, int nchunks, int nbins, un
         const unsigned long long sv = ld_acquire_u64(chunk_state + j);
         const unsigned long long sv_epoch = sv & ~SCAN_VALUE_MASK & ~(3ull << 62);
         if (sv_epoch != tag || (sv >> 62) == 0) {
-          if (clock64() - t0 > WAIT_BUDGET_CYCLES) timed_out = true;
+          if (clock64() - t0 > wait_budget) timed_out = true;
           else __nanosleep(64);
           continue;  // predecessor not published for this frame yet
         }

@@ -93,8 +93,8 @@ __global__ void __launch_bounds__(PIX_THREADS) k_backward_pixel(PixelBwdParams p
       const long long w0 = (long long)(s.X2 - s.X1) * (Py - s.Y1) - (long long)(s.Y2 - s.Y1) * (Px - s.X1);
       const long long w1 = (long long)(s.X0 - s.X2) * (Py - s.Y2) - (long long)(s.Y0 - s.Y2) * (Px - s.X2);
       const long long w2 = (long long)(s.X1 - s.X0) * (Py - s.Y0) - (long long)(s.Y1 - s.Y0) * (Px - s.X0);
-      const float fA = (float)s.A;
-      float b[3] = {__fdiv_rn((float)w0, fA), __fdiv_rn((float)w1, fA), __fdiv_rn((float)w2, fA)};
+      const float fA = f32_from_i64(s.A);
+      float b[3] = {__fdiv_rn(f32_from_i64(w0), fA), __fdiv_rn(f32_from_i64(w1), fA), __fdiv_rn(f32_from_i64(w2), fA)};
       if (PERSP)
         perspective_bary(b[0], b[1], b[2], __ldg(p.invw + vid[0]), __ldg(p.invw + vid[1]), __ldg(p.invw + vid[2]));
       const float4 g = __ldg(p.dl_drgba + i);

@@ -193,7 +193,7 @@ __device__ __forceinline__ void backward_tile(const BwdScene& sc, int x0, int y0
       r[RB_V] = ts.v0; r[RB_V + 1] = ts.v1; r[RB_V + 2] = ts.v2;
       r[RB_ALO] = (int)(unsigned)(ts.A & 0xFFFFFFFFll);
       r[RB_AHI] = (int)(ts.A >> 32);
-      r[RB_T] = __float_as_int(__frcp_rn((float)ts.A));
+      r[RB_T] = __float_as_int(__frcp_rn(f32_from_i64(ts.A)));
       if (sc.mode == PIKO_SHADE_LAMBERT) {
         const int vid[3] = {ts.v0, ts.v1, ts.v2};
 #pragma unroll
@@ -223,12 +223,21 @@ __device__ __forceinline__ void backward_tile(const BwdScene& sc, int x0, int y0
     const int X0 = r[0], Y0 = r[1], X1 = r[2], Y1 = r[3], X2 = r[4], Y2 = r[5];
     const long long A = (long long)(((unsigned long long)(unsigned)r[RB_AHI] << 32) | (unsigned)r[RB_ALO]);
     const int vid[3] = {r[RB_V], r[RB_V + 1], r[RB_V + 2]};
-    const long long Px = 256LL * x + 128, Py = 256LL * y + 128;
-    const long long w1 = (long long)(X0 - X2) * (Py - Y2) - (long long)(Y0 - Y2) * (Px - X2);
-    const long long w2 = (long long)(X1 - X0) * (Py - Y0) - (long long)(Y1 - Y0) * (Px - X0);
-    const long long w0 = A - w1 - w2;  // the three edge functions sum to A
     const float rA = __int_as_float(r[RB_T]);
-    float b[3] = {(float)w0 * rA, (float)w1 * rA, (float)w2 * rA};
+    float b[3];
+    if (A < (1LL << 31)) {
+      // the pixel is covered: its edge functions lie in [0, A], exact in wrapping 32-bit arithmetic
+      const int Px = 256 * x + 128, Py = 256 * y + 128;
+      const int w1 = edge_fn_wrap32(X2, Y2, X0, Y0, Px, Py), w2 = edge_fn_wrap32(X0, Y0, X1, Y1, Px, Py);
+      const int w0 = (int)A - w1 - w2;  // the three edge functions sum to A
+      b[0] = (float)w0 * rA; b[1] = (float)w1 * rA; b[2] = (float)w2 * rA;
+    } else {
+      const long long Px = 256LL * x + 128, Py = 256LL * y + 128;
+      const long long w1 = (long long)(X0 - X2) * (Py - Y2) - (long long)(Y0 - Y2) * (Px - X2);
+      const long long w2 = (long long)(X1 - X0) * (Py - Y0) - (long long)(Y1 - Y0) * (Px - X0);
+      const long long w0 = A - w1 - w2;
+      b[0] = f32_from_i64(w0) * rA; b[1] = f32_from_i64(w1) * rA; b[2] = f32_from_i64(w2) * rA;
+    }
     if (PERSP)
       perspective_bary(b[0], b[1], b[2], __ldg(sc.invw + vid[0]), __ldg(sc.invw + vid[1]), __ldg(sc.invw + vid[2]));
     const float4 g = __ldg(sc.dl + o);

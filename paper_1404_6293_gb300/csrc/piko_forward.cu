@@ -79,36 +79,9 @@ __device__ __forceinline__ int3 load_tri(const int* __restrict__ tris, int T, in
 // Warp-wide expansion of (triangle, bin) pairs for triangles spanning more
 // than one bin: lane j owns nb_j pairs; the warp walks all of them 32 at a
 // time, each lane finding the owner of its pair by a binary search over the
-// inclusive prefix of nb held across the lanes.
+// inclusive prefix of nb held across the lanes (warp_prefix / pair_owner in
+// piko_internal.cuh).
 // ======================================================================
-struct MultiSpan {
-  int incl, total;
-};
-
-__device__ __forceinline__ MultiSpan warp_prefix(int nb, int lane) {
-  int incl = nb;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int u = __shfl_up_sync(FULL_MASK, incl, o);
-    if (lane >= o) incl += u;
-  }
-  MultiSpan m;
-  m.incl = incl;
-  m.total = __shfl_sync(FULL_MASK, incl, 31);
-  return m;
-}
-
-// owner = the smallest lane whose inclusive prefix exceeds k (k < total)
-__device__ __forceinline__ int pair_owner(int incl, int k) {
-  int owner = 0;
-#pragma unroll
-  for (int s = 16; s > 0; s >>= 1) {
-    const int v = __shfl_sync(FULL_MASK, incl, owner + s - 1);
-    if (v <= k) owner += s;
-  }
-  return owner;
-}
-
 // Bin of pair k of the owner lane's rectangle (x0, y0, width bw; first pair
 // index first).
 __device__ __forceinline__ int pair_bin(const RasterGeom& g, int k, int first, int x0, int y0, int bw) {

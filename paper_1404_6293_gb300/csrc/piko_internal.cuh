@@ -78,6 +78,38 @@ __device__ __forceinline__ void record_error(DevStatus* st, unsigned code) {
   atomicOr(&st->flags, 1u << code);
 }
 
+// ------------------------------------------------------------- warp spans
+// Lane j owns nb_j consecutive items of a warp-wide sequence: the inclusive
+// prefix of nb over the lanes, and the total.
+struct MultiSpan {
+  int incl, total;
+};
+
+__device__ __forceinline__ MultiSpan warp_prefix(int nb, int lane) {
+  int incl = nb;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(FULL_MASK, incl, o);
+    if (lane >= o) incl += u;
+  }
+  MultiSpan m;
+  m.incl = incl;
+  m.total = __shfl_sync(FULL_MASK, incl, 31);
+  return m;
+}
+
+// owner of item k (k < total) = the smallest lane whose inclusive prefix
+// exceeds k: a binary search over the lanes' prefixes (called by all lanes)
+__device__ __forceinline__ int pair_owner(int incl, int k) {
+  int owner = 0;
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    const int v = __shfl_sync(FULL_MASK, incl, owner + s - 1);
+    if (v <= k) owner += s;
+  }
+  return owner;
+}
+
 // ------------------------------------------------------------------ setup
 // Triangle after snapping and orientation: slots 0..2 with A > 0.
 struct TriSetup {
@@ -120,6 +152,25 @@ __device__ __forceinline__ void centre_range(int vmin, int vmax, int lo, int hi,
 // Edge a->b top-left test in the A > 0, y-down orientation.
 __device__ __forceinline__ int top_left(int dx, int dy) { return (dy < 0 || (dy == 0 && dx > 0)) ? 1 : 0; }
 
+// int64 -> float32 on the integer and FP32 pipes.  A plain (float) of a
+// 64-bit integer (and a float -> int64 conversion) runs on the FP64 pipe,
+// which issues at a small fraction of the FP32 rate on this GPU; the helper
+// converts the magnitude's two 32-bit words instead.  Correctly rounded for
+// |v| < 2^32 (one rounding); within 2 ulp above that.
+__device__ __forceinline__ float f32_from_i64(long long v) {
+  const unsigned long long m = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  const float f = __fmaf_rn((float)(unsigned)(m >> 32), 4294967296.0f, (float)(unsigned)(m & 0xFFFFFFFFull));
+  return v < 0 ? -f : f;
+}
+
+// Edge function of a pixel centre P for edge (a -> b): (Xb - Xa)(Py - Ya) -
+// (Yb - Ya)(Px - Xa).  The wrapping 32-bit form is exact whenever the true
+// value lies in [-2^31, 2^31), e.g. for a pixel the triangle covers when its
+// doubled area A is below 2^31 (then the value lies in [0, A]).
+__device__ __forceinline__ int edge_fn_wrap32(int Xa, int Ya, int Xb, int Yb, int Px, int Py) {
+  return (int)((unsigned)(Xb - Xa) * (unsigned)(Py - Ya) - (unsigned)(Yb - Ya) * (unsigned)(Px - Xa));
+}
+
 // floor(n / A) for A > 0 and |n / A| < 2^25, exact.  The float estimate
 // (relative error below 2^-21) is within a few units of the quotient; the
 // integer remainder then moves it to the unique q with 0 <= n - q*A < A.
@@ -128,7 +179,7 @@ __device__ __forceinline__ int top_left(int dx, int dy) { return (dy < 0 || (dy 
 constexpr int DIV_FIX_LIMIT = 64;
 
 __device__ __forceinline__ long long floor_div_est(long long n, long long A, float rA) {
-  long long q = (long long)floorf(__fmul_rn((float)n, rA));
+  long long q = (long long)__float2int_rd(__fmul_rn(f32_from_i64(n), rA));
   long long r = n - q * A;
   for (int it = 0; r < 0 && it < DIV_FIX_LIMIT; ++it) { --q; r += A; }
   for (int it = 0; r >= A && it < DIV_FIX_LIMIT; ++it) { ++q; r -= A; }
@@ -138,8 +189,8 @@ __device__ __forceinline__ long long floor_div_est(long long n, long long A, flo
 // Same for a 128-bit numerator (huge triangles, A >= 2^38).  The estimate
 // comes from the top bits of n; the remainder is kept in 128 bits.
 __device__ __forceinline__ long long floor_div_est128(__int128 n, long long A, float rA) {
-  const float nf = (float)(long long)(n >> 32) * 4294967296.0f + (float)(unsigned)(n & 0xFFFFFFFFu);
-  long long q = (long long)floorf(nf * rA);
+  const float nf = f32_from_i64((long long)(n >> 32)) * 4294967296.0f + (float)(unsigned)(n & 0xFFFFFFFFu);
+  long long q = (long long)__float2int_rd(nf * rA);
   __int128 r = n - (__int128)q * A;
   for (int it = 0; r < 0 && it < DIV_FIX_LIMIT; ++it) { --q; r += A; }
   for (int it = 0; r >= A && it < DIV_FIX_LIMIT; ++it) { ++q; r -= A; }
@@ -277,6 +328,11 @@ void launch_scatter(const RasterGeom& g, int T, const BinRect* rect, const unsig
                     unsigned* bin_tris, unsigned long long capacity, DevStatus* st, int num_sms, cudaStream_t s);
 cudaError_t launch_process(const ProcessParams& p, int threads, int grid, cudaStream_t s);
 cudaError_t process_occupancy(const ProcessParams& p, int threads, int* blocks_per_sm);
+
+// Boxes (pixels of a triangle's bounding box inside a tile) up to this size
+// take the warp's flattened walk when the triangle is below 128 pixels a
+// side; larger boxes, and larger triangles, a whole warp per triangle.
+constexpr int DEFAULT_SMALL_PX = 4096;
 
 // Default CTA size of the Process stage for a tile of bin_px pixels.
 inline int default_process_threads(int bin_px) { return bin_px <= 64 ? 64 : (bin_px <= 256 ? 128 : 256); }

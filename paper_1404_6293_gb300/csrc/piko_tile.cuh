@@ -184,7 +184,7 @@ __device__ __forceinline__ unsigned raster_thread_body(const TriSetup& s, unsign
                                                        int py0, int py1, int x0, int y0, int bshift_x,
                                                        unsigned long long* skey) {
   const Edges<I> e = make_edges<I>(s, px0, py0);
-  const float rA = approx_rcp((float)s.A);
+  const float rA = approx_rcp(f32_from_i64(s.A));
   const DepthSetup d = depth_setup(s, rA, tag);
   unsigned frags = 0;
   I r0 = e.e0, r1 = e.e1, r2 = e.e2;
@@ -230,7 +230,7 @@ __device__ __forceinline__ unsigned raster_thread64(const TriSetup& s, unsigned 
 __device__ __forceinline__ unsigned raster_warp(const TriSetup& s, unsigned long long tag, int px0, int px1, int py0,
                                                 int py1, int x0, int y0, int bshift_x, unsigned long long* skey,
                                                 int lane) {
-  const float rA = approx_rcp((float)s.A);
+  const float rA = approx_rcp(f32_from_i64(s.A));
   const int bw = px1 - px0 + 1, n = bw * (py1 - py0 + 1);
   const int dy = 32 / bw, dx = 32 - dy * bw;
   int lx = lane % bw, ly = lane / bw;
@@ -281,17 +281,24 @@ __device__ __forceinline__ void write_empty(const TileScene& p, size_t o) {
   }
 }
 
-// Barycentrics of pixel (x, y) from a record: exact int64 edge functions
-// times 1/A.
+// Barycentrics of pixel (x, y) from a record: exact edge functions times
+// 1/A.  The record stores 1/A negated when A >= 2^31; below that the pixel's
+// edge functions (in [0, A], the pixel being covered) are exact in wrapping
+// 32-bit arithmetic.
 __device__ __forceinline__ void rec_bary(const int* r, int x, int y, float& b0, float& b1, float& b2) {
   const int Px = 256 * x + 128, Py = 256 * y + 128;
   const int X0 = r[0], Y0 = r[1], X1 = r[2], Y1 = r[3], X2 = r[4], Y2 = r[5];
-  const float rA = __int_as_float(r[R_RA]);
-  // exact edge functions from 32-bit differences (each below 2^24) widened once
-  const long long w1 = (long long)(X0 - X2) * (Py - Y2) - (long long)(Y0 - Y2) * (Px - X2);
-  const long long w2 = (long long)(X1 - X0) * (Py - Y0) - (long long)(Y1 - Y0) * (Px - X0);
-  b1 = (float)w1 * rA;
-  b2 = (float)w2 * rA;
+  const float rAs = __int_as_float(r[R_RA]);
+  if (rAs > 0.0f) {
+    b1 = (float)edge_fn_wrap32(X2, Y2, X0, Y0, Px, Py) * rAs;
+    b2 = (float)edge_fn_wrap32(X0, Y0, X1, Y1, Px, Py) * rAs;
+  } else {
+    // exact edge functions from 32-bit differences (each below 2^24) widened once
+    const long long w1 = (long long)(X0 - X2) * (Py - Y2) - (long long)(Y0 - Y2) * (Px - X2);
+    const long long w2 = (long long)(X1 - X0) * (Py - Y0) - (long long)(Y1 - Y0) * (Px - X0);
+    b1 = f32_from_i64(w1) * -rAs;
+    b2 = f32_from_i64(w2) * -rAs;
+  }
   b0 = 1.0f - b1 - b2;
 }
 
@@ -345,8 +352,8 @@ __device__ __forceinline__ void shade_from_global(const TileScene& p, unsigned t
   const int Px = 256 * x + 128, Py = 256 * y + 128;
   const long long w1 = (long long)(s.X0 - s.X2) * (Py - s.Y2) - (long long)(s.Y0 - s.Y2) * (Px - s.X2);
   const long long w2 = (long long)(s.X1 - s.X0) * (Py - s.Y0) - (long long)(s.Y1 - s.Y0) * (Px - s.X0);
-  const float rA = approx_rcp((float)s.A);
-  float b1 = (float)w1 * rA, b2 = (float)w2 * rA, b0 = 1.0f - b1 - b2;
+  const float rA = approx_rcp(f32_from_i64(s.A));
+  float b1 = f32_from_i64(w1) * rA, b2 = f32_from_i64(w2) * rA, b0 = 1.0f - b1 - b2;
   if (PERSP) perspective_bary(b0, b1, b2, __ldg(p.invw + s.v0), __ldg(p.invw + s.v1), __ldg(p.invw + s.v2));
   float c0 = 0.80f, c1 = 0.75f, c2 = 0.65f;
   if (p.color) {
@@ -381,7 +388,9 @@ __device__ __forceinline__ void shade_from_global(const TileScene& p, unsigned t
 template <bool PERSP>
 __device__ __forceinline__ void fill_record(const TileScene& p, const TriSetup& s, int* r) {
   r[0] = s.X0; r[1] = s.Y0; r[2] = s.X1; r[3] = s.Y1; r[4] = s.X2; r[5] = s.Y2;
-  r[R_RA] = __float_as_int(approx_rcp((float)s.A));
+  // 1/A, negated when A >= 2^31 (rec_bary then takes the 64-bit form)
+  const float rA = approx_rcp(f32_from_i64(s.A));
+  r[R_RA] = __float_as_int(s.A < (1LL << 31) ? rA : -rA);
   float* a = reinterpret_cast<float*>(r + R_ATTR);
   const int v[3] = {s.v0, s.v1, s.v2};
   if (PERSP) {

@@ -741,24 +741,33 @@ def measure_e2e(args, ctx, r, ds, fb, scene, world, dist, barrier) -> dict:
 
 def bin_sweep(args, ctx, scene, ds) -> dict:
     """Forward time of the headline workload at every bin size (8, 16, 32, 64)
-    under the hardware and dynamic schedules (the workload's bin-size sweep)."""
+    under the hardware and dynamic schedules (the workload's bin-size sweep),
+    and under the fused (no tiling) and unfused (one kernel per stage)
+    mappings of the same pipeline."""
     from paper_1404_6293_gb300 import _lib as L
     from paper_1404_6293_gb300.raster import Framebuffer, Rasterizer
     out = {}
     K = args.steps
-    for b in (8, 16, 32, 64):
-        for sched in ("hardware", "dynamic"):
-            r = Rasterizer(scene.width, scene.height, b, b, sched)
-            if args.perspective:
-                r.set_option(L.PIKO_OPT_PERSPECTIVE, 1)
-            fb = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode)
-            stats, covered = size_and_count(r, ds, fb)
-            step_ms, stage_ms = time_forward(ctx, r, ds, fb, K, args.warmup)
-            ms = sum(step_ms) / K
-            out[f"{b}x{b} {sched}"] = {"ms_per_step": ms, "value": scene.num_triangles / (ms * 1e-3) / 1e6,
-                                       "process_ms": float(stage_ms[:, 4].mean()),
-                                       "bin_entries": stats["bin_entries"]}
-            r.close()
+    cands = [(b, sched) for b in (8, 16, 32, 64) for sched in ("hardware", "dynamic")]
+    cands += [(16, "fused"), (16, "unfused")]  # the other two mappings (bins unused)
+    for b, sched in cands:
+        r = Rasterizer(scene.width, scene.height, b, b, sched)
+        if args.perspective:
+            r.set_option(L.PIKO_OPT_PERSPECTIVE, 1)
+        fb = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode)
+        stats, covered = size_and_count(r, ds, fb)
+        step_ms, stage_ms = time_forward(ctx, r, ds, fb, K, args.warmup)
+        ms = sum(step_ms) / K
+        rec = {"ms_per_step": ms, "value": scene.num_triangles / (ms * 1e-3) / 1e6}
+        if sched in ("fused", "unfused"):
+            # stage boundaries: raster, shading (unfused: fragment shader), depth test, composite
+            rec["stage_ms"] = {n: float(stage_ms[:, i].mean()) for i, n in
+                               enumerate(["vertex", "raster", "shade", "depth", "composite"])}
+            out[sched] = rec
+        else:
+            rec.update({"process_ms": float(stage_ms[:, 4].mean()), "bin_entries": stats["bin_entries"]})
+            out[f"{b}x{b} {sched}"] = rec
+        r.close()
     return out
 
 
@@ -1214,7 +1223,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--bins", type=int, default=16)
-    ap.add_argument("--schedule", default="hardware", choices=["static", "dynamic", "hardware"],
+    ap.add_argument("--schedule", default="hardware", choices=["static", "dynamic", "hardware", "fused", "unfused"],
                     help="tile schedule of the heightfield line (hardware: one CTA per tile, the fastest "
                          "of the bin-size x schedule sweep at 16x16)")
     ap.add_argument("--threads", type=int, default=0, help="Process CTA size (0: library default)")
@@ -1226,7 +1235,7 @@ def main():
                     help="largest box (pixels inside a tile) one thread rasterizes; larger boxes take a warp "
                          "(0: library default)")
     ap.add_argument("--deferred-bins", type=int, default=16)
-    ap.add_argument("--deferred-schedule", default="hardware", choices=["static", "dynamic", "hardware"])
+    ap.add_argument("--deferred-schedule", default="hardware", choices=["static", "dynamic", "hardware", "fused", "unfused"])
     ap.add_argument("--batch-scenes", type=int, default=256)
     ap.add_argument("--batch-bins", type=int, default=0, help="batch workload: one square bin size for all scenes "
                     "instead of the autotuner's choice (0: autotune)")

@@ -61,6 +61,19 @@ extern "C" {
 #define PIKO_SCHED_DYNAMIC 1  /* LoadBalance: persistent CTAs pop tiles from an atomic queue */
 #define PIKO_SCHED_HARDWARE 2 /* one CTA per tile, balanced by the hardware block scheduler
                                  (the schedule elimination of Sec. 5.2.2)                   */
+/* Two other mappings of the same pipeline, for the design-space comparison of
+ * Sec. 7.2 (same keys and colours; bin size and threads per tile unused):   */
+#define PIKO_SCHED_FUSED 3    /* full fusion without tiling (the FreePipe-style point of
+                                 Sec. 7.2): one pass over the triangles takes a 64-bit
+                                 atomic minimum on the key buffer in global memory, then
+                                 every pixel is shaded from its winner                     */
+#define PIKO_SCHED_UNFUSED 4  /* the Baseline pipeline of Sec. 7.1, one kernel per stage:
+                                 rasterizer (every covered sample to a global fragment
+                                 buffer), fragment shader (every fragment), depth test,
+                                 composite.  The fragment buffer grows like the bin lists
+                                 (PIKO_OPT_CHECK_CAPACITY); its overflow is reported as
+                                 PIKO_ERR_OVERFLOW.  Batches treat both as DYNAMIC.  Work
+                                 counters (piko_raster_stats) are not kept on these two.  */
 
 /* ---- shading modes ---------------------------------------------------- */
 #define PIKO_SHADE_GOURAUD 0 /* rgb = sum b_i c_i                                         */

@@ -22,6 +22,8 @@ PIKO_ERR_BAD_INDEX = 6
 PIKO_SCHED_STATIC = 0
 PIKO_SCHED_DYNAMIC = 1
 PIKO_SCHED_HARDWARE = 2
+PIKO_SCHED_FUSED = 3
+PIKO_SCHED_UNFUSED = 4
 
 PIKO_SHADE_GOURAUD = 0
 PIKO_SHADE_LAMBERT = 1

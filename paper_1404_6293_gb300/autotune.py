@@ -5,7 +5,8 @@ architecture (Sec. 7.2: spatial binning helps most scenes but not one made
 of tiny uniform triangles; fusing stages trades load balance for locality).
 This tuner searches the same knobs automatically: for a scene it times the
 forward pass under every (bin size, schedule, threads per bin) candidate with
-CUDA events and keeps the fastest.  Threads per bin is the third template
+CUDA events and keeps the fastest; the fused (no tiling) and unfused (one
+kernel per stage) mappings of Sec. 7.2 are two more candidates.  Threads per bin is the third template
 parameter of the paper's Listing 1 stage; small triangles favour fewer
 threads per bin (more CTAs per SM), large ones more (more warps per tile).  Results are cached by workload features (resolution,
 triangle count, coverage density, shading mode) so that similar scenes share
@@ -35,6 +36,9 @@ DEFAULT_SCHEDULES: Tuple[str, ...] = ("static", "dynamic", "hardware")
 THREAD_CHOICES: Tuple[int, ...] = (64, 128, 256, 512)  # the CTA sizes the library accepts
 # a batch has no hardware mapping (its tiles are dealt inside one persistent launch)
 BATCH_SCHEDULES: Tuple[str, ...] = ("static", "dynamic")
+# the other two mappings of the pipeline (no tiling; one kernel per stage):
+# bin size and threads per bin do not apply, so each is one candidate
+OTHER_MAPPINGS: Tuple[str, ...] = ("fused", "unfused")
 
 
 def default_threads(bin_px: int) -> int:
@@ -61,9 +65,10 @@ def features(scene: DeviceScene) -> str:
 class Autotuner:
     def __init__(self, bins: Iterable[Tuple[int, int]] = DEFAULT_BINS,
                  schedules: Iterable[str] = DEFAULT_SCHEDULES, reps: int = 3, cache_path: Optional[str] = None,
-                 tune_threads: bool = True):
+                 tune_threads: bool = True, other_mappings: Iterable[str] = OTHER_MAPPINGS):
         self.bins = tuple(tuple(b) for b in bins)
         self.schedules = tuple(schedules)
+        self.other_mappings = tuple(other_mappings)
         self.tune_threads = tune_threads
         self.reps = reps
         self.cache: Dict[str, dict] = {}
@@ -110,6 +115,13 @@ class Autotuner:
                     trials.append({"bin": [bw, bh], "schedule": sched, "threads": th, "ms": ms})
                     if best is None or ms < best["ms"]:
                         best = {"bin": [bw, bh], "schedule": sched, "threads": th, "ms": ms}
+        bw, bh = self.bins[0] if self.bins else (16, 16)
+        for sched in self.other_mappings:
+            th = default_threads(bw * bh)
+            ms = self.time_candidate(scene, bw, bh, sched, th)
+            trials.append({"bin": [bw, bh], "schedule": sched, "threads": th, "ms": ms})
+            if best is None or ms < best["ms"]:
+                best = {"bin": [bw, bh], "schedule": sched, "threads": th, "ms": ms}
         best["trials"] = trials
         return best
 

@@ -61,6 +61,12 @@ struct piko_raster {
   unsigned scan_epoch = 0;
   unsigned* bin_tris = nullptr;
   long long ecap = 0;
+  // fragment buffers of the unfused pipeline (PIKO_SCHED_UNFUSED)
+  unsigned* frag_pix = nullptr;
+  unsigned long long* frag_key = nullptr;
+  float4* frag_rgba = nullptr;
+  long long fcap_pix = 0, fcap_key = 0, fcap_rgba = 0;
+  unsigned* h_frags = nullptr;  // pinned: fragment count read back
   DevStatus* status = nullptr;
   unsigned long long* h_needed = nullptr;  // pinned
   long long last_entries = 0;              // bin entries of the last frame read back (0: none yet)
@@ -118,7 +124,7 @@ int piko_raster_version(void) { return 100; }
 piko_raster* piko_raster_create(int width, int height, int bin_w, int bin_h, int schedule) {
   if (width < 1 || height < 1 || width > 32767 || height > 32767) return nullptr;
   if (!valid_bin(bin_w) || !valid_bin(bin_h)) return nullptr;
-  if (schedule < PIKO_SCHED_STATIC || schedule > PIKO_SCHED_HARDWARE) return nullptr;
+  if (schedule < PIKO_SCHED_STATIC || schedule > PIKO_SCHED_UNFUSED) return nullptr;
   piko_raster* h = new piko_raster();
   h->W = width; h->H = height; h->bin_w = bin_w; h->bin_h = bin_h; h->schedule = schedule;
   h->g.W = width; h->g.H = height;
@@ -140,6 +146,7 @@ piko_raster* piko_raster_create(int width, int height, int bin_w, int bin_h, int
             cudaMemset(h->chunk_state, 0, sizeof(unsigned long long) * scan_chunks(h->nbins)) == cudaSuccess &&
             cudaMalloc(&h->status, sizeof(DevStatus)) == cudaSuccess &&
             cudaMallocHost(&h->h_needed, sizeof(unsigned long long)) == cudaSuccess &&
+            cudaMallocHost(&h->h_frags, sizeof(unsigned)) == cudaSuccess &&
             cudaMemset(h->bin_count, 0, sizeof(unsigned) * 2 * h->nbins) == cudaSuccess &&
             cudaMemset(h->status, 0, sizeof(DevStatus)) == cudaSuccess &&
             cudaDeviceSynchronize() == cudaSuccess;
@@ -163,9 +170,13 @@ void piko_raster_destroy(piko_raster* h) {
   cudaFree(h->cursor);
   cudaFree(h->chunk_state);
   cudaFree(h->bin_tris);
+  cudaFree(h->frag_pix);
+  cudaFree(h->frag_key);
+  cudaFree(h->frag_rgba);
   cudaFree(h->status);
   batch_state_free(h->batch);
   if (h->h_needed) cudaFreeHost(h->h_needed);
+  if (h->h_frags) cudaFreeHost(h->h_frags);
   cudaGetLastError();
   delete h;
 }
@@ -192,7 +203,7 @@ int piko_raster_set_option(piko_raster* h, int key, int value) {
       h->check_capacity = value;
       return PIKO_OK;
     case PIKO_OPT_SCHEDULE:
-      if (value < PIKO_SCHED_STATIC || value > PIKO_SCHED_HARDWARE)
+      if (value < PIKO_SCHED_STATIC || value > PIKO_SCHED_UNFUSED)
         return fail(h, PIKO_ERR_INVALID_ARG, "unknown schedule");
       h->schedule = value;
       return PIKO_OK;
@@ -281,6 +292,83 @@ static int check_scene(piko_raster* h, const piko_scene* s) {
   return PIKO_OK;
 }
 
+// The fused (no tiling) and unfused (one kernel per stage) mappings, after
+// the vertex stage.  Stage events: 2 after the rasterizer, 3 after shading
+// (fused: the per-pixel pass; unfused: the fragment shader), 4 after the
+// depth test (unfused), 5 at the end.
+static int forward_other_mapping(piko_raster* h, const piko_scene* s, piko_framebuffer* fb, cudaStream_t st,
+                                 bool ev) {
+  const bool unfused = h->schedule == PIKO_SCHED_UNFUSED;
+  AltInputs in;
+  in.W = h->W; in.H = h->H; in.T = s->num_triangles; in.V = s->num_vertices;
+  in.mode = s->shade_mode; in.unclamped = h->unclamped;
+  in.tris = s->tris; in.vtx = h->vtx; in.color = s->color; in.normal = s->normal; in.light = s->light_dir;
+  in.invw = h->perspective ? h->invw : nullptr;
+  in.key = reinterpret_cast<unsigned long long*>(fb->key);
+  in.rgba = reinterpret_cast<float4*>(fb->rgba);
+  in.gnorm = reinterpret_cast<uint2*>(fb->gbuf_normal);
+  in.galb = reinterpret_cast<uint2*>(fb->gbuf_albedo);
+  in.st = h->status;
+  in.frag_pix = nullptr; in.frag_key = nullptr; in.frag_rgba = nullptr; in.frag_cap = 0;
+  const bool persp = h->perspective != 0;
+  const size_t key_bytes = sizeof(unsigned long long) * (size_t)h->W * h->H;
+  int r;
+  cudaError_t e;
+  if (!unfused) {
+    if ((e = cudaMemsetAsync(fb->key, 0xFF, key_bytes, st)) != cudaSuccess) return cuda_fail(h, e, "key clear");
+    if ((e = alt_stage(in, ALT_RASTER_MIN, persp, h->num_sms, st)) != cudaSuccess) return cuda_fail(h, e, "raster");
+    if (ev) cudaEventRecord(h->stage_ev[2], st);
+    if ((e = alt_stage(in, ALT_SHADE_PIXELS, persp, h->num_sms, st)) != cudaSuccess) return cuda_fail(h, e, "shade");
+    if (ev) {
+      cudaEventRecord(h->stage_ev[3], st);
+      cudaEventRecord(h->stage_ev[4], st);
+      cudaEventRecord(h->stage_ev[5], st);
+    }
+    return PIKO_OK;
+  }
+  // fragment buffers: at least two fragments per pixel or four per triangle
+  long long want = 2LL * h->W * h->H;
+  if (4LL * s->num_triangles > want) want = 4LL * s->num_triangles;
+  want += 4096;
+  for (int attempt = 0;; ++attempt) {
+    if (h->fcap_key < want) {
+      if ((r = grow(h, &h->frag_pix, &h->fcap_pix, want, "fragment pixels")) != PIKO_OK ||
+          (r = grow(h, &h->frag_key, &h->fcap_key, want, "fragment keys")) != PIKO_OK ||
+          (r = grow(h, &h->frag_rgba, &h->fcap_rgba, want, "fragment colours")) != PIKO_OK)
+        return r;
+    }
+    const long long cap = h->fcap_key < h->fcap_pix ? (h->fcap_key < h->fcap_rgba ? h->fcap_key : h->fcap_rgba)
+                                                    : (h->fcap_pix < h->fcap_rgba ? h->fcap_pix : h->fcap_rgba);
+    in.frag_pix = h->frag_pix; in.frag_key = h->frag_key; in.frag_rgba = h->frag_rgba;
+    in.frag_cap = (unsigned long long)cap;
+    if ((e = cudaMemsetAsync(&h->status->frag_count, 0, sizeof(unsigned), st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(fb->key, 0xFF, key_bytes, st)) != cudaSuccess)
+      return cuda_fail(h, e, "fragment count / key clear");
+    if ((e = alt_stage(in, ALT_RASTER_EMIT, persp, h->num_sms, st)) != cudaSuccess) return cuda_fail(h, e, "raster");
+    if (!h->check_capacity) break;
+    e = cudaMemcpyAsync(h->h_frags, &h->status->frag_count, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "fragment count read-back");
+    const long long need = (long long)*h->h_frags;
+    if (need <= cap) break;
+    if (attempt > 0) return fail(h, PIKO_ERR_OVERFLOW, "fragment buffer too large");
+    want = need + need / 8 + 4096;
+    // the rasterizer recorded an overflow: clear it and emit again
+    if ((e = cudaMemsetAsync(h->status, 0, sizeof(unsigned) * 2, st)) != cudaSuccess)
+      return cuda_fail(h, e, "status clear");
+  }
+  if (ev) cudaEventRecord(h->stage_ev[2], st);
+  if ((e = alt_stage(in, ALT_FRAG_SHADE, persp, h->num_sms, st)) != cudaSuccess) return cuda_fail(h, e, "fragment shader");
+  if (ev) cudaEventRecord(h->stage_ev[3], st);
+  if ((e = alt_stage(in, ALT_FRAG_DEPTH, persp, h->num_sms, st)) != cudaSuccess) return cuda_fail(h, e, "depth test");
+  if (ev) cudaEventRecord(h->stage_ev[4], st);
+  if ((e = alt_stage(in, ALT_FRAG_COMPOSITE, persp, h->num_sms, st)) != cudaSuccess ||
+      (e = alt_stage(in, ALT_CLEAR_EMPTY, persp, h->num_sms, st)) != cudaSuccess)
+    return cuda_fail(h, e, "composite");
+  if (ev) cudaEventRecord(h->stage_ev[5], st);
+  return PIKO_OK;
+}
+
 int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* fb, void* cuda_stream) {
   if (!h) return PIKO_ERR_INVALID_ARG;
   int r = check_scene(h, s);
@@ -306,6 +394,8 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
   launch_vertex(h->W, h->H, V, s->pos, s->mvp, h->vtx, lambert ? s->normal : nullptr, s->light_dir,
                 lambert ? h->vdot : nullptr, h->perspective ? h->invw : nullptr, h->num_sms, st);
   if (ev) cudaEventRecord(h->stage_ev[1], st);
+  if (h->schedule == PIKO_SCHED_FUSED || h->schedule == PIKO_SCHED_UNFUSED)
+    return forward_other_mapping(h, s, fb, st, ev);
   for (int attempt = 0;; ++attempt) {
     if (h->stats && attempt > 0) cudaMemsetAsync(&h->status->binned, 0, sizeof(unsigned long long), st);
     launch_setup_count(h->g, T, s->tris, V, h->vtx, h->rect, h->bin_count, h->status, h->stats, h->num_sms, st);
@@ -376,7 +466,9 @@ int piko_raster_forward_batch(piko_raster* h, const piko_scene* scenes, int n, p
   if (!h) return PIKO_ERR_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
   h->last_stream = st;
-  int r = batch_prepare(h->batch, h->num_sms, scenes, n, fbs, bin_sizes, schedules, h->bin_w, h->bin_h, h->schedule,
+  // the batch deals tiles inside one launch: the other mappings fall back to its dynamic schedule
+  const int dsched = h->schedule > PIKO_SCHED_HARDWARE ? PIKO_SCHED_DYNAMIC : h->schedule;
+  int r = batch_prepare(h->batch, h->num_sms, scenes, n, fbs, bin_sizes, schedules, h->bin_w, h->bin_h, dsched,
                         h->unclamped, h->perspective, st, h->err);
   if (r != PIKO_OK) return r;
   for (int attempt = 0;; ++attempt) {

@@ -51,7 +51,8 @@ struct DevStatus {
   unsigned long long needed;    // bin entries the last scan required
   unsigned int queue_head;      // tile counter of the dynamic schedule
   unsigned int scan_ticket;     // next chunk number of the scan (reset by its last chunk)
-  unsigned int pad[2];
+  unsigned int frag_count;      // fragments emitted by the unfused pipeline's rasterizer
+  unsigned int pad;
   unsigned long long tests;     // statistics (PIKO_OPT_STATS): pixel samples tested
   unsigned long long frags;     // covered samples
   unsigned long long shaded;    // covered pixels after the depth test
@@ -336,6 +337,33 @@ constexpr int DEFAULT_SMALL_PX = 4096;
 
 // Default CTA size of the Process stage for a tile of bin_px pixels.
 inline int default_process_threads(int bin_px) { return bin_px <= 64 ? 64 : (bin_px <= 256 ? 128 : 256); }
+
+// The two other pipeline mappings (piko_altpipe.cu): the fused one without
+// tiling and the unfused five-stage one.  Stages run in this order:
+// fused: ALT_RASTER_MIN, ALT_SHADE_PIXELS; unfused: ALT_RASTER_EMIT,
+// ALT_FRAG_SHADE, ALT_FRAG_DEPTH, ALT_FRAG_COMPOSITE, ALT_CLEAR_EMPTY; the
+// key buffer is set to all ones before the rasterizer.
+enum { ALT_RASTER_MIN = 0, ALT_RASTER_EMIT, ALT_SHADE_PIXELS, ALT_FRAG_SHADE, ALT_FRAG_DEPTH, ALT_FRAG_COMPOSITE,
+       ALT_CLEAR_EMPTY };
+struct AltInputs {
+  int W, H, T, V, mode, unclamped;
+  const int* tris;
+  const int4* vtx;
+  const float* color;
+  const float* normal;
+  const float* light;
+  const float* invw;
+  unsigned long long* key;
+  float4* rgba;
+  uint2* gnorm;
+  uint2* galb;
+  DevStatus* st;
+  unsigned* frag_pix;              // fragment buffers (unfused): pixel, key, colour
+  unsigned long long* frag_key;    //   (G-buffer mode: the colour slots hold the
+  float4* frag_rgba;               //   normal and albedo halves)
+  unsigned long long frag_cap;
+};
+cudaError_t alt_stage(const AltInputs& in, int stage, bool persp, int num_sms, cudaStream_t s);
 
 void launch_deferred_light(int W, int H, const unsigned long long* key, const uint2* gnorm,
                            const uint2* galb, const float4* lights, int n_lights, float4* rgba,

@@ -17,7 +17,8 @@ import torch
 from . import _lib as L
 
 KEY_EMPTY = 0xFFFFFFFFFFFFFFFF
-_SCHEDULES = {"static": L.PIKO_SCHED_STATIC, "dynamic": L.PIKO_SCHED_DYNAMIC, "hardware": L.PIKO_SCHED_HARDWARE}
+_SCHEDULES = {"static": L.PIKO_SCHED_STATIC, "dynamic": L.PIKO_SCHED_DYNAMIC, "hardware": L.PIKO_SCHED_HARDWARE,
+              "fused": L.PIKO_SCHED_FUSED, "unfused": L.PIKO_SCHED_UNFUSED}
 
 
 class PikoError(RuntimeError):
@@ -116,8 +117,9 @@ class Framebuffer:
 class Rasterizer:
     """One rasterizer handle: framebuffer size, bin size and tile schedule.
 
-    schedule: "static" (DirectMap), "dynamic" (LoadBalance) or "hardware"
-    (one CTA per tile)."""
+    schedule: "static" (DirectMap), "dynamic" (LoadBalance), "hardware"
+    (one CTA per tile), or one of the other pipeline mappings: "fused" (no
+    tiling, global depth buffer) and "unfused" (one kernel per stage)."""
 
     def __init__(self, width: int, height: int, bin_w: int = 16, bin_h: int = 16, schedule="static"):
         if not torch.cuda.is_available():

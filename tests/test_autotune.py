@@ -8,7 +8,8 @@ import pytest
 import torch
 
 from paper_1404_6293_gb300 import scenes as S
-from paper_1404_6293_gb300.autotune import (BATCH_SCHEDULES, DEFAULT_BINS, DEFAULT_SCHEDULES, THREAD_CHOICES,
+from paper_1404_6293_gb300.autotune import (BATCH_SCHEDULES, DEFAULT_BINS, DEFAULT_SCHEDULES, OTHER_MAPPINGS,
+                                            THREAD_CHOICES,
                                             Autotuner, default_threads, features, thread_candidates)
 from paper_1404_6293_gb300.raster import DeviceScene
 
@@ -76,8 +77,11 @@ def test_tuned_settings_are_valid_and_render_exactly():
     k = tuner.knobs(ds[0])
     (bw, bh), sched = tuner.choose(ds[0])
     assert (bw, bh) == k["bin"] and sched == k["schedule"]
-    assert (bw, bh) in ((16, 16), (32, 32)) and sched in DEFAULT_SCHEDULES
-    assert k["threads"] in thread_candidates(bw, bh)
+    assert (bw, bh) in ((16, 16), (32, 32)) and sched in DEFAULT_SCHEDULES + OTHER_MAPPINGS
+    assert k["threads"] in thread_candidates(bw, bh) or sched in OTHER_MAPPINGS
+    # every candidate was timed: bins x schedules x threads, plus the two other mappings
+    trials = next(iter(tuner.cache.values()))["trials"]
+    assert {t["schedule"] for t in trials} == set(DEFAULT_SCHEDULES + OTHER_MAPPINGS)
     # the tuned knobs render the scene exactly
     r1 = Rasterizer(host[0].width, host[0].height, bw, bh, sched)
     r1.set_option(L.PIKO_OPT_THREADS_PER_TILE, k["threads"])

@@ -9,6 +9,8 @@ Functions without a pin against something other than this code: none of the
 fixed-point conventions can be pinned to the paper, which is silent on them
 (see the header of ``piko_oracle.c``); they are pinned to closed forms,
 invariants and the separately written scanline rasterizer by the tests.
+Near/far clipping (O16, ``set_clipping``) is a process-wide switch of the
+library: set it around calls, not from concurrent threads.
 """
 from __future__ import annotations
 
@@ -63,6 +65,11 @@ def _load():
         lib.oracle_backward.argtypes = [i32, i32, i32, P, i64, P, P, P, P, P, i32, i32, P, P, P, P, P]
         lib.oracle_loss.argtypes = [i32, i32, i32, P, i64, P, P, P, P, P, i32, i32, P, P]
         lib.oracle_loss.restype = C.c_double
+        lib.oracle_set_clipping.argtypes = [i32]
+        lib.oracle_set_clipping.restype = None
+        lib.oracle_get_clipping.argtypes = []
+        lib.oracle_get_clipping.restype = i32
+        lib.oracle_clip_count.argtypes = [i32, i32, i32, P, i64, P, P, P]
         _lib = lib
         return lib
 
@@ -231,3 +238,39 @@ def half_from_double(x: float) -> int:
 
 def double_from_half(h: int) -> float:
     return float(_load().oracle_double_from_half(int(h)))
+
+
+def set_clipping(on: bool) -> None:
+    """O16: near/far clipping instead of the culls of O2/O3 for every later
+    call (a process-wide switch of the library; off by default)."""
+    _load().oracle_set_clipping(1 if on else 0)
+
+
+def get_clipping() -> bool:
+    return bool(_load().oracle_get_clipping())
+
+
+class clipping:
+    """Context manager: O16 clipping on (or off) inside the block."""
+
+    def __init__(self, on: bool = True):
+        self.on = on
+
+    def __enter__(self):
+        self.prev = get_clipping()
+        set_clipping(self.on)
+        return self
+
+    def __exit__(self, *exc):
+        set_clipping(self.prev)
+        return False
+
+
+def clip_count(scene, mvp=None) -> int:
+    """Number of sub-triangles the clipping step (O16) makes of the scene."""
+    lib = _load()
+    pos, tris, M = _geom(scene, mvp)
+    n = C.c_int64(0)
+    lib.oracle_clip_count(scene.width, scene.height, pos.shape[0], _p(pos), tris.shape[0], _p(tris), _p(M),
+                          C.byref(n))
+    return int(n.value)

@@ -50,6 +50,22 @@
  *       in the triangle's clip-space (or world-space) plane is then the value
  *       at the point the sample's ray meets the plane, the standard
  *       hyperbolic interpolation; with equal w it reduces to O11.
+ *   O16 optional near/far clipping (oracle_set_clipping(1)) in place of the
+ *       culls of O2/O3: a triangle with a vertex outside -w <= z <= w (or
+ *       with w not > 0) is clipped in clip space, first against z + w >= 0,
+ *       then against w - z >= 0 (Sutherland-Hodgman over the edges in
+ *       order from vertex 0; a crossing at t = d_a / (d_a - d_b), the new
+ *       point a + t (b - a) per component, all float32, each operation
+ *       rounded, no fused multiply-add).  The polygon (3 to 5 points) is
+ *       fanned from its first point into (p0, p_k, p_k+1).  Each point is
+ *       divided, mapped and snapped as in O4/O5, its Z clamped to
+ *       [0, 2^24-1] instead of culled, w not > 0 culling its sub-triangle.
+ *       Sub-triangles rasterize as in O6-O10 with the original triangle's
+ *       index in the key.  A clipped triangle is shaded (and differentiated)
+ *       from its original vertices with clip-space weights b = n / sum(n),
+ *       n = a x c, a_i = X_i - x W_i, c_i = Y_i - y W_i for the pixel
+ *       centre's NDC (x, y): the point where the centre's ray meets the
+ *       triangle's plane, i.e. perspective-correct whatever O15's flag.
  *
  * The paper fixes none of the bit-level rules above (fixed-point format,
  * fill rule, depth format, rounding, tie-break, light model); they are the
@@ -79,8 +95,14 @@ typedef struct {
   int32_t X, Y;
   uint32_t Z;
   int32_t ok;
-  double w; /* clip w (O1), for O15 */
+  double w;      /* clip w (O1), for O15 */
+  float c[4];    /* clip coordinates (O1), for O16 */
 } ovtx;
+
+/* O16 near/far clipping instead of culling (off by default) */
+static int g_clip = 0;
+void oracle_set_clipping(int on) { g_clip = on ? 1 : 0; }
+int oracle_get_clipping(void) { return g_clip; }
 
 static void vertex_stage_one(int W, int H, const float *p, const float *M, ovtx *o) {
   float c[4];
@@ -97,6 +119,7 @@ static void vertex_stage_one(int W, int H, const float *p, const float *M, ovtx 
   }
   o->X = 0; o->Y = 0; o->Z = 0; o->ok = 0;
   o->w = (double)c[3];
+  for (int k = 0; k < 4; ++k) o->c[k] = c[k];
   if (!(c[3] > 0.0f)) return;                                   /* O2 */
   float nx = c[0] / c[3], ny = c[1] / c[3], nz = c[2] / c[3];
   if (!(nz >= -1.0f && nz <= 1.0f)) return;                     /* O3 */
@@ -185,13 +208,150 @@ static int cover_and_depth(const otri *t, int px, int py, uint32_t *z, int64_t w
   return 1;
 }
 
-static otri *setup_all(const ovtx *vs, int V, int64_t T, const int32_t *tris, uint8_t **valid,
-                       int *bad) {
-  otri *ts = (otri *)malloc(sizeof(otri) * (size_t)(T > 0 ? T : 1));
-  uint8_t *ok = (uint8_t *)malloc((size_t)(T > 0 ? T : 1));
-  for (int64_t i = 0; i < T; ++i) ok[i] = (uint8_t)setup_triangle(vs, V, tris + 3 * i, &ts[i], bad);
-  *valid = ok;
-  return ts;
+/* ------------------------------------------------------------------ O16 */
+typedef struct {
+  float c[4];
+} cvert;
+
+/* one Sutherland-Hodgman pass: plane 0 keeps z + w >= 0, plane 1 w - z >= 0 */
+static int clip_plane(const cvert *in, int n, cvert *out, int plane) {
+  int m = 0;
+  for (int k = 0; k < n; ++k) {
+    const cvert *a = &in[k], *b = &in[(k + 1) % n];
+    float da = plane == 0 ? a->c[2] + a->c[3] : a->c[3] - a->c[2];
+    float db = plane == 0 ? b->c[2] + b->c[3] : b->c[3] - b->c[2];
+    int ina = da >= 0.0f, inb = db >= 0.0f;
+    if (ina) out[m++] = *a;
+    if (ina != inb) {
+      float den = da - db;
+      float t = da / den;
+      cvert v;
+      for (int q = 0; q < 4; ++q) {
+        float d = b->c[q] - a->c[q];
+        float u = t * d;
+        v.c[q] = a->c[q] + u;
+      }
+      out[m++] = v;
+    }
+  }
+  return m;
+}
+
+/* O4/O5 for a clipped point: 1 if it snaps inside the guard band */
+static int snap_point(int W, int H, const float *c, int64_t *X, int64_t *Y, int64_t *Z) {
+  if (!(c[3] > 0.0f)) return 0;
+  float nx = c[0] / c[3], ny = c[1] / c[3], nz = c[2] / c[3];
+  float sx = (nx * 0.5f + 0.5f) * (float)W;
+  float sy = (0.5f - ny * 0.5f) * (float)H;
+  float sz = (nz * 0.5f + 0.5f) * 16777215.0f;
+  float fx = sx * 256.0f, fy = sy * 256.0f;
+  if (!(fabsf(fx) < 8388608.0f && fabsf(fy) < 8388608.0f)) return 0;
+  float zr = rintf(sz);
+  if (!(zr >= 0.0f)) zr = 0.0f; /* NaN or below the near plane by rounding */
+  if (zr > 16777215.0f) zr = 16777215.0f;
+  *X = (int64_t)rintf(fx);
+  *Y = (int64_t)rintf(fy);
+  *Z = (int64_t)zr;
+  return 1;
+}
+
+/* orientation and area of a triangle given by snapped points (O6) */
+static int setup_points(const int64_t *X, const int64_t *Y, const int64_t *Z, otri *t) {
+  for (int k = 0; k < 3; ++k) { t->X[k] = X[k]; t->Y[k] = Y[k]; t->Z[k] = Z[k]; t->vid[k] = -1; }
+  int64_t A = (t->X[1] - t->X[0]) * (t->Y[2] - t->Y[0]) - (t->X[2] - t->X[0]) * (t->Y[1] - t->Y[0]);
+  if (A == 0) return 0;
+  if (A < 0) {
+    int64_t s;
+    s = t->X[1]; t->X[1] = t->X[2]; t->X[2] = s;
+    s = t->Y[1]; t->Y[1] = t->Y[2]; t->Y[2] = s;
+    s = t->Z[1]; t->Z[1] = t->Z[2]; t->Z[2] = s;
+    A = -A;
+  }
+  t->A = A;
+  return 1;
+}
+
+/* 1 if clipping applies to triangle idx (O16): its indices are valid and a
+ * vertex failed the vertex stage */
+static int needs_clip(const ovtx *vs, int V, const int32_t *idx) {
+  if (!g_clip) return 0;
+  for (int k = 0; k < 3; ++k)
+    if (idx[k] < 0 || idx[k] >= V) return 0;
+  return !(vs[idx[0]].ok && vs[idx[1]].ok && vs[idx[2]].ok);
+}
+
+/* the sub-triangles of a clipped triangle (at most 3), in fan order */
+static int clip_triangle(int W, int H, const ovtx *vs, const int32_t *idx, otri *out) {
+  cvert p[8], q[8];
+  for (int k = 0; k < 3; ++k)
+    for (int c = 0; c < 4; ++c) p[k].c[c] = vs[idx[k]].c[c];
+  int n = clip_plane(p, 3, q, 0);
+  n = clip_plane(q, n, p, 1);
+  int m = 0;
+  for (int k = 1; k + 1 < n; ++k) {
+    int64_t X[3], Y[3], Z[3];
+    const cvert *tri[3] = {&p[0], &p[k], &p[k + 1]};
+    int ok = 1;
+    for (int j = 0; j < 3 && ok; ++j) ok = snap_point(W, H, tri[j]->c, &X[j], &Y[j], &Z[j]);
+    if (ok && setup_points(X, Y, Z, &out[m])) ++m;
+  }
+  return m;
+}
+
+/* All triangles set up: the T input triangles first (valid[i] = survives
+ * O2-O6), then the sub-triangles of clipped ones (O16); orig[i] is the input
+ * index each one keys with.  *total = T + number of sub-triangles. */
+typedef struct {
+  otri *ts;
+  uint8_t *valid;
+  int32_t *orig;
+  int64_t total;
+} oset;
+
+static oset setup_all(int W, int H, const ovtx *vs, int V, int64_t T, const int32_t *tris, int *bad) {
+  oset o;
+  int64_t cap = T + 16;
+  o.ts = (otri *)malloc(sizeof(otri) * (size_t)cap);
+  o.valid = (uint8_t *)malloc((size_t)cap);
+  o.orig = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+  o.total = T;
+  for (int64_t i = 0; i < T; ++i) {
+    o.valid[i] = (uint8_t)setup_triangle(vs, V, tris + 3 * i, &o.ts[i], bad);
+    o.orig[i] = (int32_t)i;
+  }
+  for (int64_t i = 0; i < T; ++i) {
+    if (!needs_clip(vs, V, tris + 3 * i)) continue;
+    otri sub[3];
+    int m = clip_triangle(W, H, vs, tris + 3 * i, sub);
+    for (int k = 0; k < m; ++k) {
+      if (o.total == cap) {
+        cap = 2 * cap;
+        o.ts = (otri *)realloc(o.ts, sizeof(otri) * (size_t)cap);
+        o.valid = (uint8_t *)realloc(o.valid, (size_t)cap);
+        o.orig = (int32_t *)realloc(o.orig, sizeof(int32_t) * (size_t)cap);
+      }
+      o.ts[o.total] = sub[k];
+      o.valid[o.total] = 1;
+      o.orig[o.total] = (int32_t)i;
+      ++o.total;
+    }
+  }
+  return o;
+}
+
+static void free_set(oset *o) {
+  free(o->ts); free(o->valid); free(o->orig);
+}
+
+int oracle_clip_count(int W, int H, int V, const float *pos, int64_t T, const int32_t *tris, const float *M,
+                      int64_t *nsub) {
+  int bad = 0;
+  ovtx *vs = vertex_stage_all(W, H, V, pos, M);
+  oset o = setup_all(W, H, vs, V, T, tris, &bad);
+  *nsub = o.total - T;
+  free_set(&o);
+  free(vs);
+  return bad ? ORACLE_BAD_INDEX : ORACLE_OK;
 }
 
 /* ------------------------------------------------- O10, brute force over all */
@@ -199,25 +359,24 @@ int oracle_raster_brute(int W, int H, int V, const float *pos, int64_t T, const 
                         const float *M, uint64_t *key, uint32_t *count) {
   int bad = 0;
   ovtx *vs = vertex_stage_all(W, H, V, pos, M);
-  uint8_t *valid;
-  otri *ts = setup_all(vs, V, T, tris, &valid, &bad);
+  oset o = setup_all(W, H, vs, V, T, tris, &bad);
   for (int py = 0; py < H; ++py)
     for (int px = 0; px < W; ++px) {
       uint64_t best = KEY_EMPTY;
       uint32_t n = 0;
-      for (int64_t i = 0; i < T; ++i) {
-        if (!valid[i]) continue;
+      for (int64_t i = 0; i < o.total; ++i) {
+        if (!o.valid[i]) continue;
         uint32_t z;
         int64_t w[3];
-        if (!cover_and_depth(&ts[i], px, py, &z, w)) continue;
+        if (!cover_and_depth(&o.ts[i], px, py, &z, w)) continue;
         ++n;
-        uint64_t k = ((uint64_t)z << 32) | (uint32_t)i;
+        uint64_t k = ((uint64_t)z << 32) | (uint32_t)o.orig[i];
         if (k < best) best = k;
       }
       key[(size_t)py * W + px] = best;
       if (count) count[(size_t)py * W + px] = n;
     }
-  free(ts); free(valid); free(vs);
+  free_set(&o); free(vs);
   return bad ? ORACLE_BAD_INDEX : ORACLE_OK;
 }
 
@@ -226,22 +385,21 @@ int oracle_keys_at(int W, int H, int V, const float *pos, int64_t T, const int32
                    const float *M, int64_t npix, const int32_t *pix, uint64_t *key) {
   int bad = 0;
   ovtx *vs = vertex_stage_all(W, H, V, pos, M);
-  uint8_t *valid;
-  otri *ts = setup_all(vs, V, T, tris, &valid, &bad);
+  oset o = setup_all(W, H, vs, V, T, tris, &bad);
   for (int64_t j = 0; j < npix; ++j) {
     int px = pix[2 * j], py = pix[2 * j + 1];
     uint64_t best = KEY_EMPTY;
-    for (int64_t i = 0; i < T; ++i) {
-      if (!valid[i]) continue;
+    for (int64_t i = 0; i < o.total; ++i) {
+      if (!o.valid[i]) continue;
       uint32_t z;
       int64_t w[3];
-      if (!cover_and_depth(&ts[i], px, py, &z, w)) continue;
-      uint64_t k = ((uint64_t)z << 32) | (uint32_t)i;
+      if (!cover_and_depth(&o.ts[i], px, py, &z, w)) continue;
+      uint64_t k = ((uint64_t)z << 32) | (uint32_t)o.orig[i];
       if (k < best) best = k;
     }
     key[j] = best;
   }
-  free(ts); free(valid); free(vs);
+  free_set(&o); free(vs);
   return bad ? ORACLE_BAD_INDEX : ORACLE_OK;
 }
 
@@ -254,6 +412,7 @@ typedef struct {
   int64_t T;
   const otri *ts;
   const uint8_t *valid;
+  const int32_t *orig;
   uint64_t *key;
 } band_job;
 
@@ -285,7 +444,7 @@ static void *band_worker(void *arg) {
         uint32_t z;
         int64_t w[3];
         if (!cover_and_depth(t, (int)px, (int)py, &z, w)) continue;
-        uint64_t k = ((uint64_t)z << 32) | (uint32_t)i;
+        uint64_t k = ((uint64_t)z << 32) | (uint32_t)j->orig[i];
         uint64_t *dst = &j->key[(size_t)py * j->W + px];
         if (k < *dst) *dst = k;
       }
@@ -297,14 +456,14 @@ int oracle_raster_bbox(int W, int H, int V, const float *pos, int64_t T, const i
                        const float *M, uint64_t *key, int nthreads) {
   int bad = 0;
   ovtx *vs = vertex_stage_all(W, H, V, pos, M);
-  uint8_t *valid;
-  otri *ts = setup_all(vs, V, T, tris, &valid, &bad);
+  oset o = setup_all(W, H, vs, V, T, tris, &bad);
   if (nthreads < 1) nthreads = 1;
   if (nthreads > H) nthreads = H > 0 ? H : 1;
   band_job *jobs = (band_job *)calloc((size_t)nthreads, sizeof(band_job));
   pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
   for (int k = 0; k < nthreads; ++k) {
-    jobs[k].W = W; jobs[k].H = H; jobs[k].T = T; jobs[k].ts = ts; jobs[k].valid = valid;
+    jobs[k].W = W; jobs[k].H = H; jobs[k].T = o.total; jobs[k].ts = o.ts; jobs[k].valid = o.valid;
+    jobs[k].orig = o.orig;
     jobs[k].key = key;
     jobs[k].y0 = (int)((int64_t)H * k / nthreads);
     jobs[k].y1 = (int)((int64_t)H * (k + 1) / nthreads);
@@ -315,7 +474,7 @@ int oracle_raster_bbox(int W, int H, int V, const float *pos, int64_t T, const i
     for (int k = 0; k < nthreads; ++k) pthread_create(&th[k], NULL, band_worker, &jobs[k]);
     for (int k = 0; k < nthreads; ++k) pthread_join(th[k], NULL);
   }
-  free(th); free(jobs); free(ts); free(valid); free(vs);
+  free(th); free(jobs); free_set(&o); free(vs);
   return bad ? ORACLE_BAD_INDEX : ORACLE_OK;
 }
 
@@ -338,10 +497,11 @@ int oracle_raster_scanline(int W, int H, int V, const float *pos, int64_t T, con
                            const float *M, uint64_t *key) {
   int bad = 0;
   ovtx *vs = vertex_stage_all(W, H, V, pos, M);
+  oset o = setup_all(W, H, vs, V, T, tris, &bad);
   for (size_t i = 0; i < (size_t)W * H; ++i) key[i] = KEY_EMPTY;
-  for (int64_t i = 0; i < T; ++i) {
-    otri t;
-    if (!setup_triangle(vs, V, tris + 3 * i, &t, &bad)) continue;
+  for (int64_t i = 0; i < o.total; ++i) {
+    if (!o.valid[i]) continue;
+    const otri t = o.ts[i];
     static const int ea[3] = {1, 2, 0}, eb[3] = {2, 0, 1};
     for (int py = 0; py < H; ++py) {
       int64_t Py = 256 * (int64_t)py + 128;
@@ -369,12 +529,13 @@ int oracle_raster_scanline(int W, int H, int V, const float *pos, int64_t T, con
         int64_t w2 = (t.X[1] - t.X[0]) * (Py - t.Y[0]) - (t.Y[1] - t.Y[0]) * (Px - t.X[0]);
         i128 num = (i128)w1 * (t.Z[1] - t.Z[0]) + (i128)w2 * (t.Z[2] - t.Z[0]);
         int64_t z = t.Z[0] + (int64_t)sl_floor_div128(num, (i128)t.A);
-        uint64_t k = ((uint64_t)z << 32) | (uint32_t)i;
+        uint64_t k = ((uint64_t)z << 32) | (uint32_t)o.orig[i];
         uint64_t *dst = &key[(size_t)py * W + px];
         if (k < *dst) *dst = k;
       }
     }
   }
+  free_set(&o);
   free(vs);
   return bad ? ORACLE_BAD_INDEX : ORACLE_OK;
 }
@@ -424,12 +585,34 @@ typedef struct {
 
 /* barycentrics of the winning triangle at (px,py), or 0 if key is empty;
  * screen-space (O11), or perspective-correct (O15) when persp is set */
-static int pixel_winner(const ovtx *vs, int V, const int32_t *tris, uint64_t k, int px, int py,
+static int pixel_winner_clipped(int W, int H, const ovtx *vs, const int32_t *idx, uint64_t k, int px,
+                                int py, winner *o) {
+  /* O16: the pixel centre's NDC and the clip-space weights of its ray's
+   * point on the triangle's plane */
+  double x = ((double)px + 0.5) / (double)W * 2.0 - 1.0;
+  double y = 1.0 - ((double)py + 0.5) / (double)H * 2.0;
+  double a[3], c[3];
+  for (int i = 0; i < 3; ++i) {
+    const ovtx *v = &vs[idx[i]];
+    a[i] = (double)v->c[0] - x * (double)v->c[3];
+    c[i] = (double)v->c[1] - y * (double)v->c[3];
+    o->vid[i] = idx[i];
+  }
+  double n[3] = {a[1] * c[2] - a[2] * c[1], a[2] * c[0] - a[0] * c[2], a[0] * c[1] - a[1] * c[0]};
+  double sum = n[0] + n[1] + n[2];
+  for (int i = 0; i < 3; ++i) o->b[i] = sum != 0.0 ? n[i] / sum : 1.0 / 3.0;
+  o->z = (uint32_t)(k >> 32);
+  return 1;
+}
+
+static int pixel_winner(int W, int H, const ovtx *vs, int V, const int32_t *tris, uint64_t k, int px, int py,
                         int persp, winner *o) {
   if (k == KEY_EMPTY) return 0;
   uint32_t id = (uint32_t)(k & 0xFFFFFFFFu);
   otri t;
   int bad = 0;
+  if (needs_clip(vs, V, tris + 3 * (int64_t)id))
+    return pixel_winner_clipped(W, H, vs, tris + 3 * (int64_t)id, k, px, py, o);
   if (!setup_triangle(vs, V, tris + 3 * (int64_t)id, &t, &bad)) return 0;
   int64_t w[3];
   uint32_t z;
@@ -493,7 +676,7 @@ int oracle_shade(int W, int H, int V, const float *pos, int64_t T, const int32_t
       size_t p = (size_t)py * W + px;
       winner wn;
       double rgb[3] = {0, 0, 0}, n[3] = {0, 0, 0}, alb[3] = {0, 0, 0};
-      int hit = pixel_winner(vs, V, tris, key[p], px, py, persp, &wn);
+      int hit = pixel_winner(W, H, vs, V, tris, key[p], px, py, persp, &wn);
       if (hit) shade_pixel(&wn, color, normal, L, mode, unclamped, rgb, n, alb);
       if (rgba) {
         for (int c = 0; c < 3; ++c) rgba[4 * p + c] = rgb[c];
@@ -571,7 +754,7 @@ int oracle_backward(int W, int H, int V, const float *pos, int64_t T, const int3
     for (int px = 0; px < W; ++px) {
       size_t p = (size_t)py * W + px;
       winner wn;
-      if (!pixel_winner(vs, V, tris, key[p], px, py, persp, &wn)) continue;
+      if (!pixel_winner(W, H, vs, V, tris, key[p], px, py, persp, &wn)) continue;
       const double *g = dl_drgba + 4 * p;
       double rgb[3], n[3], alb[3];
       shade_pixel(&wn, color, normal, L, mode, unclamped, rgb, n, alb);
@@ -613,7 +796,7 @@ double oracle_loss(int W, int H, int V, const float *pos, int64_t T, const int32
       size_t p = (size_t)py * W + px;
       winner wn;
       double rgb[3] = {0, 0, 0}, n[3], alb[3];
-      if (pixel_winner(vs, V, tris, key[p], px, py, persp, &wn))
+      if (pixel_winner(W, H, vs, V, tris, key[p], px, py, persp, &wn))
         shade_pixel(&wn, color, normal, L, mode, unclamped, rgb, n, alb);
       for (int c = 0; c < 3; ++c) {
         double e = rgb[c] - (double)target[4 * p + c];

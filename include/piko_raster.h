@@ -105,6 +105,16 @@ extern "C" {
                                        scene of a batch; piko_raster_backward_batch follows
                                        the setting of the last piko_raster_forward_batch,
                                        piko_raster_backward the handle's current setting  */
+#define PIKO_OPT_CLIP 11            /* 1: near/far clipping instead of culling: a triangle with
+                                       a vertex outside -w <= z <= w (or w not > 0) is clipped
+                                       against z = -w, then z = w, in clip space; the polygon
+                                       is fanned into sub-triangles that rasterize with the
+                                       triangle's index in the key, and a clipped triangle is
+                                       shaded (and differentiated) from its vertices with the
+                                       clip-space weights of each pixel centre's ray
+                                       (perspective-correct).  Single-scene calls only
+                                       (piko_raster_forward_batch rejects it); the sub-triangle
+                                       list grows like the bin lists.  Default 0: culling      */
 #define PIKO_OPT_WAIT_BUDGET 9      /* how long a device-side wait (scan look-back, batch grid
                                        barrier) may spin before it gives up, records
                                        PIKO_ERR_TIMEOUT and lets the frame's later phases

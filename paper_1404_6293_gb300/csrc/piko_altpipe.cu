@@ -35,6 +35,7 @@ struct AltParams {
   uint2* frag_gn;
   uint2* frag_ga;
   unsigned long long frag_cap;
+  unsigned clip_cap;  // capacity of the clipped sub-triangle list (sc.clip_tris)
 };
 
 constexpr int ALT_THREADS = 256;
@@ -118,19 +119,34 @@ __global__ void __launch_bounds__(ALT_THREADS) k_alt_raster(const __grid_constan
   const int lane = threadIdx.x & 31;
   const int W = p.sc.g.W, H = p.sc.g.H;
   const int warps_total = gridDim.x * (blockDim.x >> 5);
-  for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < p.T; base += warps_total * 32) {
+  // the frame's triangles: the input ones, then the clipped sub-triangles
+  int TT = p.T;
+  if (p.sc.clip_tris) {
+    const unsigned n = *reinterpret_cast<const volatile unsigned*>(&p.st->clip_count);
+    TT += (int)(n < p.clip_cap ? n : p.clip_cap);
+  }
+  for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < TT; base += warps_total * 32) {
     const int t = base + lane;
     TriSetup s{};
     bool ok = false, big = false;
     int px0 = 0, px1 = -1, py0 = 0, py1 = -1;
-    if (t < p.T) {
-      const int a = __ldg(p.sc.tris + 3 * (size_t)t), b = __ldg(p.sc.tris + 3 * (size_t)t + 1),
-                c = __ldg(p.sc.tris + 3 * (size_t)t + 2);
-      // an index outside [0, V) culls the triangle (the count pass of the
-      // binned path reports it; here it is reported too)
-      if ((unsigned)a >= (unsigned)p.V || (unsigned)b >= (unsigned)p.V || (unsigned)c >= (unsigned)p.V) {
-        record_error(p.st, PIKO_ERR_BAD_INDEX);
-      } else if (setup_triangle(a, b, c, p.sc.vtx, s)) {
+    unsigned key_id = (unsigned)t;
+    if (t < TT) {
+      bool live;
+      if (t >= p.T) {  // a clipped sub-triangle keys with its triangle's index
+        const int4* cp = p.sc.clip_tris + 3 * (size_t)(t - p.T);
+        live = setup_points(__ldg(cp), __ldg(cp + 1), __ldg(cp + 2), s);
+        key_id = __ldg(p.sc.clip_orig + (t - p.T));
+      } else {
+        const int a = __ldg(p.sc.tris + 3 * (size_t)t), b = __ldg(p.sc.tris + 3 * (size_t)t + 1),
+                  c = __ldg(p.sc.tris + 3 * (size_t)t + 2);
+        // an index outside [0, V) culls the triangle (the count pass of the
+        // binned path reports it; here it is reported too)
+        live = (unsigned)a < (unsigned)p.V && (unsigned)b < (unsigned)p.V && (unsigned)c < (unsigned)p.V;
+        if (!live) record_error(p.st, PIKO_ERR_BAD_INDEX);
+        else live = setup_triangle(a, b, c, p.sc.vtx, s);
+      }
+      if (live) {
         const int minX = min(s.X0, min(s.X1, s.X2)), maxX = max(s.X0, max(s.X1, s.X2));
         const int minY = min(s.Y0, min(s.Y1, s.Y2)), maxY = max(s.Y0, max(s.Y1, s.Y2));
         centre_range(minX, maxX, 0, W - 1, px0, px1);
@@ -141,8 +157,8 @@ __global__ void __launch_bounds__(ALT_THREADS) k_alt_raster(const __grid_constan
           const bool small32 = maxX - minX < 32768 && maxY - minY < 32768;
           big = npx > ALT_SMALL_PX;
           if (!big) {
-            if (small32) alt_walk<EMIT, int>(p, s, (unsigned)t, px0, px1, py0, py1);
-            else alt_walk<EMIT, long long>(p, s, (unsigned)t, px0, px1, py0, py1);
+            if (small32) alt_walk<EMIT, int>(p, s, key_id, px0, px1, py0, py1);
+            else alt_walk<EMIT, long long>(p, s, key_id, px0, px1, py0, py1);
           }
         }
       }
@@ -161,7 +177,8 @@ __global__ void __launch_bounds__(ALT_THREADS) k_alt_raster(const __grid_constan
       sj.v0 = sj.v1 = sj.v2 = 0;
       const int qx0 = __shfl_sync(FULL_MASK, px0, j), qx1 = __shfl_sync(FULL_MASK, px1, j);
       const int qy0 = __shfl_sync(FULL_MASK, py0, j), qy1 = __shfl_sync(FULL_MASK, py1, j);
-      alt_warp_box<EMIT>(p, sj, (unsigned)(base + j), qx0, qx1, qy0, qy1, lane);
+      const unsigned kid = __shfl_sync(FULL_MASK, key_id, j);
+      alt_warp_box<EMIT>(p, sj, kid, qx0, qx1, qy0, qy1, lane);
     }
   }
 }
@@ -253,18 +270,24 @@ cudaError_t alt_stage(const AltInputs& in, int stage, bool persp, int num_sms, c
   sc.slot_bits = 0; sc.nslots = 0; sc.rec_stride = 0; sc.tri_base = 0;
   sc.tris = in.tris; sc.vtx = in.vtx; sc.color = in.color; sc.normal = in.normal; sc.light = in.light;
   sc.vdot = nullptr; sc.invw = persp ? in.invw : nullptr;
+  sc.T = in.T; sc.clip_tris = in.clip_tris; sc.clip_orig = in.clip_orig;
+  sc.pos = in.clip_tris ? reinterpret_cast<const float4*>(in.pos) : nullptr;
+  sc.mvp = in.mvp;
   sc.key_out = in.key; sc.rgba_out = in.rgba; sc.gnorm_out = in.gnorm; sc.galb_out = in.galb;
   p.T = in.T; p.V = in.V; p.st = in.st;
   p.frag_pix = in.frag_pix; p.frag_key = in.frag_key; p.frag_rgba = in.frag_rgba;
   p.frag_gn = reinterpret_cast<uint2*>(in.frag_rgba);  // G-buffer mode: two uint2 halves of the same slots
   p.frag_ga = p.frag_gn + (in.frag_rgba ? in.frag_cap : 0);
   p.frag_cap = in.frag_cap;
+  p.clip_cap = in.clip_cap;
   const long long npx = (long long)in.W * in.H;
   switch (stage) {
     case ALT_RASTER_MIN:
     case ALT_RASTER_EMIT: {
       if (in.T <= 0) return cudaSuccess;
       long long g = ((in.T + 31) / 32 + (ALT_THREADS / 32) - 1) / (ALT_THREADS / 32);
+      if (g > 16LL * num_sms) g = 16LL * num_sms;
+      if (in.clip_tris) g += (long long)(in.clip_cap / 32 + 1) / (ALT_THREADS / 32) + 1;
       if (g > 16LL * num_sms) g = 16LL * num_sms;
       if (stage == ALT_RASTER_EMIT) k_alt_raster<true><<<(int)g, ALT_THREADS, 0, s>>>(p);
       else k_alt_raster<false><<<(int)g, ALT_THREADS, 0, s>>>(p);

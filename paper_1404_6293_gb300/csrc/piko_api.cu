@@ -24,7 +24,7 @@ int batch_launch_backward(BatchState* bs, const piko_scene* scenes, int n, const
 
 int piko_backward_launch(int W, int H, int mode, int unclamped, int T, int V, const int* tris, const int4* vtx,
                          const float* color, const float* normal, const float* light, const float* invw,
-                         const unsigned long long* key,
+                         const float* pos, const float* mvp, const unsigned long long* key,
                          const float* dl_drgba, float* dcolor, float* dnormal, float* dlight, int num_sms,
                          cudaStream_t s);
 
@@ -39,6 +39,7 @@ struct piko_raster {
   int small_px = 32;
   int stats = 0;
   int batch_launch = 0;  // 0 persistent cooperative, 1 one launch per phase
+  int clip = 0;                      // near/far clipping instead of culling (PIKO_OPT_CLIP)
   long long wait_budget = 40000000;  // clock cycles a device-side wait may take (PIKO_OPT_WAIT_BUDGET)
   int withhold = 0;                  // test hooks (PIKO_OPT_TEST_WITHHOLD)
   BatchState* batch = nullptr;
@@ -67,6 +68,11 @@ struct piko_raster {
   float4* frag_rgba = nullptr;
   long long fcap_pix = 0, fcap_key = 0, fcap_rgba = 0;
   unsigned* h_frags = nullptr;  // pinned: fragment count read back
+  // near/far clipping: sub-triangles (3 snapped points each) and their triangle
+  int4* clip_tris = nullptr;
+  unsigned* clip_orig = nullptr;
+  long long ccap_tris = 0, ccap_orig = 0;
+  unsigned* h_clips = nullptr;  // pinned: sub-triangle count read back
   DevStatus* status = nullptr;
   unsigned long long* h_needed = nullptr;  // pinned
   long long last_entries = 0;              // bin entries of the last frame read back (0: none yet)
@@ -147,6 +153,7 @@ piko_raster* piko_raster_create(int width, int height, int bin_w, int bin_h, int
             cudaMalloc(&h->status, sizeof(DevStatus)) == cudaSuccess &&
             cudaMallocHost(&h->h_needed, sizeof(unsigned long long)) == cudaSuccess &&
             cudaMallocHost(&h->h_frags, sizeof(unsigned)) == cudaSuccess &&
+            cudaMallocHost(&h->h_clips, sizeof(unsigned)) == cudaSuccess &&
             cudaMemset(h->bin_count, 0, sizeof(unsigned) * 2 * h->nbins) == cudaSuccess &&
             cudaMemset(h->status, 0, sizeof(DevStatus)) == cudaSuccess &&
             cudaDeviceSynchronize() == cudaSuccess;
@@ -173,10 +180,13 @@ void piko_raster_destroy(piko_raster* h) {
   cudaFree(h->frag_pix);
   cudaFree(h->frag_key);
   cudaFree(h->frag_rgba);
+  cudaFree(h->clip_tris);
+  cudaFree(h->clip_orig);
   cudaFree(h->status);
   batch_state_free(h->batch);
   if (h->h_needed) cudaFreeHost(h->h_needed);
   if (h->h_frags) cudaFreeHost(h->h_frags);
+  if (h->h_clips) cudaFreeHost(h->h_clips);
   cudaGetLastError();
   delete h;
 }
@@ -218,6 +228,10 @@ int piko_raster_set_option(piko_raster* h, int key, int value) {
     case PIKO_OPT_PERSPECTIVE:
       if (value != 0 && value != 1) return fail(h, PIKO_ERR_INVALID_ARG, "perspective must be 0 or 1");
       h->perspective = value;
+      return PIKO_OK;
+    case PIKO_OPT_CLIP:
+      if (value != 0 && value != 1) return fail(h, PIKO_ERR_INVALID_ARG, "clip must be 0 or 1");
+      h->clip = value;
       return PIKO_OK;
     case PIKO_OPT_WAIT_BUDGET:
       if (value < 1 || value > 1000000) return fail(h, PIKO_ERR_INVALID_ARG, "wait budget must be 1..1000000 kcycles");
@@ -292,6 +306,38 @@ static int check_scene(piko_raster* h, const piko_scene* s) {
   return PIKO_OK;
 }
 
+// Near/far clipping: the sub-triangle list for this frame.  With the
+// capacity check the count is read back (one host sync) and the list grown
+// and refilled once if it overflowed; without it an overflow is reported as
+// PIKO_ERR_OVERFLOW and the frame writes nothing.
+static int clip_pass(piko_raster* h, const piko_scene* s, cudaStream_t st) {
+  const int T = s->num_triangles;
+  long long want = T / 8 + 1024;
+  int r;
+  for (int attempt = 0;; ++attempt) {
+    if (h->ccap_tris < 3 * want || h->ccap_orig < want) {
+      if ((r = grow(h, &h->clip_tris, &h->ccap_tris, 3 * want, "clipped triangles")) != PIKO_OK ||
+          (r = grow(h, &h->clip_orig, &h->ccap_orig, want, "clipped triangle indices")) != PIKO_OK)
+        return r;
+    }
+    const long long cap = h->ccap_tris / 3 < h->ccap_orig ? h->ccap_tris / 3 : h->ccap_orig;
+    cudaError_t e = cudaMemsetAsync(&h->status->clip_count, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "clip count clear");
+    launch_clip(h->W, h->H, T, s->tris, s->num_vertices, s->pos, s->mvp, h->vtx, h->clip_tris, h->clip_orig,
+                (unsigned)cap, h->status, h->num_sms, st);
+    if (!h->check_capacity) return PIKO_OK;
+    e = cudaMemcpyAsync(h->h_clips, &h->status->clip_count, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "clip count read-back");
+    const long long need = (long long)*h->h_clips;
+    if (need <= cap) return PIKO_OK;
+    if (attempt > 0) return fail(h, PIKO_ERR_OVERFLOW, "clipped triangle list too large");
+    want = need + need / 8 + 1024;
+    if ((e = cudaMemsetAsync(h->status, 0, sizeof(unsigned) * 2, st)) != cudaSuccess)
+      return cuda_fail(h, e, "status clear");
+  }
+}
+
 // The fused (no tiling) and unfused (one kernel per stage) mappings, after
 // the vertex stage.  Stage events: 2 after the rasterizer, 3 after shading
 // (fused: the per-pixel pass; unfused: the fragment shader), 4 after the
@@ -310,6 +356,10 @@ static int forward_other_mapping(piko_raster* h, const piko_scene* s, piko_frame
   in.galb = reinterpret_cast<uint2*>(fb->gbuf_albedo);
   in.st = h->status;
   in.frag_pix = nullptr; in.frag_key = nullptr; in.frag_rgba = nullptr; in.frag_cap = 0;
+  in.pos = s->pos; in.mvp = s->mvp;
+  in.clip_tris = h->clip ? h->clip_tris : nullptr;
+  in.clip_orig = h->clip ? h->clip_orig : nullptr;
+  in.clip_cap = h->clip ? (unsigned)(h->ccap_tris < h->ccap_orig ? h->ccap_tris : h->ccap_orig) : 0u;
   const bool persp = h->perspective != 0;
   const size_t key_bytes = sizeof(unsigned long long) * (size_t)h->W * h->H;
   int r;
@@ -393,12 +443,17 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
   if (h->stats) cudaMemsetAsync(&h->status->tests, 0, 4 * sizeof(unsigned long long), st);
   launch_vertex(h->W, h->H, V, s->pos, s->mvp, h->vtx, lambert ? s->normal : nullptr, s->light_dir,
                 lambert ? h->vdot : nullptr, h->perspective ? h->invw : nullptr, h->num_sms, st);
+  if (h->clip && (r = clip_pass(h, s, st)) != PIKO_OK) return r;
+  const int4* clip_tris = h->clip ? h->clip_tris : nullptr;
+  const unsigned clip_cap = h->clip ? (unsigned)(h->ccap_tris < h->ccap_orig ? h->ccap_tris : h->ccap_orig) : 0u;
+  if (clip_cap && (r = grow(h, &h->rect, &h->tcap, (long long)T + clip_cap, "bin rectangles")) != PIKO_OK) return r;
   if (ev) cudaEventRecord(h->stage_ev[1], st);
   if (h->schedule == PIKO_SCHED_FUSED || h->schedule == PIKO_SCHED_UNFUSED)
     return forward_other_mapping(h, s, fb, st, ev);
   for (int attempt = 0;; ++attempt) {
     if (h->stats && attempt > 0) cudaMemsetAsync(&h->status->binned, 0, sizeof(unsigned long long), st);
-    launch_setup_count(h->g, T, s->tris, V, h->vtx, h->rect, h->bin_count, h->status, h->stats, h->num_sms, st);
+    launch_setup_count(h->g, T, s->tris, V, h->vtx, h->rect, h->bin_count, h->status, h->stats, h->num_sms, st,
+                       clip_tris, clip_cap);
     if (ev) cudaEventRecord(h->stage_ev[2], st);
     launch_scan(h->nbins, h->bin_count, h->bin_off, h->cursor, (unsigned long long)h->ecap, h->status,
                 h->chunk_state, ++h->scan_epoch, st, h->wait_budget, h->withhold);
@@ -417,7 +472,7 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
     if (e != cudaSuccess) return cuda_fail(h, e, "status clear");
   }
   launch_scatter(h->g, T, h->rect, h->bin_off, h->cursor, h->bin_tris, (unsigned long long)h->ecap, h->status,
-                 h->num_sms, st);
+                 h->num_sms, st, clip_tris, clip_cap);
   if (ev) cudaEventRecord(h->stage_ev[4], st);
 
   ProcessParams p;
@@ -440,6 +495,10 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
   p.light = s->light_dir;
   p.vdot = h->vdot;
   p.invw = h->perspective ? h->invw : nullptr;
+  p.clip_tris = clip_tris;
+  p.clip_orig = h->clip ? h->clip_orig : nullptr;
+  p.pos = s->pos;
+  p.mvp = s->mvp;
   p.bin_off = h->bin_off;
   p.bin_tris = h->bin_tris;
   p.key_out = reinterpret_cast<unsigned long long*>(fb->key);
@@ -466,6 +525,7 @@ int piko_raster_forward_batch(piko_raster* h, const piko_scene* scenes, int n, p
   if (!h) return PIKO_ERR_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
   h->last_stream = st;
+  if (h->clip) return fail(h, PIKO_ERR_INVALID_ARG, "near/far clipping is available for single scenes only");
   // the batch deals tiles inside one launch: the other mappings fall back to its dynamic schedule
   const int dsched = h->schedule > PIKO_SCHED_HARDWARE ? PIKO_SCHED_DYNAMIC : h->schedule;
   int r = batch_prepare(h->batch, h->num_sms, scenes, n, fbs, bin_sizes, schedules, h->bin_w, h->bin_h, dsched,
@@ -549,7 +609,8 @@ int piko_raster_backward(piko_raster* h, const piko_scene* s, const piko_framebu
   launch_vertex(h->W, h->H, s->num_vertices, s->pos, s->mvp, h->vtx, nullptr, nullptr, nullptr, invw, h->num_sms,
                 st);
   if (piko_backward_launch(h->W, h->H, s->shade_mode, h->unclamped, s->num_triangles, s->num_vertices, s->tris,
-                           h->vtx, s->color, s->normal, s->light_dir, invw, reinterpret_cast<const unsigned long long*>(fwd->key), dl_drgba, dl_dcolor,
+                           h->vtx, s->color, s->normal, s->light_dir, invw, h->clip ? s->pos : nullptr, s->mvp,
+                           reinterpret_cast<const unsigned long long*>(fwd->key), dl_drgba, dl_dcolor,
                            dl_dnormal, dl_dlight, h->num_sms, st) != 0)
     return cuda_fail(h, cudaGetLastError(), "backward launch");
   return PIKO_OK;

@@ -28,6 +28,8 @@ __global__ void __launch_bounds__(BWD_THREADS, 1024 / BWD_THREADS) k_backward(Ba
   if (p.sc.dlight && p.sc.mode == PIKO_SHADE_LAMBERT) bwd_flush_light(sm, p.sc.dlight, gl0, gl1, gl2);
 }
 
+// A winner the vertex stage rejected was clipped (near/far clipping on, pos
+// set): its weights are the clip-space ray weights of the pixel centre.
 // Per-pixel form, for scenes of tiny triangles (a tile would hold nearly as
 // many triangles as pixels, so the tile form's shared table buys nothing):
 // each warp takes 32 consecutive pixels; lanes whose pixels share a winning
@@ -42,6 +44,8 @@ struct PixelBwdParams {
   const float* normal;
   const float* light;
   const float* invw;
+  const float4* pos;  // near/far clipping: positions and matrix of clipped winners (NULL: off)
+  const float* mvp;
   const unsigned long long* key;
   const float4* dl_drgba;
   float* dcolor;
@@ -76,10 +80,16 @@ __global__ void __launch_bounds__(PIX_THREADS) k_backward_pixel(PixelBwdParams p
     bool hit = k != KEY_EMPTY && (unsigned)(k & 0xFFFFFFFFu) < (unsigned)p.T;
     unsigned t = hit ? (unsigned)(k & 0xFFFFFFFFu) : 0xFFFFFFFFu;
     TriSetup s;
+    bool clipped = false;
     if (hit) {
       const int ia = __ldg(p.tris + 3 * (size_t)t), ib = __ldg(p.tris + 3 * (size_t)t + 1),
                 ic = __ldg(p.tris + 3 * (size_t)t + 2);
-      hit = ia >= 0 && ia < p.V && ib >= 0 && ib < p.V && ic >= 0 && ic < p.V && setup_triangle(ia, ib, ic, p.vtx, s);
+      const bool in_range = ia >= 0 && ia < p.V && ib >= 0 && ib < p.V && ic >= 0 && ic < p.V;
+      hit = in_range && setup_triangle(ia, ib, ic, p.vtx, s);
+      if (!hit && in_range && p.pos) {  // a winner the vertex stage rejected was clipped
+        clipped = hit = true;
+        s.v0 = ia; s.v1 = ib; s.v2 = ic;
+      }
       if (!hit) t = 0xFFFFFFFFu;
     }
     float v[PIX_VALS];
@@ -89,14 +99,21 @@ __global__ void __launch_bounds__(PIX_THREADS) k_backward_pixel(PixelBwdParams p
     if (hit) {
       const int y = i / p.W, x = i - y * p.W;
       vid[0] = s.v0; vid[1] = s.v1; vid[2] = s.v2;
-      const long long Px = 256LL * x + 128, Py = 256LL * y + 128;
-      const long long w0 = (long long)(s.X2 - s.X1) * (Py - s.Y1) - (long long)(s.Y2 - s.Y1) * (Px - s.X1);
-      const long long w1 = (long long)(s.X0 - s.X2) * (Py - s.Y2) - (long long)(s.Y0 - s.Y2) * (Px - s.X2);
-      const long long w2 = (long long)(s.X1 - s.X0) * (Py - s.Y0) - (long long)(s.Y1 - s.Y0) * (Px - s.X0);
-      const float fA = f32_from_i64(s.A);
-      float b[3] = {__fdiv_rn(f32_from_i64(w0), fA), __fdiv_rn(f32_from_i64(w1), fA), __fdiv_rn(f32_from_i64(w2), fA)};
-      if (PERSP)
-        perspective_bary(b[0], b[1], b[2], __ldg(p.invw + vid[0]), __ldg(p.invw + vid[1]), __ldg(p.invw + vid[2]));
+      float b[3];
+      if (clipped) {
+        clip_ray_weights(p.pos, p.mvp, p.W, p.H, vid, x, y, b[0], b[1], b[2]);
+      } else {
+        const long long Px = 256LL * x + 128, Py = 256LL * y + 128;
+        const long long w0 = (long long)(s.X2 - s.X1) * (Py - s.Y1) - (long long)(s.Y2 - s.Y1) * (Px - s.X1);
+        const long long w1 = (long long)(s.X0 - s.X2) * (Py - s.Y2) - (long long)(s.Y0 - s.Y2) * (Px - s.X2);
+        const long long w2 = (long long)(s.X1 - s.X0) * (Py - s.Y0) - (long long)(s.Y1 - s.Y0) * (Px - s.X0);
+        const float fA = f32_from_i64(s.A);
+        b[0] = __fdiv_rn(f32_from_i64(w0), fA);
+        b[1] = __fdiv_rn(f32_from_i64(w1), fA);
+        b[2] = __fdiv_rn(f32_from_i64(w2), fA);
+        if (PERSP)
+          perspective_bary(b[0], b[1], b[2], __ldg(p.invw + vid[0]), __ldg(p.invw + vid[1]), __ldg(p.invw + vid[2]));
+      }
       const float4 g = __ldg(p.dl_drgba + i);
       if (p.mode == PIKO_SHADE_GOURAUD) {
 #pragma unroll
@@ -214,7 +231,7 @@ using namespace piko;
 
 int piko_backward_launch(int W, int H, int mode, int unclamped, int T, int V, const int* tris, const int4* vtx,
                          const float* color, const float* normal, const float* light, const float* invw,
-                         const unsigned long long* key,
+                         const float* pos, const float* mvp, const unsigned long long* key,
                          const float* dl_drgba, float* dcolor, float* dnormal, float* dlight, int num_sms,
                          cudaStream_t s) {
   const long long npix = (long long)W * H;
@@ -223,6 +240,7 @@ int piko_backward_launch(int W, int H, int mode, int unclamped, int T, int V, co
     PixelBwdParams p;
     p.W = W; p.H = H; p.mode = mode; p.unclamped = unclamped; p.T = T; p.V = V;
     p.tris = tris; p.vtx = vtx; p.color = color; p.normal = normal; p.light = light; p.invw = invw;
+    p.pos = reinterpret_cast<const float4*>(pos); p.mvp = mvp;
     p.key = key; p.dl_drgba = reinterpret_cast<const float4*>(dl_drgba);
     p.dcolor = dcolor; p.dnormal = dnormal; p.dlight = dlight;
     long long blocks = (npix + PIX_THREADS - 1) / PIX_THREADS;
@@ -238,6 +256,7 @@ int piko_backward_launch(int W, int H, int mode, int unclamped, int T, int V, co
   BwdScene& c = p.sc;
   c.W = W; c.H = H; c.mode = mode; c.unclamped = unclamped; c.T = T; c.V = V;
   c.tris = tris; c.vtx = vtx; c.color = color; c.normal = normal; c.light = light; c.invw = invw;
+  c.pos = reinterpret_cast<const float4*>(pos); c.mvp = mvp;
   c.key = key; c.dl = reinterpret_cast<const float4*>(dl_drgba);
   c.dcolor = dcolor; c.dnormal = dnormal; c.dlight = dlight;
   p.ntx = (W + BWD_TILE_W - 1) / BWD_TILE_W;

@@ -348,6 +348,11 @@ __device__ void load_tile_scene(const BatchParams& b, int s, TileScene& t) {
   t.light = d.light;
   t.vdot = b.vdot + d.vtx_base;
   t.invw = b.invw ? b.invw + d.vtx_base : nullptr;
+  t.T = d.T;
+  t.clip_tris = nullptr;  // batches do not clip
+  t.clip_orig = nullptr;
+  t.pos = nullptr;
+  t.mvp = nullptr;
   t.key_out = d.key_out;
   t.rgba_out = d.rgba_out;
   t.gnorm_out = d.gnorm_out;
@@ -480,6 +485,8 @@ __global__ void __launch_bounds__(BWD_THREADS, 1024 / BWD_THREADS) k_batch_backw
     c.W = d.g.W; c.H = d.g.H; c.mode = d.mode; c.unclamped = d.unclamped; c.T = d.T; c.V = d.V;
     c.tris = d.tris; c.vtx = b.vtx + d.vtx_base; c.color = d.color; c.normal = d.normal; c.light = d.light;
     c.invw = b.invw ? b.invw + d.vtx_base : nullptr;
+    c.pos = nullptr;  // batches do not clip
+    c.mvp = nullptr;
     c.key = d.key_out; c.dl = d.dl; c.dcolor = d.dcolor; c.dnormal = d.dnormal; c.dlight = d.dlight;
     float L0 = 0.f, L1 = 0.f, L2 = 0.f;
     if (c.mode == PIKO_SHADE_LAMBERT) {

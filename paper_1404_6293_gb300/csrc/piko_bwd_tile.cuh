@@ -60,6 +60,8 @@ struct BwdScene {
   const float* normal;
   const float* light;
   const float* invw;  // 1 / clip w per vertex: perspective-correct attributes (NULL: screen-space)
+  const float4* pos;  // near/far clipping: positions and matrix of clipped winners (NULL: off)
+  const float* mvp;
   const unsigned long long* key;
   const float4* dl;
   float* dcolor;
@@ -185,9 +187,23 @@ __device__ __forceinline__ void backward_tile(const BwdScene& sc, int x0, int y0
     const int ia = __ldg(sc.tris + 3 * (size_t)tri), ib = __ldg(sc.tris + 3 * (size_t)tri + 1),
               ic = __ldg(sc.tris + 3 * (size_t)tri + 2);
     TriSetup ts;
-    const bool ok = ia >= 0 && ia < sc.V && ib >= 0 && ib < sc.V && ic >= 0 && ic < sc.V &&
-                    setup_triangle(ia, ib, ic, sc.vtx, ts);
-    r[RB_OK] = ok ? 1 : 0;
+    const bool in_range = ia >= 0 && ia < sc.V && ib >= 0 && ib < sc.V && ic >= 0 && ic < sc.V;
+    const bool ok = in_range && setup_triangle(ia, ib, ic, sc.vtx, ts);
+    // a winner the vertex stage rejected was clipped: per-pixel ray weights (2)
+    const bool clipped = !ok && in_range && sc.pos;
+    r[RB_OK] = ok ? 1 : (clipped ? 2 : 0);
+    if (clipped) {
+      ts.v0 = ia; ts.v1 = ib; ts.v2 = ic;
+      r[RB_V] = ia; r[RB_V + 1] = ib; r[RB_V + 2] = ic;
+      if (sc.mode == PIKO_SHADE_LAMBERT) {
+        const int vid[3] = {ia, ib, ic};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const float* nn = sc.normal + 3 * (size_t)vid[j];
+          r[RB_VD + j] = __float_as_int(__ldg(nn) * L0 + __ldg(nn + 1) * L1 + __ldg(nn + 2) * L2);
+        }
+      }
+    }
     if (ok) {
       r[0] = ts.X0; r[1] = ts.Y0; r[2] = ts.X1; r[3] = ts.Y1; r[4] = ts.X2; r[5] = ts.Y2;
       r[RB_V] = ts.v0; r[RB_V + 1] = ts.v1; r[RB_V + 2] = ts.v2;
@@ -225,7 +241,9 @@ __device__ __forceinline__ void backward_tile(const BwdScene& sc, int x0, int y0
     const int vid[3] = {r[RB_V], r[RB_V + 1], r[RB_V + 2]};
     const float rA = __int_as_float(r[RB_T]);
     float b[3];
-    if (A < (1LL << 31)) {
+    if (r[RB_OK] == 2) {
+      clip_ray_weights(sc.pos, sc.mvp, sc.W, sc.H, vid, x, y, b[0], b[1], b[2]);
+    } else if (A < (1LL << 31)) {
       // the pixel is covered: its edge functions lie in [0, A], exact in wrapping 32-bit arithmetic
       const int Px = 256 * x + 128, Py = 256 * y + 128;
       const int w1 = edge_fn_wrap32(X2, Y2, X0, Y0, Px, Py), w2 = edge_fn_wrap32(X0, Y0, X1, Y1, Px, Py);
@@ -238,7 +256,7 @@ __device__ __forceinline__ void backward_tile(const BwdScene& sc, int x0, int y0
       const long long w0 = A - w1 - w2;
       b[0] = f32_from_i64(w0) * rA; b[1] = f32_from_i64(w1) * rA; b[2] = f32_from_i64(w2) * rA;
     }
-    if (PERSP)
+    if (PERSP && r[RB_OK] == 1)
       perspective_bary(b[0], b[1], b[2], __ldg(sc.invw + vid[0]), __ldg(sc.invw + vid[1]), __ldg(sc.invw + vid[2]));
     const float4 g = __ldg(sc.dl + o);
     if (sc.mode == PIKO_SHADE_GOURAUD) {

@@ -1,6 +1,7 @@
 // piko_forward.cu -- forward kernels of the binned rasterizer.
 //
 //   k_vertex       vertex stage: transform, divide, viewport, 16.8 snap (Sec. 7.1, Vertex Shader)
+//   k_clip         near/far clipping of the triangles that cross z = -w or z = w (optional)
 //   k_setup_count  triangle setup + AssignBin to bounding-box bins, per-bin counts
 //                  (AssignToBoundingBox directive, Sec. 4.3; bin lists of Sec. 6)
 //   k_scan         exclusive prefix sum of the counts into CSR offsets (the order-preserving
@@ -60,6 +61,118 @@ void launch_vertex(int W, int H, int V, const float* pos, const float* mvp, int4
   else
     k_vertex<false><<<blocks, 256, 0, s>>>(W, H, V, reinterpret_cast<const float4*>(pos), mvp, vtx, normal, light,
                                            vdot, nullptr);
+}
+
+// ======================================================================
+// Near/far clipping (optional).  A triangle with a vertex the vertex stage
+// rejected is clipped in clip space against z + w >= 0 and then w - z >= 0
+// (Sutherland-Hodgman over its edges in order from vertex 0; the crossing
+// point a + t (b - a), t = d_a / (d_a - d_b), every operation rounded, no
+// fused multiply-add); the polygon (3 to 5 points) is fanned from its first
+// point; each sub-triangle whose points snap inside the guard band (w > 0,
+// Z clamped to [0, 2^24 - 1]) is appended to the sub-triangle list with
+// the index of its triangle.  The triangle itself stays culled.
+// ======================================================================
+struct ClipPt {
+  float c[4];
+};
+
+__device__ __forceinline__ int clip_plane_pts(const ClipPt* in, int n, ClipPt* out, int plane) {
+  int m = 0;
+  for (int k = 0; k < n; ++k) {
+    const ClipPt& a = in[k];
+    const ClipPt& b = in[k + 1 < n ? k + 1 : 0];
+    const float da = plane == 0 ? __fadd_rn(a.c[2], a.c[3]) : __fsub_rn(a.c[3], a.c[2]);
+    const float db = plane == 0 ? __fadd_rn(b.c[2], b.c[3]) : __fsub_rn(b.c[3], b.c[2]);
+    const bool ina = da >= 0.0f, inb = db >= 0.0f;
+    if (ina) out[m++] = a;
+    if (ina != inb) {
+      const float t = __fdiv_rn(da, __fsub_rn(da, db));
+      ClipPt v;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v.c[q] = __fadd_rn(a.c[q], __fmul_rn(t, __fsub_rn(b.c[q], a.c[q])));
+      out[m++] = v;
+    }
+  }
+  return m;
+}
+
+// divide, viewport and snap of a clipped point: {X, Y, Z, 1}, or false
+__device__ __forceinline__ bool snap_clipped(const ClipPt& p, float fW, float fH, int4& o) {
+  const float w = p.c[3];
+  if (!(w > 0.0f)) return false;
+  const float nx = __fdiv_rn(p.c[0], w), ny = __fdiv_rn(p.c[1], w), nz = __fdiv_rn(p.c[2], w);
+  const float sx = __fmul_rn(__fadd_rn(__fmul_rn(nx, 0.5f), 0.5f), fW);
+  const float sy = __fmul_rn(__fsub_rn(0.5f, __fmul_rn(ny, 0.5f)), fH);
+  const float sz = __fmul_rn(__fadd_rn(__fmul_rn(nz, 0.5f), 0.5f), 16777215.0f);
+  const float fx = __fmul_rn(sx, 256.0f), fy = __fmul_rn(sy, 256.0f);
+  if (!(fabsf(fx) < 8388608.0f && fabsf(fy) < 8388608.0f)) return false;
+  float zr = rintf(sz);
+  if (!(zr >= 0.0f)) zr = 0.0f;  // NaN, or below the near plane by rounding
+  if (zr > 16777215.0f) zr = 16777215.0f;
+  o = make_int4(__float2int_rn(fx), __float2int_rn(fy), (int)zr, 1);
+  return true;
+}
+
+__global__ void __launch_bounds__(256) k_clip(int W, int H, int T, const int* __restrict__ tris, int V,
+                                              const float4* __restrict__ pos, const float* __restrict__ mvp,
+                                              const int4* __restrict__ vtx, int4* __restrict__ clip_tris,
+                                              unsigned* __restrict__ clip_orig, unsigned cap, DevStatus* st) {
+  pdl_wait();  // snapped vertices
+  pdl_launch_dependents();
+  const float fW = (float)W, fH = (float)H;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+    const int i0 = __ldg(tris + 3 * (size_t)t), i1 = __ldg(tris + 3 * (size_t)t + 1),
+              i2 = __ldg(tris + 3 * (size_t)t + 2);
+    if ((unsigned)i0 >= (unsigned)V || (unsigned)i1 >= (unsigned)V || (unsigned)i2 >= (unsigned)V) continue;
+    if (__ldg(vtx + i0).w & __ldg(vtx + i1).w & __ldg(vtx + i2).w) continue;  // nothing to clip
+    ClipPt p[8], q[8];
+    const int id[3] = {i0, i1, i2};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float4 v = __ldg(pos + id[k]);
+      if (mvp) {
+        p[k].c[0] = mvp_row(mvp + 0, v); p[k].c[1] = mvp_row(mvp + 4, v);
+        p[k].c[2] = mvp_row(mvp + 8, v); p[k].c[3] = mvp_row(mvp + 12, v);
+      } else {
+        p[k].c[0] = v.x; p[k].c[1] = v.y; p[k].c[2] = v.z; p[k].c[3] = v.w;
+      }
+    }
+    int n = clip_plane_pts(p, 3, q, 0);
+    n = clip_plane_pts(q, n, p, 1);
+    for (int k = 1; k + 1 < n; ++k) {
+      int4 a, b, c;
+      if (!snap_clipped(p[0], fW, fH, a) || !snap_clipped(p[k], fW, fH, b) || !snap_clipped(p[k + 1], fW, fH, c))
+        continue;
+      const unsigned slot = atomicAdd(&st->clip_count, 1u);
+      if (slot < cap) {
+        clip_tris[3 * (size_t)slot] = a;
+        clip_tris[3 * (size_t)slot + 1] = b;
+        clip_tris[3 * (size_t)slot + 2] = c;
+        clip_orig[slot] = (unsigned)t;
+      } else {
+        record_error(st, PIKO_ERR_OVERFLOW);
+      }
+    }
+  }
+}
+
+void launch_clip(int W, int H, int T, const int* tris, int V, const float* pos, const float* mvp, const int4* vtx,
+                 int4* clip_tris, unsigned* clip_orig, unsigned cap, DevStatus* st, int num_sms, cudaStream_t s) {
+  if (T <= 0) return;
+  long long blocks = (T + 255) / 256;
+  if (blocks > 8LL * num_sms) blocks = 8LL * num_sms;
+  launch_pdl(k_clip, (int)blocks, 256, 0, s, W, H, T, tris, V, reinterpret_cast<const float4*>(pos), mvp, vtx,
+             clip_tris, clip_orig, cap, st);
+}
+
+// Triangles of the frame: the input ones, then the clipped sub-triangles
+// (when clipping is on).  How many sub-triangles there are is known on the
+// device only, after the clip pass.
+__device__ __forceinline__ int frame_triangles(int T, const int4* clip_tris, unsigned clip_cap, const DevStatus* st) {
+  if (!clip_tris) return T;
+  const unsigned n = *reinterpret_cast<const volatile unsigned*>(&st->clip_count);
+  return T + (int)(n < clip_cap ? n : clip_cap);
 }
 
 // ======================================================================
@@ -211,7 +324,8 @@ __device__ __forceinline__ void count_batch(const RasterGeom& g, int T, int t, i
 __global__ void __launch_bounds__(256) k_setup_count(RasterGeom g, int T, const int* __restrict__ tris, int V,
                                                      const int4* __restrict__ vtx, BinRect* __restrict__ rect,
                                                      unsigned* __restrict__ cnt, int nbins, DevStatus* st,
-                                                     int stats) {
+                                                     int stats, const int4* __restrict__ clip_tris,
+                                                     unsigned clip_cap) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   // the vertex stage does not touch the status word, and everything before
   // it has completed (it is launched without the early-start attribute)
@@ -224,10 +338,17 @@ __global__ void __launch_bounds__(256) k_setup_count(RasterGeom g, int T, const 
   // CTAs fit an SM, and the other warps hide the gathers' latency (two
   // batches in flight per warp needed 48 registers, five CTAs, and ran 2%
   // slower end to end)
-  for (int base = (blockIdx.x * (blockDim.x >> 5) + wib) * 32; base < T; base += step) {
-    const int3 ia = load_tri(tris, T, base + lane);
-    const TriVerts va = gather_verts(ia, V, vtx, base + lane < T);
-    count_batch(g, T, base + lane, ia, va, rect, cnt, nbins, st, stats, lane, lt_mask);
+  const int TT = frame_triangles(T, clip_tris, clip_cap, st);
+  for (int base = (blockIdx.x * (blockDim.x >> 5) + wib) * 32; base < TT; base += step) {
+    const int t = base + lane;
+    const int3 ia = load_tri(tris, T, t);
+    TriVerts va = gather_verts(ia, V, vtx, t < T);
+    if (t >= T && t < TT) {  // a clipped sub-triangle: its snapped points
+      const int4* c = clip_tris + 3 * (size_t)(t - T);
+      va.p0 = c[0]; va.p1 = c[1]; va.p2 = c[2];
+      va.in_range = true;
+    }
+    count_batch(g, TT, t, ia, va, rect, cnt, nbins, st, stats, lane, lt_mask);
   }
 }
 
@@ -243,13 +364,16 @@ static int resident_per_sm(K kernel, int threads) {
 }
 
 void launch_setup_count(const RasterGeom& g, int T, const int* tris, int V, const int4* vtx, BinRect* rect,
-                        unsigned* bin_count, DevStatus* st, int stats, int num_sms, cudaStream_t s) {
+                        unsigned* bin_count, DevStatus* st, int stats, int num_sms, cudaStream_t s,
+                        const int4* clip_tris, unsigned clip_cap) {
   static const int per_sm = resident_per_sm(k_setup_count, 256);
-  int warps = (T + 31) / 32;
+  const long long TT = (long long)T + (clip_tris ? clip_cap : 0u);
+  int warps = (int)((TT + 31) / 32);
   int blocks = (warps + 7) / 8;
   blocks = blocks < num_sms * per_sm ? blocks : num_sms * per_sm;
   if (blocks < 1) blocks = 1;  // with no triangles the kernel still resets the scan ticket
-  launch_pdl(k_setup_count, blocks, 256, 0, s, g, T, tris, V, vtx, rect, bin_count, g.nbx * g.nby, st, stats);
+  launch_pdl(k_setup_count, blocks, 256, 0, s, g, T, tris, V, vtx, rect, bin_count, g.nbx * g.nby, st, stats,
+             clip_tris, clip_cap);
 }
 
 void launch_scan(int nbins, unsigned* bin_count, unsigned* bin_off, unsigned* cursor, unsigned long long capacity,
@@ -300,10 +424,12 @@ __device__ __forceinline__ unsigned single_pos(const RasterGeom& g, BinRect r, c
 __global__ void __launch_bounds__(256) k_scatter(RasterGeom g, int T, const BinRect* __restrict__ rect,
                                                  const unsigned* __restrict__ bin_off,
                                                  unsigned* __restrict__ cursor, unsigned* __restrict__ bin_tris,
-                                                 unsigned long long capacity, const DevStatus* st) {
+                                                 unsigned long long capacity, const DevStatus* st,
+                                                 const int4* __restrict__ clip_tris, unsigned clip_cap) {
   pdl_wait();  // offsets, cursors and the status of the scan
   pdl_launch_dependents();
   if (st->flags & STATUS_SKIP_MASK) return;
+  T = frame_triangles(T, clip_tris, clip_cap, st);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int step = gridDim.x * (blockDim.x >> 5) * 32;
   BinRect none;
@@ -321,13 +447,16 @@ __global__ void __launch_bounds__(256) k_scatter(RasterGeom g, int T, const BinR
 }
 
 void launch_scatter(const RasterGeom& g, int T, const BinRect* rect, const unsigned* bin_off, unsigned* cursor,
-                    unsigned* bin_tris, unsigned long long capacity, DevStatus* st, int num_sms, cudaStream_t s) {
-  if (T <= 0) return;
+                    unsigned* bin_tris, unsigned long long capacity, DevStatus* st, int num_sms, cudaStream_t s,
+                    const int4* clip_tris, unsigned clip_cap) {
+  const long long TT = (long long)T + (clip_tris ? clip_cap : 0u);
+  if (TT <= 0) return;
   static const int per_sm = resident_per_sm(k_scatter, 256);
-  int warps = (T + 31) / 32;
+  int warps = (int)((TT + 31) / 32);
   int blocks = (warps + 7) / 8;
   blocks = blocks < num_sms * per_sm ? blocks : num_sms * per_sm;
-  launch_pdl(k_scatter, blocks, 256, 0, s, g, T, rect, bin_off, cursor, bin_tris, capacity, st);
+  launch_pdl(k_scatter, blocks, 256, 0, s, g, T, rect, bin_off, cursor, bin_tris, capacity, st, clip_tris,
+             clip_cap);
 }
 
 }  // namespace piko

@@ -52,7 +52,7 @@ struct DevStatus {
   unsigned int queue_head;      // tile counter of the dynamic schedule
   unsigned int scan_ticket;     // next chunk number of the scan (reset by its last chunk)
   unsigned int frag_count;      // fragments emitted by the unfused pipeline's rasterizer
-  unsigned int pad;
+  unsigned int clip_count;      // sub-triangles appended by the clip pass
   unsigned long long tests;     // statistics (PIKO_OPT_STATS): pixel samples tested
   unsigned long long frags;     // covered samples
   unsigned long long shaded;    // covered pixels after the depth test
@@ -140,6 +140,24 @@ __device__ __forceinline__ bool setup_triangle(int a, int b, int c, const int4* 
     s.A = -A;
   }
   return true;
+}
+
+// Orients a triangle given by three snapped points {X, Y, Z, valid} (a
+// clipped sub-triangle); false if A == 0.  Vertex indices are not known.
+__device__ __forceinline__ bool setup_points(int4 p0, int4 p1, int4 p2, TriSetup& s) {
+  long long A = (long long)(p1.x - p0.x) * (long long)(p2.y - p0.y) -
+                (long long)(p2.x - p0.x) * (long long)(p1.y - p0.y);
+  s.X0 = p0.x; s.Y0 = p0.y; s.Z0 = p0.z; s.v0 = s.v1 = s.v2 = 0;
+  if (A >= 0) {
+    s.X1 = p1.x; s.Y1 = p1.y; s.Z1 = p1.z;
+    s.X2 = p2.x; s.Y2 = p2.y; s.Z2 = p2.z;
+    s.A = A;
+  } else {
+    s.X1 = p2.x; s.Y1 = p2.y; s.Z1 = p2.z;
+    s.X2 = p1.x; s.Y2 = p1.y; s.Z2 = p1.z;
+    s.A = -A;
+  }
+  return A != 0;
 }
 
 // Pixel columns / rows whose centres lie inside [min, max] of the snapped
@@ -267,6 +285,42 @@ __device__ __forceinline__ int4 snap_vertex(float4 p, const float* m, float fW, 
   return o;
 }
 
+// Weights of a clipped triangle's vertices v[3] at pixel (x, y) of a W x H
+// framebuffer: the clip-space weights of the point where the pixel centre's
+// ray meets the triangle's plane.  With a_i = X_i - x W_i and c_i = Y_i -
+// y W_i (clip coordinates of vertex i from the float32 transform, NDC (x, y)
+// of the centre) the weights satisfy a . b = c . b = 0 and sum b = 1, so
+// b = (a x c) / sum(a x c).  Float64 (a rare path, and the products cancel).
+__device__ __forceinline__ void clip_ray_weights(const float4* pos, const float* mvp, int W, int H, const int v[3],
+                                                 int x, int y, float& b0, float& b1, float& b2) {
+  const double xn = __dsub_rn(__dmul_rn(__ddiv_rn((double)x + 0.5, (double)W), 2.0), 1.0);
+  const double yn = __dsub_rn(1.0, __dmul_rn(__ddiv_rn((double)y + 0.5, (double)H), 2.0));
+  double a[3], c[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float4 q = __ldg(pos + v[k]);
+    float cx = q.x, cy = q.y, cw = q.w;
+    if (mvp) {
+      cx = mvp_row(mvp + 0, q);
+      cy = mvp_row(mvp + 4, q);
+      cw = mvp_row(mvp + 12, q);
+    }
+    a[k] = __dsub_rn((double)cx, __dmul_rn(xn, (double)cw));
+    c[k] = __dsub_rn((double)cy, __dmul_rn(yn, (double)cw));
+  }
+  const double n0 = __dsub_rn(__dmul_rn(a[1], c[2]), __dmul_rn(a[2], c[1]));
+  const double n1 = __dsub_rn(__dmul_rn(a[2], c[0]), __dmul_rn(a[0], c[2]));
+  const double n2 = __dsub_rn(__dmul_rn(a[0], c[1]), __dmul_rn(a[1], c[0]));
+  const double sum = __dadd_rn(__dadd_rn(n0, n1), n2);
+  if (sum != 0.0) {
+    b0 = (float)__ddiv_rn(n0, sum);
+    b1 = (float)__ddiv_rn(n1, sum);
+    b2 = (float)__ddiv_rn(n2, sum);
+  } else {
+    b0 = b1 = b2 = 1.0f / 3.0f;
+  }
+}
+
 // --------------------------------------------------------------- kernels
 // Records wanted for a scene whose bin lists hold `entries` entries over
 // `tiles` tiles: 1.4 x the mean, in multiples of 32 (1.4 x covers the
@@ -297,6 +351,10 @@ struct ProcessParams {
   const float* light;
   const float* vdot;  // n_v . L per vertex (Lambert)
   const float* invw;  // 1 / clip w per vertex: perspective-correct attributes (NULL: screen-space)
+  const int4* clip_tris;   // near/far clipping: sub-triangles (NULL: off)
+  const unsigned* clip_orig;
+  const float* pos;        // the scene's positions and matrix (clipped winners' shading)
+  const float* mvp;
   const unsigned* bin_off;
   const unsigned* bin_tris;
   unsigned long long* key_out;
@@ -315,8 +373,16 @@ void launch_vertex(int W, int H, int V, const float* pos, const float* mvp, int4
 // (single-bin and multi-bin entries), zero between frames; the scan turns
 // them into CSR offsets and scatter cursors (capacity: entries the bin lists
 // can hold; above it PIKO_ERR_OVERFLOW is recorded).
+// With clipping, clip_tris / clip_cap describe the sub-triangle list of the
+// clip pass (triangles T.. of the frame); otherwise NULL / 0.
 void launch_setup_count(const RasterGeom& g, int T, const int* tris, int V, const int4* vtx,
-                        BinRect* rect, unsigned* bin_count, DevStatus* st, int stats, int num_sms, cudaStream_t s);
+                        BinRect* rect, unsigned* bin_count, DevStatus* st, int stats, int num_sms, cudaStream_t s,
+                        const int4* clip_tris = nullptr, unsigned clip_cap = 0);
+// Near/far clipping of the triangles with a rejected vertex: sub-triangles
+// (3 snapped points each) and their triangle's index appended at
+// st->clip_count (PIKO_ERR_OVERFLOW past cap).
+void launch_clip(int W, int H, int T, const int* tris, int V, const float* pos, const float* mvp, const int4* vtx,
+                 int4* clip_tris, unsigned* clip_orig, unsigned cap, DevStatus* st, int num_sms, cudaStream_t s);
 // chunk_state: scan_chunks(nbins) words, zero at allocation; epoch must
 // differ between consecutive scans on the same state array.  wait_budget:
 // clock cycles a look-back wait may take before PIKO_ERR_TIMEOUT; withhold:
@@ -326,7 +392,8 @@ void launch_scan(int nbins, unsigned* bin_count, unsigned* bin_off, unsigned* cu
                  long long wait_budget = 40000000, int withhold = 0);
 int scan_chunks(int nbins);
 void launch_scatter(const RasterGeom& g, int T, const BinRect* rect, const unsigned* bin_off, unsigned* cursor,
-                    unsigned* bin_tris, unsigned long long capacity, DevStatus* st, int num_sms, cudaStream_t s);
+                    unsigned* bin_tris, unsigned long long capacity, DevStatus* st, int num_sms, cudaStream_t s,
+                    const int4* clip_tris = nullptr, unsigned clip_cap = 0);
 cudaError_t launch_process(const ProcessParams& p, int threads, int grid, cudaStream_t s);
 cudaError_t process_occupancy(const ProcessParams& p, int threads, int* blocks_per_sm);
 
@@ -358,6 +425,11 @@ struct AltInputs {
   uint2* gnorm;
   uint2* galb;
   DevStatus* st;
+  const float* pos;                // positions and matrix (clipped winners' shading)
+  const float* mvp;
+  const int4* clip_tris;           // near/far clipping: sub-triangles (NULL: off)
+  const unsigned* clip_orig;
+  unsigned clip_cap;
   unsigned* frag_pix;              // fragment buffers (unfused): pixel, key, colour
   unsigned long long* frag_key;    //   (G-buffer mode: the colour slots hold the
   float4* frag_rgba;               //   normal and albedo halves)

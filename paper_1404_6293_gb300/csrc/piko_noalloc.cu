@@ -224,6 +224,10 @@ extern "C" int piko_raster_forward_noalloc(const piko_scene* s, piko_framebuffer
   p.light = s->light_dir;
   p.vdot = vdot;
   p.invw = nullptr;  // screen-space attributes only
+  p.clip_tris = nullptr;  // no clipping: out-of-range vertices cull their triangles
+  p.clip_orig = nullptr;
+  p.pos = s->pos;
+  p.mvp = s->mvp;
   p.bin_off = bin_off;
   p.bin_tris = bin_tris;
   p.key_out = reinterpret_cast<unsigned long long*>(fb->key);

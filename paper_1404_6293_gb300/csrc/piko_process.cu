@@ -25,6 +25,11 @@ __host__ __device__ inline TileScene scene_of(const ProcessParams& p) {
   sc.light = p.light;
   sc.vdot = p.vdot;
   sc.invw = p.invw;
+  sc.T = p.num_triangles;
+  sc.clip_tris = p.clip_tris;
+  sc.clip_orig = p.clip_orig;
+  sc.pos = p.clip_tris ? reinterpret_cast<const float4*>(p.pos) : nullptr;
+  sc.mvp = p.mvp;
   sc.key_out = p.key_out;
   sc.rgba_out = p.rgba_out;
   sc.gnorm_out = p.gnorm_out;

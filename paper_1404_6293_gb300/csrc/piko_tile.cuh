@@ -40,6 +40,15 @@ struct TileScene {
   const float* light;
   const float* vdot;
   const float* invw;  // 1 / clip w per vertex, or NULL for screen-space attributes
+  // near/far clipping: triangles T.. of the frame are clipped sub-triangles
+  // (3 snapped points each in clip_tris, their triangle in clip_orig); pos
+  // and mvp give a clipped winner's clip coordinates for shading (NULL: no
+  // clipping)
+  int T;
+  const int4* clip_tris;
+  const unsigned* clip_orig;
+  const float4* pos;
+  const float* mvp;
   unsigned long long* key_out;
   float4* rgba_out;
   uint2* gnorm_out;
@@ -343,23 +352,15 @@ __device__ __forceinline__ void shade_from_record(const TileScene& p, const int*
   p.galb_out[o] = pack_half4(c0, c1, c2, 1.0f);
 }
 
-// Fallback for winners without a record: everything re-read from global memory.
-template <bool PERSP>
-__device__ __forceinline__ void shade_from_global(const TileScene& p, unsigned t, int x, int y, size_t o) {
-  TriSetup s;
-  setup_triangle(__ldg(p.tris + 3 * (size_t)t), __ldg(p.tris + 3 * (size_t)t + 1), __ldg(p.tris + 3 * (size_t)t + 2),
-                 p.vtx, s);
-  const int Px = 256 * x + 128, Py = 256 * y + 128;
-  const long long w1 = (long long)(s.X0 - s.X2) * (Py - s.Y2) - (long long)(s.Y0 - s.Y2) * (Px - s.X2);
-  const long long w2 = (long long)(s.X1 - s.X0) * (Py - s.Y0) - (long long)(s.Y1 - s.Y0) * (Px - s.X0);
-  const float rA = approx_rcp(f32_from_i64(s.A));
-  float b1 = f32_from_i64(w1) * rA, b2 = f32_from_i64(w2) * rA, b0 = 1.0f - b1 - b2;
-  if (PERSP) perspective_bary(b0, b1, b2, __ldg(p.invw + s.v0), __ldg(p.invw + s.v1), __ldg(p.invw + s.v2));
+// Attributes of a winner with barycentrics (b0, b1, b2) over vertices
+// (v0, v1, v2), read from global memory, shaded and written at o.
+__device__ __forceinline__ void shade_vertices(const TileScene& p, int v0, int v1, int v2, float b0, float b1,
+                                               float b2, size_t o) {
   float c0 = 0.80f, c1 = 0.75f, c2 = 0.65f;
   if (p.color) {
-    const float* q0 = p.color + 3 * (size_t)s.v0;
-    const float* q1 = p.color + 3 * (size_t)s.v1;
-    const float* q2 = p.color + 3 * (size_t)s.v2;
+    const float* q0 = p.color + 3 * (size_t)v0;
+    const float* q1 = p.color + 3 * (size_t)v1;
+    const float* q2 = p.color + 3 * (size_t)v2;
     c0 = b0 * __ldg(q0) + b1 * __ldg(q1) + b2 * __ldg(q2);
     c1 = b0 * __ldg(q0 + 1) + b1 * __ldg(q1 + 1) + b2 * __ldg(q2 + 1);
     c2 = b0 * __ldg(q0 + 2) + b1 * __ldg(q1 + 2) + b2 * __ldg(q2 + 2);
@@ -368,9 +369,9 @@ __device__ __forceinline__ void shade_from_global(const TileScene& p, unsigned t
     if (p.rgba_out) p.rgba_out[o] = make_float4(c0, c1, c2, 1.0f);
     return;
   }
-  const float* n0 = p.normal + 3 * (size_t)s.v0;
-  const float* n1 = p.normal + 3 * (size_t)s.v1;
-  const float* n2 = p.normal + 3 * (size_t)s.v2;
+  const float* n0 = p.normal + 3 * (size_t)v0;
+  const float* n1 = p.normal + 3 * (size_t)v1;
+  const float* n2 = p.normal + 3 * (size_t)v2;
   const float nx = b0 * __ldg(n0) + b1 * __ldg(n1) + b2 * __ldg(n2);
   const float ny = b0 * __ldg(n0 + 1) + b1 * __ldg(n1 + 1) + b2 * __ldg(n2 + 1);
   const float nz = b0 * __ldg(n0 + 2) + b1 * __ldg(n1 + 2) + b2 * __ldg(n2 + 2);
@@ -382,6 +383,34 @@ __device__ __forceinline__ void shade_from_global(const TileScene& p, unsigned t
   float d = nx * __ldg(p.light) + ny * __ldg(p.light + 1) + nz * __ldg(p.light + 2);
   if (!p.unclamped) d = fmaxf(d, 0.0f);
   if (p.rgba_out) p.rgba_out[o] = make_float4(c0 * d, c1 * d, c2 * d, 1.0f);
+}
+
+// Fallback for winners without a record: everything re-read from global
+// memory.  A winner whose vertices the vertex stage rejected was clipped: it
+// shades with its clip-space ray weights (perspective-correct by
+// construction).
+template <bool PERSP>
+__device__ __forceinline__ void shade_from_global(const TileScene& p, unsigned t, int x, int y, size_t o) {
+  const int v[3] = {__ldg(p.tris + 3 * (size_t)t), __ldg(p.tris + 3 * (size_t)t + 1),
+                    __ldg(p.tris + 3 * (size_t)t + 2)};
+  TriSetup s;
+  if (!setup_triangle(v[0], v[1], v[2], p.vtx, s)) {
+    if (!p.pos) {
+      write_empty(p, o);
+      return;
+    }
+    float b0, b1, b2;
+    clip_ray_weights(p.pos, p.mvp, p.g.W, p.g.H, v, x, y, b0, b1, b2);
+    shade_vertices(p, v[0], v[1], v[2], b0, b1, b2, o);
+    return;
+  }
+  const int Px = 256 * x + 128, Py = 256 * y + 128;
+  const long long w1 = (long long)(s.X0 - s.X2) * (Py - s.Y2) - (long long)(s.Y0 - s.Y2) * (Px - s.X2);
+  const long long w2 = (long long)(s.X1 - s.X0) * (Py - s.Y0) - (long long)(s.Y1 - s.Y0) * (Px - s.X0);
+  const float rA = approx_rcp(f32_from_i64(s.A));
+  float b1 = f32_from_i64(w1) * rA, b2 = f32_from_i64(w2) * rA, b0 = 1.0f - b1 - b2;
+  if (PERSP) perspective_bary(b0, b1, b2, __ldg(p.invw + s.v0), __ldg(p.invw + s.v1), __ldg(p.invw + s.v2));
+  shade_vertices(p, s.v0, s.v1, s.v2, b0, b1, b2, o);
 }
 
 // Fills the shared-memory record of one bin entry (PERSP: with 1/w).
@@ -455,10 +484,19 @@ __device__ __forceinline__ void process_tile(const TileScene& p, int tile, unsig
     const unsigned i = c + tid;
     bool pushed = false;
     if (i < end) {
-      const unsigned t = __ldg(bin_tris + i) - (unsigned)p.tri_base;
-      const unsigned slot = (i - beg) < (unsigned)p.nslots ? (i - beg) : no_slot;
+      unsigned t = __ldg(bin_tris + i) - (unsigned)p.tri_base;
+      unsigned slot = (i - beg) < (unsigned)p.nslots ? (i - beg) : no_slot;
       TriSetup s;
-      load_setup(p, t, s);
+      if (p.clip_tris && t >= (unsigned)p.T) {
+        // a clipped sub-triangle: its points, the key of its triangle, no
+        // record (the winner shades from its triangle's clip coordinates)
+        const int4* c = p.clip_tris + 3 * (size_t)(t - (unsigned)p.T);
+        setup_points(__ldg(c), __ldg(c + 1), __ldg(c + 2), s);
+        t = __ldg(p.clip_orig + (t - (unsigned)p.T));
+        slot = no_slot;
+      } else {
+        load_setup(p, t, s);
+      }
       if (slot != no_slot) fill_record<PERSP>(p, s, sm.srec + slot * p.rec_stride);
       const int minX = min(s.X0, min(s.X1, s.X2)), maxX = max(s.X0, max(s.X1, s.X2));
       const int minY = min(s.Y0, min(s.Y1, s.Y2)), maxY = max(s.Y0, max(s.Y1, s.Y2));

@@ -826,6 +826,10 @@ def measure_deferred(args, ctx) -> dict:
     lights = torch.from_numpy(S.point_lights(scene.width, scene.height, 64)).cuda()
     bins = args.deferred_bins
     r = Rasterizer(scene.width, scene.height, bins, bins, args.deferred_schedule)
+    if args.small_px:
+        r.set_option(L.PIKO_OPT_SMALL_TRI_PIXELS, args.small_px)
+    if args.threads:
+        r.set_option(L.PIKO_OPT_THREADS_PER_TILE, args.threads)
     ds = DeviceScene.from_host(scene)
     fb = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode)
     out = torch.empty((scene.height, scene.width, 4), dtype=torch.float32, device="cuda")

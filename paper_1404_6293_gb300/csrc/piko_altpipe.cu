@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(ALT_THREADS) k_alt_shade_pixels(const __grid_c
       continue;
     }
     const int y = (int)(o / W), x = (int)(o - (long long)y * W);
-    shade_from_global<PERSP>(p.sc, (unsigned)(k & 0xFFFFFFFFu), x, y, (size_t)o);
+    shade_from_global<PERSP, true>(p.sc, (unsigned)(k & 0xFFFFFFFFu), x, y, (size_t)o);
   }
 }
 
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(ALT_THREADS) k_frag_shade(const __grid_constan
        i += (unsigned long long)gridDim.x * blockDim.x) {
     const unsigned o = p.frag_pix[i];
     const int y = (int)(o / (unsigned)W), x = (int)(o - (unsigned)y * (unsigned)W);
-    shade_from_global<PERSP>(fs, (unsigned)(p.frag_key[i] & 0xFFFFFFFFu), x, y, (size_t)i);
+    shade_from_global<PERSP, true>(fs, (unsigned)(p.frag_key[i] & 0xFFFFFFFFu), x, y, (size_t)i);
   }
 }
 

@@ -45,14 +45,15 @@ __host__ __device__ inline TileScene scene_of(const ProcessParams& p) {
 // instance fits 64 registers without spilling.
 // One instance per schedule (SCHED = PIKO_SCHED_*), so that each carries
 // only its own tile loop, per value of the work-counter option (STATS), so
-// that the counters hold no registers when they are off, and per attribute
-// interpolation (PERSP: perspective-correct).  The scene is
+// that the counters hold no registers when they are off, per attribute
+// interpolation (PERSP: perspective-correct) and per clipping setting
+// (CLIP: sub-triangles and clipped winners).  The scene is
 // read in place from the grid-constant parameter block.
 struct ProcessLaunch {
   ProcessParams p;
   TileScene sc;
 };
-template <int SCHED, bool STATS, bool PERSP>
+template <int SCHED, bool STATS, bool PERSP, bool CLIP>
 __global__ void __maxnreg__(PIKO_PROCESS_MAXNREG) k_process(const __grid_constant__ ProcessLaunch pl) {
   const ProcessParams& p = pl.p;
   extern __shared__ __align__(16) unsigned long long smem[];
@@ -91,7 +92,7 @@ __global__ void __maxnreg__(PIKO_PROCESS_MAXNREG) k_process(const __grid_constan
     }
     if (tile >= p.ntiles) break;
     const unsigned beg = __ldg(p.bin_off + tile), end = __ldg(p.bin_off + tile + 1);
-    process_tile<STATS, PERSP>(sc, tile, beg, end, p.bin_tris, sm, big_base, st);
+    process_tile<STATS, PERSP, CLIP>(sc, tile, beg, end, p.bin_tris, sm, big_base, st);
   }
   if (STATS) {  // one atomic per warp: same-address atomics from every thread serialise
     for (int o = 16; o > 0; o >>= 1) {
@@ -120,16 +121,22 @@ static size_t smem_bytes(const ProcessParams& p, int threads) {
 
 using ProcessKernel = void (*)(ProcessLaunch);
 
-template <bool STATS, bool PERSP>
+template <bool STATS, bool PERSP, bool CLIP>
 static ProcessKernel process_kernel_of(int schedule) {
-  if (schedule == PIKO_SCHED_DYNAMIC) return k_process<PIKO_SCHED_DYNAMIC, STATS, PERSP>;
-  if (schedule == PIKO_SCHED_HARDWARE) return k_process<PIKO_SCHED_HARDWARE, STATS, PERSP>;
-  return k_process<PIKO_SCHED_STATIC, STATS, PERSP>;
+  if (schedule == PIKO_SCHED_DYNAMIC) return k_process<PIKO_SCHED_DYNAMIC, STATS, PERSP, CLIP>;
+  if (schedule == PIKO_SCHED_HARDWARE) return k_process<PIKO_SCHED_HARDWARE, STATS, PERSP, CLIP>;
+  return k_process<PIKO_SCHED_STATIC, STATS, PERSP, CLIP>;
+}
+
+template <bool CLIP>
+static ProcessKernel process_kernel_clip(const ProcessParams& p) {
+  if (p.invw)
+    return p.stats ? process_kernel_of<true, true, CLIP>(p.schedule) : process_kernel_of<false, true, CLIP>(p.schedule);
+  return p.stats ? process_kernel_of<true, false, CLIP>(p.schedule) : process_kernel_of<false, false, CLIP>(p.schedule);
 }
 
 static ProcessKernel process_kernel(const ProcessParams& p) {
-  if (p.invw) return p.stats ? process_kernel_of<true, true>(p.schedule) : process_kernel_of<false, true>(p.schedule);
-  return p.stats ? process_kernel_of<true, false>(p.schedule) : process_kernel_of<false, false>(p.schedule);
+  return p.clip_tris ? process_kernel_clip<true>(p) : process_kernel_clip<false>(p);
 }
 
 cudaError_t process_occupancy(const ProcessParams& p0, int threads, int* blocks_per_sm) {

@@ -386,16 +386,17 @@ __device__ __forceinline__ void shade_vertices(const TileScene& p, int v0, int v
 }
 
 // Fallback for winners without a record: everything re-read from global
-// memory.  A winner whose vertices the vertex stage rejected was clipped: it
-// shades with its clip-space ray weights (perspective-correct by
-// construction).
-template <bool PERSP>
+// memory.  CLIP (near/far clipping on): a winner whose vertices the vertex
+// stage rejected was clipped, and shades with its clip-space ray weights
+// (perspective-correct by construction); one kernel instance per setting so
+// that the default path carries none of it.
+template <bool PERSP, bool CLIP = false>
 __device__ __forceinline__ void shade_from_global(const TileScene& p, unsigned t, int x, int y, size_t o) {
   const int v[3] = {__ldg(p.tris + 3 * (size_t)t), __ldg(p.tris + 3 * (size_t)t + 1),
                     __ldg(p.tris + 3 * (size_t)t + 2)};
   TriSetup s;
   if (!setup_triangle(v[0], v[1], v[2], p.vtx, s)) {
-    if (!p.pos) {
+    if (!CLIP || !p.pos) {
       write_empty(p, o);
       return;
     }
@@ -466,9 +467,10 @@ __device__ __forceinline__ void load_setup(const TileScene& p, unsigned t, TriSe
 // Process one tile: tile is the scene-local tile index, [beg, end) its range
 // in bin_tris.  Called by every thread of the CTA (nt threads, a power of
 // two); contains CTA barriers.  big_base tracks the large-triangle ring.
-// PERSP: perspective-correct attributes (p.invw set); one kernel instance
-// per value so that the screen-space path carries none of it.
-template <bool STATS, bool PERSP = false>
+// PERSP: perspective-correct attributes (p.invw set); CLIP: near/far
+// clipping (entries T.. are clipped sub-triangles); one kernel instance per
+// setting so that the default path carries none of either.
+template <bool STATS, bool PERSP = false, bool CLIP = false>
 __device__ __forceinline__ void process_tile(const TileScene& p, int tile, unsigned beg, unsigned end,
                                              const unsigned* __restrict__ bin_tris, const TileSmem& sm,
                                              unsigned& big_base, TileStats& st) {
@@ -487,7 +489,7 @@ __device__ __forceinline__ void process_tile(const TileScene& p, int tile, unsig
       unsigned t = __ldg(bin_tris + i) - (unsigned)p.tri_base;
       unsigned slot = (i - beg) < (unsigned)p.nslots ? (i - beg) : no_slot;
       TriSetup s;
-      if (p.clip_tris && t >= (unsigned)p.T) {
+      if (CLIP && t >= (unsigned)p.T) {
         // a clipped sub-triangle: its points, the key of its triangle, no
         // record (the winner shades from its triangle's clip coordinates)
         const int4* c = p.clip_tris + 3 * (size_t)(t - (unsigned)p.T);
@@ -570,7 +572,7 @@ __device__ __forceinline__ void process_tile(const TileScene& p, int tile, unsig
     if (slot != no_slot)
       shade_from_record<PERSP>(p, sm.srec + slot * p.rec_stride, x, y, o);
     else
-      shade_from_global<PERSP>(p, t, x, y, o);
+      shade_from_global<PERSP, CLIP>(p, t, x, y, o);
   }
   __syncthreads();
 }

@@ -622,6 +622,7 @@ def run_ours(args):
             "C3_deferred_powerlaw_1080p": measure_deferred(args, ctx),
             "C4_sphere_64_views": measure_sphere(args, ctx),
             "C5_batch_256_scenes": measure_batch(args, ctx),
+            "F4_reyes_sample": measure_reyes(args, ctx),
         }
     clocks.close()
     if dist is not None:
@@ -810,6 +811,48 @@ def measure_random256(args, ctx) -> dict:
                                                      f"one thread, {dt:.3f} s"}
         rec["cpu_baseline"] = cb
     r.close()
+    return rec
+
+
+def measure_reyes(args, ctx) -> dict:
+    """The Reyes Sample stage on this path: micropolygon grids (256 Bezier
+    patches diced to about half-pixel quads, two triangles each, 1024 x 768)
+    sampled at pixel centres with the Sample stage's 32 x 32 bins and a
+    diffuse (Lambert) Shade; the 16 x 16 hardware-scheduled launch beside it."""
+    from paper_1404_6293_gb300 import scenes as S
+    from paper_1404_6293_gb300.raster import DeviceScene, Framebuffer, Rasterizer
+    scene = S.reyes_grids()
+    ds = DeviceScene.from_host(scene)
+    K = args.steps
+    runs = {}
+    for bins, sched in ((32, "dynamic"), (16, "hardware")):
+        r = Rasterizer(scene.width, scene.height, bins, bins, sched)
+        fb = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode)
+        stats, covered = size_and_count(r, ds, fb)
+        m0 = ctx.clocks.mark()
+        step_ms, stage_ms = time_forward(ctx, r, ds, fb, K, args.warmup)
+        clk = ctx.clocks.summary(m0)
+        if r.status()[0] != 0:
+            raise RuntimeError("status error in the micropolygon loop")
+        runs[(bins, sched)] = (sum(step_ms) / K, stage_ms, stats, covered, clk)
+        r.close()
+    ms, stage_ms, stats, covered, clk = runs[(32, "dynamic")]
+    proc_ms = float(stage_ms[:, 4].mean())
+    rec = {"workload": f"Reyes Sample: {scene.num_triangles} micropolygon triangles (256 bicubic patches diced to "
+                       "~0.5-px quads), 1024x768, Lambert, 32x32 bins, dynamic",
+           "value": scene.num_triangles / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms,
+           "micropolygons_per_s": scene.num_triangles / 2 / (ms * 1e-3),
+           "shaded_gfrag_s": covered / (ms * 1e-3) / 1e9,
+           "stage_ms": {n: float(stage_ms[:, i].mean()) for i, n in
+                        enumerate(["vertex", "setup_count", "scan", "scatter", "process"])},
+           "work": {**stats, "covered_pixels": covered},
+           "roofline": process_roofline(ctx, scene, stats, proc_ms, clk),
+           "bins_16x16_hardware": {"ms_per_step": runs[(16, "hardware")][0],
+                                   "value": scene.num_triangles / (runs[(16, "hardware")][0] * 1e-3) / 1e6},
+           "clocks": clk, "gpu_launches": 5 * K,
+           "parity": "keys bit-exact, colour <= 1e-5 vs the oracle at this size (tests/test_gpu_reyes.py)"}
+    if not args.no_cpu_baseline:
+        rec["cpu_baseline"] = cpu_baseline(scene, args.config_cpu_seconds, single_seconds=2.0)
     return rec
 
 
@@ -1208,7 +1251,7 @@ def run_single_workload(args):
     clocks = ClockSampler(0)
     ctx = Ctx(clocks)
     fn = {"random256": measure_random256, "deferred": measure_deferred, "sphere": measure_sphere,
-          "batch": measure_batch}[args.workload]
+          "batch": measure_batch, "reyes": measure_reyes}[args.workload]
     rec = fn(args, ctx)
     clocks.close()
     line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -1247,7 +1290,7 @@ def main():
     ap.add_argument("--batch-launch", default="persistent", choices=["persistent", "per-phase"],
                     help="batch workload: one cooperative launch, or one launch per phase (for launch lists)")
     ap.add_argument("--workload", default="heightfield",
-                    choices=["heightfield", "random256", "deferred", "sphere", "batch"],
+                    choices=["heightfield", "random256", "deferred", "sphere", "batch", "reyes"],
                     help="heightfield: the headline line (with every other configuration under 'configs'); "
                          "the others: that configuration alone as the line")
     ap.add_argument("--no-configs", action="store_true", help="headline line only (no bin sweep, no other configs)")

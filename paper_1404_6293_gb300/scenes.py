@@ -344,6 +344,72 @@ def sphere_views(num_views=64, width=512, height=512, slices=250, stacks=200, se
     return scene, _f32(np.stack(mvps))
 
 
+def reyes_grids(width=1024, height=768, num_patches=256, seed=1243, micropoly_px=0.5, side_min=16.0,
+                side_max=160.0, max_dice=128) -> Scene:
+    """Micropolygon grids as a Reyes Dice stage would emit them (the input of
+    the Sample stage, Sec. 7.1 of the Piko paper): seeded bicubic Bezier
+    patches, each diced into an n x n grid of quads of about `micropoly_px`
+    pixels a side (n = ceil(screen side / micropoly_px), capped at
+    `max_dice`), every quad split into two triangles.  Patch screen sides
+    are log-uniform in [side_min, side_max] pixels, centres uniform, control
+    points on a random tilted plane with a seeded bulge; depth in NDC (w = 1).
+    Per-vertex normals from the patch's partial derivatives and a per-patch
+    albedo; Lambert with the light of Listing 1.  Split and Dice themselves
+    are not part of this generator's output contract: only their result."""
+    rng = SplitMix64(seed)
+    P = int(num_patches)
+    side = side_min * np.exp(rng.uniform(P) * np.log(side_max / side_min))
+    cx = rng.uniform(P) * width
+    cy = rng.uniform(P) * height
+    z0 = rng.uniform(P) * 1.6 - 0.8
+    tilt = (rng.uniform(2 * P).reshape(P, 2) - 0.5) * 0.6
+    bulge = (rng.uniform(16 * P).reshape(P, 4, 4) - 0.5) * 0.5
+    rot = rng.uniform(P) * 2.0 * np.pi
+    alb = rng.uniform(3 * P).reshape(P, 3)
+    # Bernstein basis of degree 3
+    def bern(t):
+        return np.stack([(1 - t) ** 3, 3 * t * (1 - t) ** 2, 3 * t ** 2 * (1 - t), t ** 3], -1)
+
+    def dbern(t):
+        return np.stack([-3 * (1 - t) ** 2, 3 * (1 - t) ** 2 - 6 * t * (1 - t), 6 * t * (1 - t) - 3 * t ** 2,
+                         3 * t ** 2], -1)
+    pos_l, tri_l, nrm_l, col_l = [], [], [], []
+    base = 0
+    for k in range(P):
+        n = int(min(max_dice, max(1, np.ceil(side[k] / micropoly_px))))
+        # control points: a square of side `side` in pixels, rotated, on a
+        # tilted plane in depth with a bulge (depth units: NDC)
+        g = np.linspace(-0.5, 0.5, 4)
+        gu, gv = np.meshgrid(g, g, indexing="ij")
+        ct, st = np.cos(rot[k]), np.sin(rot[k])
+        px = cx[k] + side[k] * (ct * gu - st * gv)
+        py = cy[k] + side[k] * (st * gu + ct * gv)
+        pz = z0[k] + tilt[k, 0] * gu + tilt[k, 1] * gv + bulge[k] * 0.2
+        C = np.stack([px * (2.0 / width) - 1.0, 1.0 - py * (2.0 / height), np.clip(pz, -0.95, 0.95)], -1)
+        t = np.linspace(0.0, 1.0, n + 1)
+        Bu, Bv, dBu, dBv = bern(t), bern(t), dbern(t), dbern(t)
+        S = np.einsum("ia,jb,abc->ijc", Bu, Bv, C)
+        Su = np.einsum("ia,jb,abc->ijc", dBu, Bv, C)
+        Sv = np.einsum("ia,jb,abc->ijc", Bu, dBv, C)
+        N = np.cross(Su, Sv)
+        N /= np.maximum(np.linalg.norm(N, axis=-1, keepdims=True), 1e-12)
+        N[..., 2] = -np.abs(N[..., 2])  # facing the viewer (-z)
+        pos_l.append(np.concatenate([S.reshape(-1, 3), np.ones(((n + 1) ** 2, 1))], 1))
+        nrm_l.append(N.reshape(-1, 3))
+        col_l.append(np.tile(alb[k], ((n + 1) ** 2, 1)))
+        j, i = np.meshgrid(np.arange(n), np.arange(n))
+        a = (i * (n + 1) + j).ravel() + base
+        b = a + 1
+        c = a + (n + 1)
+        d = c + 1
+        tri_l.append(np.stack([np.stack([a, b, c], 1), np.stack([b, d, c], 1)], 1).reshape(-1, 3))
+        base += (n + 1) ** 2
+    return Scene(width, height, _f32(np.concatenate(pos_l)), _i32(np.concatenate(tri_l)),
+                 color=_f32(np.concatenate(col_l)), normal=_f32(np.concatenate(nrm_l)),
+                 light_dir=listing1_light(), shade_mode=SHADE_LAMBERT,
+                 name=f"reyes{P}_{width}x{height}")
+
+
 def target_image(width, height, seed=1240, views=1) -> np.ndarray:
     """A seeded target image float32 [views,H,W,4] in [0,1] for an L2 loss."""
     rng = SplitMix64(seed)

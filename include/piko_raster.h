@@ -77,14 +77,14 @@ extern "C" {
 
 /* ---- shading modes ---------------------------------------------------- */
 #define PIKO_SHADE_GOURAUD 0 /* rgb = sum b_i c_i                                         */
-#define PIKO_SHADE_LAMBERT 1 /* rgb = albedo * max(0, n . L), Listing 1                    */
+#define PIKO_SHADE_LAMBERT 1 /* rgb = albedo * max(0, n . L): diffuse (Sec. 4.1 example) */
 #define PIKO_SHADE_GBUFFER 2 /* no colour; FP16 normal and albedo for a deferred light pass */
 
 /* ---- options for piko_raster_set_option ------------------------------- */
 #define PIKO_OPT_THREADS_PER_TILE 1 /* CTA size of the Process stage: 64, 128, 256 or 512
                                        (the threads-per-bin knob of Listing 1 / Sec. 6)   */
-#define PIKO_OPT_UNCLAMPED 2        /* 1: Lambert without the max(0, .) clamp, exactly as
-                                       Listing 1 prints it; default 0                      */
+#define PIKO_OPT_UNCLAMPED 2        /* 1: Lambert without the max(0, .) clamp,
+                                       rgb = albedo * (n . L); default 0 (clamped)         */
 #define PIKO_OPT_CHECK_CAPACITY 3   /* 1 (default): forward reads the bin-list size back
                                        after the scan (one host sync) and grows scratch
                                        before scattering; 0: no sync, overflow is reported

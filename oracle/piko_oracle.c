@@ -34,7 +34,8 @@
  *       over all triangles covering it (nearest depth, ties to the lower
  *       index); an empty pixel keeps 0xFFFFFFFFFFFFFFFF.
  *   O11 shading of the winning triangle in float64 with b_i = w_i / A:
- *       Gouraud rgb = sum b_i c_i; Lambert (Listing 1 of the paper)
+ *       Gouraud rgb = sum b_i c_i; Lambert (the diffuse shader of the paper's
+ *       example fragment-shader stage, Sec. 4.1)
  *       rgb = albedo * max(0, n . L) with n = sum b_i n_i (not renormalised)
  *       and albedo = sum b_i c_i, or the constant (0.80, 0.75, 0.65) when no
  *       colours are given.  Covered pixels get alpha 1, empty ones 0.

@@ -956,6 +956,7 @@ def measure_sphere(args, ctx) -> dict:
     key_all = torch.empty((nv, H, W), dtype=torch.int64, device="cuda")
     rgba_all = torch.empty((nv, H, W, 4), dtype=torch.float32, device="cuda")
     g_all = torch.empty_like(rgba_all)
+    neg2_tgt = tgt * -2.0  # the loss gradient 2 (rgba - target) as one elementwise pass
     fbs = [Framebuffer(key_all[v], rgba_all[v]) for v in range(nv)]
     gviews = [g_all[v] for v in range(nv)]
     dc = torch.zeros_like(ds.color)
@@ -973,45 +974,51 @@ def measure_sphere(args, ctx) -> dict:
     def fwd_pass():
         rb.forward_batch(views, fbs, bins, scheds)
 
+    def loss_pass():
+        torch.add(neg2_tgt, rgba_all, alpha=2.0, out=g_all)
+
     def bwd_pass():
         dc.zero_(); dn.zero_(); dl.zero_()
-        torch.sub(rgba_all, tgt, out=g_all).mul_(2.0)
-        g_all[..., 3] = 0.0
         rb.backward_batch(views, fbs, gviews, [dc] * nv, [dn] * nv, [dl] * nv)
 
     side = torch.cuda.Stream()
     side.wait_stream(stream)
     with torch.cuda.stream(side):
         for _ in range(2):
-            fwd_pass(); bwd_pass()
+            fwd_pass(); loss_pass(); bwd_pass()
     stream.wait_stream(side)
     torch.cuda.synchronize()
-    gf, gb = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    gf, gl, gb = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
     with torch.cuda.graph(gf):
         fwd_pass()
+    with torch.cuda.graph(gl):
+        loss_pass()
     with torch.cuda.graph(gb):
         bwd_pass()
     torch.cuda.synchronize()
     K = args.steps
     for _ in range(args.warmup):
         ctx.flush.zero_()
-        gf.replay(); gb.replay()
-    evs = [(ctx.event(), ctx.event(), ctx.event()) for _ in range(K)]
+        gf.replay(); gl.replay(); gb.replay()
+    evs = [(ctx.event(), ctx.event(), ctx.event(), ctx.event()) for _ in range(K)]
     torch.cuda.synchronize()
     m0 = ctx.clocks.mark()
-    for s, f, e in evs:
+    for s, f, l, e in evs:
         ctx.flush.zero_()
         s.record(stream)
         gf.replay()
         f.record(stream)
+        gl.replay()
+        l.record(stream)
         gb.replay()
         e.record(stream)
     torch.cuda.synchronize()
     clk = ctx.clocks.summary(m0)
     assert rb.status()[0] == 0
-    fwd = np.array([s.elapsed_time(f) for s, f, _ in evs])
-    bwd = np.array([f.elapsed_time(e) for _, f, e in evs])
-    ms = float((fwd + bwd).mean())
+    fwd = np.array([s.elapsed_time(f) for s, f, _, _ in evs])
+    lossg = np.array([f.elapsed_time(l) for _, f, l, _ in evs])
+    bwd = np.array([l.elapsed_time(e) for _, _, l, e in evs])
+    ms = float((fwd + lossg + bwd).mean())
     T = nv * sph.num_triangles
     V = sph.num_vertices
     bw_bytes = nv * W * H * (8 + 16) + V * (16 + 12 * 2) + nv * V * 12 * 2
@@ -1019,10 +1026,11 @@ def measure_sphere(args, ctx) -> dict:
     rec = {"workload": "sphere 99.5k triangles, 64 views 512x512, forward + L2-loss backward (colour, normal, light)",
            "value": T / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms,
            "shaded_gfrag_s": covered / (ms * 1e-3) / 1e9,
-           "how": "the 64 views as one forward_batch and one backward_batch (16x16 bins, dynamic), each "
-                  "replayed from a CUDA graph; the backward includes the loss gradient",
-           "forward_ms": float(fwd.mean()), "backward_ms": float(bwd.mean()), "covered_pixels": covered,
-           "roofline": {"kernel": "backward (64 views, incl. loss gradient)", "bound": "hbm",
+           "how": "the 64 views as one forward_batch, the loss gradient (one elementwise torch op) and one "
+                  "backward_batch (16x16 bins, dynamic), each replayed from its own CUDA graph",
+           "forward_ms": float(fwd.mean()), "loss_gradient_ms": float(lossg.mean()),
+           "backward_ms": float(bwd.mean()), "covered_pixels": covered,
+           "roofline": {"kernel": "k_batch_backward (64 views, with the gradient arrays' zeroing)", "bound": "hbm",
                         "achieved": bw_bytes / bt / 1e9, "peak": ctx.hbm, "unit": "GB/s",
                         "frac": bw_bytes / bt / 1e9 / ctx.hbm, "traffic": None,
                         "bytes": "24 B per pixel (key, dL/dRGBA) + 40 B per vertex read + 24 B per vertex per view "
@@ -1085,7 +1093,14 @@ def measure_batch(args, ctx) -> dict:
 
     gen = torch.Generator(device="cuda").manual_seed(1240)
     target = torch.rand((P, 4), generator=gen, device="cuda")
+    # the loss is sum over pixels of |rgb - target|^2; its gradient 2 (rgba -
+    # target) is one elementwise pass, g = 2 rgba + (-2 target) (the backward
+    # reads only the rgb part of g)
+    neg2_target = target * -2.0
     g_all = torch.empty((P, 4), device="cuda")
+
+    def loss_grad(rgba):
+        torch.add(neg2_target, rgba, alpha=2.0, out=g_all)
     gviews = [g_all[po[i]:po[i + 1]].view(host[i].height, host[i].width, 4) for i in range(n)]
 
     # ---- plain: one handle per resolution, 16x16 bins, static
@@ -1105,8 +1120,7 @@ def measure_batch(args, ctx) -> dict:
         dc_p.zero_(); dn_p.zero_(); dl_p.zero_()
         for i in range(n):
             handles[(host[i].width, host[i].height)].forward(ds[i], fbs_p[i])
-        torch.sub(rgba_p, target, out=g_all).mul_(2.0)
-        g_all[:, 3] = 0.0
+        loss_grad(rgba_p)
         for i in range(n):
             handles[(host[i].width, host[i].height)].backward(ds[i], fbs_p[i], gviews[i], dcv_p[i], dnv_p[i], dlv_p[i])
 
@@ -1131,18 +1145,21 @@ def measure_batch(args, ctx) -> dict:
     def batched_fwd():
         rb.forward_batch(ds, fbs_b, bins, scheds)
 
+    def batched_loss():
+        loss_grad(rgba_b)
+
     def batched_bwd():
         dc_b.zero_(); dn_b.zero_(); dl_b.zero_()
-        torch.sub(rgba_b, target, out=g_all).mul_(2.0)
-        g_all[:, 3] = 0.0
         rb.backward_batch(ds, fbs_b, gviews, dcv_b, dnv_b, dlv_b)
 
     for _ in range(2):
-        batched_fwd(); batched_bwd()
+        batched_fwd(); batched_loss(); batched_bwd()
     torch.cuda.synchronize()
-    gf, gb = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    gf, gl, gb = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
     with torch.cuda.graph(gf):
         batched_fwd()
+    with torch.cuda.graph(gl):
+        batched_loss()
     with torch.cuda.graph(gb):
         batched_bwd()
     torch.cuda.synchronize()
@@ -1170,8 +1187,8 @@ def measure_batch(args, ctx) -> dict:
     m0 = ctx.clocks.mark()
     ms_plain = sum(timed([plain_step], args.steps, args.warmup))
     m1 = ctx.clocks.mark()
-    f_ms, b_ms = timed([gf.replay, gb.replay], args.steps, args.warmup)
-    ms_batch = f_ms + b_ms
+    f_ms, l_ms, b_ms = timed([gf.replay, gl.replay, gb.replay], args.steps, args.warmup)
+    ms_batch = f_ms + l_ms + b_ms
     clk = ctx.clocks.summary(m1)
     clk["plain_loop"] = {k: v for k, v in ctx.clocks.summary(m0, m1).items() if k in ("sm_mhz", "samples", "reasons")}
     assert rb.status()[0] == 0
@@ -1193,10 +1210,11 @@ def measure_batch(args, ctx) -> dict:
            "plain": {"value": T / (ms_plain * 1e-3) / 1e6, "ms_per_step": ms_plain,
                      "how": "per-scene piko_raster_forward then piko_raster_backward, 16x16 static"},
            "batched": {"value": T / (ms_batch * 1e-3) / 1e6, "ms_per_step": ms_batch,
-                       "forward_ms": f_ms, "backward_ms": b_ms,
+                       "forward_ms": f_ms, "loss_gradient_ms": l_ms, "backward_ms": b_ms,
                        "how": ("forward_batch (one persistent cooperative launch)" if args.batch_launch ==
-                               "persistent" else "forward_batch (one launch per phase)") + " and loss gradient + "
-                              "backward_batch, each replayed from a CUDA graph",
+                               "persistent" else "forward_batch (one launch per phase)") + ", the loss gradient "
+                              "(one elementwise torch op) and backward_batch (with the gradient arrays' zeroing), "
+                              "each replayed from its own CUDA graph",
                        "autotune_s": tune_s, "static_scenes": n_static,
                        "bins_used": sorted(set(f"{a}x{b}" for a, b in bins)),
                        "autotune": {"choice": tune_report["choice"], "classes": tune_report["classes"],
@@ -1205,7 +1223,7 @@ def measure_batch(args, ctx) -> dict:
                                     "uniform_forward_ms": {f"{u['bin'][0]}x{u['bin'][1]} {u['schedule']}": u["ms"]
                                                            for u in tune_report["uniform"]}}},
            "speedup_batched_over_plain": ms_plain / ms_batch,
-           "roofline": {"kernel": "k_batch_backward (with the loss gradient)", "bound": "hbm",
+           "roofline": {"kernel": "k_batch_backward (with the gradient arrays' zeroing)", "bound": "hbm",
                         "achieved": bw_bytes / (b_ms * 1e-3) / 1e9, "peak": ctx.hbm, "unit": "GB/s",
                         "frac": bw_bytes / (b_ms * 1e-3) / 1e9 / ctx.hbm, "traffic": None,
                         "algorithmic_bytes": bw_bytes},

@@ -1,6 +1,6 @@
 // piko_backward.cu -- attribute gradients of one scene through the shading of
-// the forward pass: the per-tile form (piko_bwd_tile.cuh) and a per-pixel
-// form for scenes of tiny triangles.
+// the forward pass: the tile form (a warp per 16 x 16 tile, piko_bwd_tile.cuh)
+// and a per-pixel form for scenes of tiny triangles.
 #include "piko_bwd_tile.cuh"
 
 namespace piko {
@@ -10,28 +10,35 @@ struct BackwardParams {
   int ntx, ntiles;
 };
 
-template <bool PERSP>
-__global__ void __launch_bounds__(BWD_THREADS, 1024 / BWD_THREADS) k_backward(BackwardParams p) {
+// Warp form (backward_warp_tile): each warp takes whole tiles, grid-stride.
+constexpr int BACKWARD_WARPS = BWD_THREADS / 32;
+struct BackwardSmem {
+  float stage[BACKWARD_WARPS][BWD_VALS][33];
+};
+#ifndef PIKO_BWD_MINB
+#define PIKO_BWD_MINB 3
+#endif
+template <bool PERSP, bool CLIP>
+__global__ void __launch_bounds__(BWD_THREADS, PIKO_BWD_MINB) k_backward(const __grid_constant__ BackwardParams p) {
   extern __shared__ __align__(16) unsigned char bwd_smem_raw[];
-  BwdSmem& sm = *reinterpret_cast<BwdSmem*>(bwd_smem_raw);
+  BackwardSmem& sm = *reinterpret_cast<BackwardSmem*>(bwd_smem_raw);
+  const int warp = threadIdx.x >> 5;
   float L0 = 0.f, L1 = 0.f, L2 = 0.f;
   if (p.sc.mode == PIKO_SHADE_LAMBERT) {
     L0 = __ldg(p.sc.light); L1 = __ldg(p.sc.light + 1); L2 = __ldg(p.sc.light + 2);
   }
-  float gl0 = 0.f, gl1 = 0.f, gl2 = 0.f;
-  bwd_clear(sm);
-  __syncthreads();
-  for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
+  const int nwarps = gridDim.x * BACKWARD_WARPS;
+  for (int tile = blockIdx.x * BACKWARD_WARPS + warp; tile < p.ntiles; tile += nwarps) {
     const int ty = tile / p.ntx, tx = tile - ty * p.ntx;
-    backward_tile<PERSP>(p.sc, tx * BWD_TILE_W, ty * BWD_TILE_H, sm, L0, L1, L2, gl0, gl1, gl2);
+    backward_warp_tile<PERSP, CLIP>(p.sc, tx * BWD_TILE_W, ty * BWD_TILE_H, sm.stage[warp], L0, L1, L2);
   }
-  if (p.sc.dlight && p.sc.mode == PIKO_SHADE_LAMBERT) bwd_flush_light(sm, p.sc.dlight, gl0, gl1, gl2);
 }
+constexpr size_t BACKWARD_SMEM = sizeof(BackwardSmem);
 
 // A winner the vertex stage rejected was clipped (near/far clipping on, pos
 // set): its weights are the clip-space ray weights of the pixel centre.
 // Per-pixel form, for scenes of tiny triangles (a tile would hold nearly as
-// many triangles as pixels, so the tile form's shared table buys nothing):
+// many triangles as pixels, so the tile form's runs are a pixel or two long):
 // each warp takes 32 consecutive pixels; lanes whose pixels share a winning
 // triangle are summed in shared memory and one lane issues the atomics for
 // the group; the light gradient is reduced over the whole CTA.
@@ -200,8 +207,16 @@ __global__ void __launch_bounds__(PIX_THREADS) k_backward_pixel(PixelBwdParams p
   }
 }
 
+using BackwardKernel = void (*)(BackwardParams);
+
+BackwardKernel backward_kernel(bool persp, bool clip) {
+  if (persp) return clip ? k_backward<true, true> : k_backward<true, false>;
+  return clip ? k_backward<false, true> : k_backward<false, false>;
+}
+
 // Blocks of the single-scene backward kernel: as many as fit on the device
-// at once (the shared-memory opt-in is per device, so it is cached per device).
+// at once, a tile per warp (the shared-memory opt-in is per device, so it is
+// cached per device).
 int backward_grid(int tiles, int num_sms) {
   static int per_sm_of[64] = {0};
   int dev = 0;
@@ -209,19 +224,21 @@ int backward_grid(int tiles, int num_sms) {
   int& per_sm = per_sm_of[dev & 63];
   if (per_sm == 0) {
     int v = 0;
-    // both instances share the launch bounds and the shared-memory size
-    if (cudaFuncSetAttribute(k_backward<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BwdSmem)) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(k_backward<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BwdSmem)) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_backward<false>, BWD_THREADS, sizeof(BwdSmem)) !=
-            cudaSuccess ||
+    bool ok = true;
+    // the instances share the launch bounds and the shared-memory size
+    for (int k = 0; k < 4; ++k)
+      ok = ok && cudaFuncSetAttribute(backward_kernel(k & 1, k & 2), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)BACKWARD_SMEM) == cudaSuccess;
+    if (!ok ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, backward_kernel(false, false), BWD_THREADS,
+                                                      BACKWARD_SMEM) != cudaSuccess ||
         v < 1)
       v = 1;
     per_sm = v;
   }
   long long blocks = (long long)per_sm * num_sms;
-  if (blocks > tiles) blocks = tiles;
+  const long long need = (tiles + BACKWARD_WARPS - 1) / BACKWARD_WARPS;
+  if (blocks > need) blocks = need;
   return blocks < 1 ? 1 : (int)blocks;
 }
 
@@ -235,7 +252,10 @@ int piko_backward_launch(int W, int H, int mode, int unclamped, int T, int V, co
                          const float* dl_drgba, float* dcolor, float* dnormal, float* dlight, int num_sms,
                          cudaStream_t s) {
   const long long npix = (long long)W * H;
-  if (4LL * T > npix) {
+#ifndef PIKO_BWD_PIXEL_FORM  // 0: every scene takes the tile form (for comparisons)
+#define PIKO_BWD_PIXEL_FORM 1
+#endif
+  if (PIKO_BWD_PIXEL_FORM && 4LL * T > npix) {
     // more than one triangle per four pixels: triangles of a few pixels
     PixelBwdParams p;
     p.W = W; p.H = H; p.mode = mode; p.unclamped = unclamped; p.T = T; p.V = V;
@@ -262,9 +282,6 @@ int piko_backward_launch(int W, int H, int mode, int unclamped, int T, int V, co
   p.ntx = (W + BWD_TILE_W - 1) / BWD_TILE_W;
   p.ntiles = p.ntx * ((H + BWD_TILE_H - 1) / BWD_TILE_H);
   const int blocks = backward_grid(p.ntiles, num_sms);
-  if (invw)
-    k_backward<true><<<blocks, BWD_THREADS, sizeof(BwdSmem), s>>>(p);
-  else
-    k_backward<false><<<blocks, BWD_THREADS, sizeof(BwdSmem), s>>>(p);
+  backward_kernel(invw != nullptr, pos != nullptr)<<<blocks, BWD_THREADS, BACKWARD_SMEM, s>>>(p);
   return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }

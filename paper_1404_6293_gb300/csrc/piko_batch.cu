@@ -466,28 +466,39 @@ struct BatchBwdParams {
   const float* invw;  // as in BatchParams
 };
 
+// Warp form: each warp takes whole tiles (grid-stride over the batch's
+// tiles), with no CTA barrier; the scene of a tile is found by every lane
+// (uniform loads) and its descriptor kept in the warp's shared slot (in
+// registers it would cost the tile loop its occupancy).
+constexpr int BATCH_BWD_WARPS = BWD_THREADS / 32;
+struct BatchBwdSmem {
+  float stage[BATCH_BWD_WARPS][BWD_VALS][33];
+  BwdScene sc[BATCH_BWD_WARPS];
+};
 template <bool PERSP>
-__global__ void __launch_bounds__(BWD_THREADS, 1024 / BWD_THREADS) k_batch_backward(BatchBwdParams b) {
+#ifndef PIKO_BWD_MINB
+#define PIKO_BWD_MINB 3
+#endif
+__global__ void __launch_bounds__(BWD_THREADS, PIKO_BWD_MINB) k_batch_backward(BatchBwdParams b) {
   extern __shared__ __align__(16) unsigned char bwd_smem_raw[];
-  BwdSmem& sm = *reinterpret_cast<BwdSmem*>(bwd_smem_raw);
-  __shared__ int s_scene;
-  float gl0 = 0.f, gl1 = 0.f, gl2 = 0.f;
-  bwd_clear(sm);
-  __syncthreads();
-  for (int i = blockIdx.x; i < b.total_btiles; i += gridDim.x) {
-    if (threadIdx.x == 0) s_scene = find_scene(b.btile_prefix, b.n, i);
-    __syncthreads();
-    const int s = s_scene;
-    __syncthreads();  // s_scene is rewritten for the next tile
+  BatchBwdSmem& sm = *reinterpret_cast<BatchBwdSmem*>(bwd_smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * BATCH_BWD_WARPS;
+  BwdScene& c = sm.sc[warp];
+  for (int i = blockIdx.x * BATCH_BWD_WARPS + warp; i < b.total_btiles; i += nwarps) {
+    const int s = find_scene(b.btile_prefix, b.n, i);
     const BatchScene& d = b.sc[s];
-    if (d.dl == nullptr || d.mode == PIKO_SHADE_GBUFFER) continue;  // the same for the whole CTA
-    BwdScene c;
-    c.W = d.g.W; c.H = d.g.H; c.mode = d.mode; c.unclamped = d.unclamped; c.T = d.T; c.V = d.V;
-    c.tris = d.tris; c.vtx = b.vtx + d.vtx_base; c.color = d.color; c.normal = d.normal; c.light = d.light;
-    c.invw = b.invw ? b.invw + d.vtx_base : nullptr;
-    c.pos = nullptr;  // batches do not clip
-    c.mvp = nullptr;
-    c.key = d.key_out; c.dl = d.dl; c.dcolor = d.dcolor; c.dnormal = d.dnormal; c.dlight = d.dlight;
+    if (d.dl == nullptr || d.mode == PIKO_SHADE_GBUFFER) continue;  // the same for the whole warp
+    __syncwarp();  // the previous tile's reads of c are done
+    if (lane == 0) {
+      c.W = d.g.W; c.H = d.g.H; c.mode = d.mode; c.unclamped = d.unclamped; c.T = d.T; c.V = d.V;
+      c.tris = d.tris; c.vtx = b.vtx + d.vtx_base; c.color = d.color; c.normal = d.normal; c.light = d.light;
+      c.invw = b.invw ? b.invw + d.vtx_base : nullptr;
+      c.pos = nullptr;  // batches do not clip
+      c.mvp = nullptr;
+      c.key = d.key_out; c.dl = d.dl; c.dcolor = d.dcolor; c.dnormal = d.dnormal; c.dlight = d.dlight;
+    }
+    __syncwarp();
     float L0 = 0.f, L1 = 0.f, L2 = 0.f;
     if (c.mode == PIKO_SHADE_LAMBERT) {
       L0 = __ldg(c.light); L1 = __ldg(c.light + 1); L2 = __ldg(c.light + 2);
@@ -495,10 +506,10 @@ __global__ void __launch_bounds__(BWD_THREADS, 1024 / BWD_THREADS) k_batch_backw
     const int lt = i - __ldg(b.btile_prefix + s);
     const int ntx = (c.W + BWD_TILE_W - 1) / BWD_TILE_W;
     const int ty = lt / ntx, tx = lt - ty * ntx;
-    backward_tile<PERSP>(c, tx * BWD_TILE_W, ty * BWD_TILE_H, sm, L0, L1, L2, gl0, gl1, gl2);
-    if (c.dlight && c.mode == PIKO_SHADE_LAMBERT) bwd_flush_light(sm, c.dlight, gl0, gl1, gl2);
+    backward_warp_tile<PERSP>(c, tx * BWD_TILE_W, ty * BWD_TILE_H, sm.stage[warp], L0, L1, L2);
   }
 }
+constexpr size_t BATCH_BWD_SMEM = sizeof(BatchBwdSmem);
 
 }  // namespace piko
 
@@ -882,22 +893,23 @@ int batch_launch_backward(BatchState* bs, const piko_scene* scenes, int n, const
     int v = 0;
     // both instances share the launch bounds and the shared-memory size
     if (cudaFuncSetAttribute(k_batch_backward<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(BwdSmem)) != cudaSuccess ||
+                             (int)BATCH_BWD_SMEM) != cudaSuccess ||
         cudaFuncSetAttribute(k_batch_backward<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(BwdSmem)) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_batch_backward<false>, BWD_THREADS, sizeof(BwdSmem)) !=
+                             (int)BATCH_BWD_SMEM) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_batch_backward<false>, BWD_THREADS, BATCH_BWD_SMEM) !=
             cudaSuccess ||
         v < 1)
       v = 1;
     per_sm = v;
   }
   long long blocks = (long long)per_sm * num_sms;
-  if (blocks > p.total_btiles) blocks = p.total_btiles;
+  const long long need = (p.total_btiles + BATCH_BWD_WARPS - 1) / BATCH_BWD_WARPS;  // a tile per warp
+  if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
   if (bs->persp)
-    k_batch_backward<true><<<(int)blocks, BWD_THREADS, sizeof(BwdSmem), stream>>>(p);
+    k_batch_backward<true><<<(int)blocks, BWD_THREADS, BATCH_BWD_SMEM, stream>>>(p);
   else
-    k_batch_backward<false><<<(int)blocks, BWD_THREADS, sizeof(BwdSmem), stream>>>(p);
+    k_batch_backward<false><<<(int)blocks, BWD_THREADS, BATCH_BWD_SMEM, stream>>>(p);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     err = std::string("batch backward launch: ") + cudaGetErrorString(e);

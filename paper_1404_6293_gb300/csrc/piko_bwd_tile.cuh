@@ -10,20 +10,15 @@
 //   dL/dn_i += (g . albedo) b_i L   when s > 0 (or unclamped)
 //   dL/dL   += (g . albedo) n
 //
-// One CTA of BWD_THREADS threads takes a 16-pixel-wide tile, one pixel per thread:
-//  1. the distinct winning triangles of the tile go into a shared hash table
-//     (one insert per group of lanes with the same triangle);
-//  2. the table is compacted into slots and each slot's triangle is set up
-//     once (vertex indices, snapped positions, 2 x area);
-//  3. every pixel computes its 12 terms (below) from its slot's setup; the
-//     lanes of a warp that share a slot are summed, one lane per term, into
-//     the slot's shared accumulators;
-//  4. each slot then issues its gradient atomics (9 colour, 9 normal) and
-//     adds its share of the light gradient.
-// So the setup runs once per (tile, visible triangle) and the global atomics
-// number 18 per (tile, visible triangle) instead of per pixel group.  Tiles of
-// tiny triangles (more than BWD_DIRECT_SLOTS of them) add their terms to the
-// gradients directly, per pixel or per group of lanes.
+// A warp takes a 16 x 16 tile of pixels (backward_warp_tile, below) with no
+// CTA barrier: the warps of a CTA work on separate tiles.  Each lane walks a
+// column of the tile and keeps, for as long as its pixels keep the same
+// winning triangle (a run), that triangle's setup (vertex indices, snapped
+// positions, 2 x area) and the sums of its 12 per-pixel terms (below) in
+// registers; a run that ends is summed with the other lanes' runs of the same
+// triangle and added to the gradient arrays with one set of atomics.  A
+// triangle is set up once per run rather than per pixel, and a triangle that
+// covers a column of the tile is flushed once for it.
 #pragma once
 
 #include "piko_internal.cuh"
@@ -33,11 +28,9 @@ namespace piko {
 #ifndef PIKO_BWD_TILE_H
 #define PIKO_BWD_TILE_H 16
 #endif
-constexpr int BWD_TILE_W = 16;               // pixels per tile row (a warp covers two rows)
+constexpr int BWD_TILE_W = 16;               // pixels per tile row (a warp pass covers two rows)
 constexpr int BWD_TILE_H = PIKO_BWD_TILE_H;  // rows per tile
-constexpr int BWD_THREADS = BWD_TILE_W * BWD_TILE_H;
-constexpr int BWD_HASH_BITS = BWD_THREADS > 128 ? 9 : 8;
-constexpr int BWD_HASH = 1 << BWD_HASH_BITS;  // twice the most distinct triangles a tile can hold
+constexpr int BWD_THREADS = 256;             // CTA size of the backward kernels (8 warps, a tile each)
 // Terms per pixel: q = 3 j + c (c < 3) is g_c s b_j, the colour gradient of
 // vertex j (g_c b_j for Gouraud); q = 9 + j is G b_j with G = g . albedo
 // (0 where the clamp is inactive).  The normal and light gradients are
@@ -45,12 +38,6 @@ constexpr int BWD_HASH = 1 << BWD_HASH_BITS;  // twice the most distinct triangl
 // sum(G b_j), so they are formed once per slot from the sums.
 constexpr int BWD_VALS = 12;
 constexpr unsigned BWD_NONE = 0xFFFFFFFFu;
-
-// per-slot words: oriented X0 Y0 X1 Y1 X2 Y2, vertex ids v0 v1 v2, A (lo, hi),
-// the triangle id (replaced by 1/A once the slot is set up), a valid flag and
-// n_j . L of the three vertices (Lambert); 17 words (odd: distinct slots fall
-// in distinct banks)
-constexpr int RB_V = 6, RB_ALO = 9, RB_AHI = 10, RB_T = 11, RB_OK = 12, RB_VD = 13, BWD_REC = 17;
 
 struct BwdScene {
   int W, H, mode, unclamped, T, V;
@@ -69,59 +56,136 @@ struct BwdScene {
   float* dlight;
 };
 
-// Tiles with more distinct triangles than this (under 3 pixels per triangle)
-// skip the shared accumulators: their slots would each collect only a pixel
-// or two, so the terms go straight to the gradient arrays.
-constexpr int BWD_DIRECT_SLOTS = 96;
+// ---------------------------------------------------------------- warp form
+// One warp takes a BWD_TILE_W x BWD_TILE_H tile in passes of 16 x 2 pixels:
+// lane l follows column l mod 16 down the rows of parity l / 16.  A run that
+// ends is flushed (bwd_run_flush): lanes ending runs of the same triangle
+// are summed through the warp's staging area, one lane per term, with one
+// set of atomics per group, and runs of one or two lanes add their own terms.
 
-struct BwdSmem {
-  unsigned hkey[BWD_HASH];
-  unsigned short hslot[BWD_HASH];
-  int rec[BWD_THREADS * BWD_REC];
-  float acc[BWD_DIRECT_SLOTS * BWD_VALS];  // only tiles with at most BWD_DIRECT_SLOTS slots accumulate here
-  float stage[BWD_THREADS / 32][BWD_VALS][33];  // padded: lane q reads row q, column m
-  float lred[BWD_THREADS / 32][3];
-  int nslot;
+// The setup of a lane's current triangle: oriented snapped positions, A
+// (lo, hi words), 1/A, vertex ids, n_j . L (Lambert) and kind (0: nothing to
+// add, 1: covered by its snapped edges, 2: clipped winner, ray weights).
+struct BwdRun {
+  int X0, Y0, X1, Y1, X2, Y2, alo, ahi;
+  float rA, d0, d1, d2;
+  int v0, v1, v2, kind;
 };
 
-__device__ __forceinline__ void bwd_clear(BwdSmem& sm) {
-  for (int e = threadIdx.x; e < BWD_HASH; e += blockDim.x) sm.hkey[e] = BWD_NONE;
-  if (threadIdx.x == 0) sm.nslot = 0;
+__device__ __forceinline__ BwdRun bwd_run_shfl(const BwdRun& r, int src) {
+  BwdRun o;
+  o.X0 = __shfl_sync(FULL_MASK, r.X0, src); o.Y0 = __shfl_sync(FULL_MASK, r.Y0, src);
+  o.X1 = __shfl_sync(FULL_MASK, r.X1, src); o.Y1 = __shfl_sync(FULL_MASK, r.Y1, src);
+  o.X2 = __shfl_sync(FULL_MASK, r.X2, src); o.Y2 = __shfl_sync(FULL_MASK, r.Y2, src);
+  o.alo = __shfl_sync(FULL_MASK, r.alo, src); o.ahi = __shfl_sync(FULL_MASK, r.ahi, src);
+  o.rA = __shfl_sync(FULL_MASK, r.rA, src);
+  o.d0 = __shfl_sync(FULL_MASK, r.d0, src); o.d1 = __shfl_sync(FULL_MASK, r.d1, src);
+  o.d2 = __shfl_sync(FULL_MASK, r.d2, src);
+  o.v0 = __shfl_sync(FULL_MASK, r.v0, src); o.v1 = __shfl_sync(FULL_MASK, r.v1, src);
+  o.v2 = __shfl_sync(FULL_MASK, r.v2, src);
+  o.kind = __shfl_sync(FULL_MASK, r.kind, src);
+  return o;
 }
 
-// Sums the CTA's light-gradient shares (all threads call it; it has barriers).
-__device__ __forceinline__ void bwd_flush_light(BwdSmem& sm, float* dlight, float& gl0, float& gl1, float& gl2) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int o = 16; o > 0; o >>= 1) {
-    gl0 += __shfl_xor_sync(FULL_MASK, gl0, o);
-    gl1 += __shfl_xor_sync(FULL_MASK, gl1, o);
-    gl2 += __shfl_xor_sync(FULL_MASK, gl2, o);
+// Sets up triangle t (a winner of this scene) for the backward pass.  CLIP:
+// near/far clipping may be on (sc.pos set).
+template <bool CLIP>
+__device__ __forceinline__ void bwd_run_setup(const BwdScene& sc, unsigned t, float L0, float L1, float L2,
+                                              BwdRun& r) {
+  const int ia = __ldg(sc.tris + 3 * (size_t)t), ib = __ldg(sc.tris + 3 * (size_t)t + 1),
+            ic = __ldg(sc.tris + 3 * (size_t)t + 2);
+  const bool in_range = ia >= 0 && ia < sc.V && ib >= 0 && ib < sc.V && ic >= 0 && ic < sc.V;
+  TriSetup ts;
+  const bool ok = in_range && setup_triangle(ia, ib, ic, sc.vtx, ts);
+  // a winner the vertex stage rejected was clipped: per-pixel ray weights
+  const bool clipped = CLIP && !ok && in_range && sc.pos;
+  r.kind = ok ? 1 : (clipped ? 2 : 0);
+  if (ok) {
+    r.X0 = ts.X0; r.Y0 = ts.Y0; r.X1 = ts.X1; r.Y1 = ts.Y1; r.X2 = ts.X2; r.Y2 = ts.Y2;
+    r.v0 = ts.v0; r.v1 = ts.v1; r.v2 = ts.v2;
+    r.alo = (int)(unsigned)(ts.A & 0xFFFFFFFFll);
+    r.ahi = (int)(ts.A >> 32);
+    r.rA = __frcp_rn(f32_from_i64(ts.A));
+  } else {
+    r.v0 = ia; r.v1 = ib; r.v2 = ic;
   }
-  if (lane == 0) {
-    sm.lred[warp][0] = gl0; sm.lred[warp][1] = gl1; sm.lred[warp][2] = gl2;
+  if (r.kind != 0 && sc.mode == PIKO_SHADE_LAMBERT) {
+    const float* n0 = sc.normal + 3 * (size_t)r.v0;
+    const float* n1 = sc.normal + 3 * (size_t)r.v1;
+    const float* n2 = sc.normal + 3 * (size_t)r.v2;
+    r.d0 = __ldg(n0) * L0 + __ldg(n0 + 1) * L1 + __ldg(n0 + 2) * L2;
+    r.d1 = __ldg(n1) * L0 + __ldg(n1 + 1) * L1 + __ldg(n1 + 2) * L2;
+    r.d2 = __ldg(n2) * L0 + __ldg(n2 + 1) * L1 + __ldg(n2 + 2) * L2;
   }
-  __syncthreads();
-  if (threadIdx.x < 3) {
-    float a = 0.f;
-    for (int w = 0; w < BWD_THREADS / 32; ++w) a += sm.lred[w][threadIdx.x];
-    if (a != 0.f) atomicAdd(dlight + threadIdx.x, a);
-  }
-  gl0 = gl1 = gl2 = 0.f;
-  __syncthreads();
 }
 
-// Adds term q of slot record r to the scene's gradients: a colour term goes
-// to dL/dc of its vertex; a G b_j sum goes to dL/dn_j (times L) and, when
-// `light` is set, to this thread's share of dL/dL (times n_j).
-__device__ __forceinline__ void bwd_add_term(const BwdScene& sc, const int* r, int q, float val, bool has_c,
-                                             bool has_n, bool light, float L0, float L1, float L2, float& gl0,
-                                             float& gl1, float& gl2) {
-  if (q < 9) {
-    const int j = q / 3, c = q - 3 * j;
-    if (has_c) atomicAdd(sc.dcolor + 3 * (size_t)r[RB_V + j] + c, val);
+// Adds the 12 terms of pixel (x, y), covered by run r, with dL/drgba g, to acc.
+template <bool PERSP, bool CLIP>
+__device__ __forceinline__ void bwd_run_terms(const BwdScene& sc, const BwdRun& r, int x, int y, const float4 g,
+                                              float (&acc)[BWD_VALS]) {
+  const int vid[3] = {r.v0, r.v1, r.v2};
+  float b[3];
+  if (CLIP && r.kind == 2) {
+    clip_ray_weights(sc.pos, sc.mvp, sc.W, sc.H, vid, x, y, b[0], b[1], b[2]);
+  } else if (r.ahi == 0 && r.alo >= 0) {
+    // A < 2^31: the covered pixel's edge functions lie in [0, A], exact in
+    // wrapping 32-bit arithmetic
+    const int Px = 256 * x + 128, Py = 256 * y + 128;
+    const int w1 = edge_fn_wrap32(r.X2, r.Y2, r.X0, r.Y0, Px, Py), w2 = edge_fn_wrap32(r.X0, r.Y0, r.X1, r.Y1, Px, Py);
+    const int w0 = r.alo - w1 - w2;  // the three edge functions sum to A
+    b[0] = (float)w0 * r.rA; b[1] = (float)w1 * r.rA; b[2] = (float)w2 * r.rA;
+  } else {
+    const long long A = (long long)(((unsigned long long)(unsigned)r.ahi << 32) | (unsigned)r.alo);
+    const long long Px = 256LL * x + 128, Py = 256LL * y + 128;
+    const long long w1 = (long long)(r.X0 - r.X2) * (Py - r.Y2) - (long long)(r.Y0 - r.Y2) * (Px - r.X2);
+    const long long w2 = (long long)(r.X1 - r.X0) * (Py - r.Y0) - (long long)(r.Y1 - r.Y0) * (Px - r.X0);
+    const long long w0 = A - w1 - w2;
+    b[0] = f32_from_i64(w0) * r.rA; b[1] = f32_from_i64(w1) * r.rA; b[2] = f32_from_i64(w2) * r.rA;
+  }
+  if (PERSP && r.kind == 1)
+    perspective_bary(b[0], b[1], b[2], __ldg(sc.invw + vid[0]), __ldg(sc.invw + vid[1]), __ldg(sc.invw + vid[2]));
+  if (sc.mode == PIKO_SHADE_GOURAUD) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      acc[3 * j] += g.x * b[j]; acc[3 * j + 1] += g.y * b[j]; acc[3 * j + 2] += g.z * b[j];
+    }
     return;
   }
-  const size_t vb = 3 * (size_t)r[RB_V + (q - 9)];
+  float a0 = 0.80f, a1 = 0.75f, a2 = 0.65f;  // material of Listing 1 without colours
+  if (sc.color) {
+    a0 = a1 = a2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float* c = sc.color + 3 * (size_t)vid[j];
+      a0 += b[j] * __ldg(c); a1 += b[j] * __ldg(c + 1); a2 += b[j] * __ldg(c + 2);
+    }
+  }
+  // n . L = sum_j b_j (n_j . L), by linearity
+  const float d = b[0] * r.d0 + b[1] * r.d1 + b[2] * r.d2;
+  const bool active = sc.unclamped || d > 0.f;
+  const float sh = sc.unclamped ? d : fmaxf(d, 0.f);
+  const float G = active ? (g.x * a0 + g.y * a1 + g.z * a2) : 0.f;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    if (sc.color) {
+      acc[3 * j] += g.x * sh * b[j]; acc[3 * j + 1] += g.y * sh * b[j]; acc[3 * j + 2] += g.z * sh * b[j];
+    }
+    acc[9 + j] += G * b[j];
+  }
+}
+
+// Adds term q (see BWD_VALS) with value val of a triangle whose vertex j (the
+// vertex of term q) is vj to the scene's gradients: a colour term goes to
+// dL/dc of the vertex; a G b_j sum goes to dL/dn_j (times L) and, when
+// `light` is set, to this thread's share of dL/dL (times n_j).
+__device__ __forceinline__ void bwd_add_term_v(const BwdScene& sc, int vj, int q, float val, bool has_c, bool has_n,
+                                               bool light, float L0, float L1, float L2, float& gl0, float& gl1,
+                                               float& gl2) {
+  if (q < 9) {
+    if (has_c) atomicAdd(sc.dcolor + 3 * (size_t)vj + (q % 3), val);
+    return;
+  }
+  const size_t vb = 3 * (size_t)vj;
   if (has_n) {
     atomicAdd(sc.dnormal + vb, val * L0);
     atomicAdd(sc.dnormal + vb + 1, val * L1);
@@ -134,216 +198,113 @@ __device__ __forceinline__ void bwd_add_term(const BwdScene& sc, const int* r, i
   }
 }
 
-// One tile with its top-left pixel (x0, y0).  Entered and left with a clear
-// hash table (bwd_clear once per CTA before the first tile); blockDim.x must
-// be BWD_THREADS.  gl* collect this thread's share of dL/dL.
-// PERSP: perspective-correct barycentrics (sc.invw set).
-template <bool PERSP = false>
-__device__ __forceinline__ void backward_tile(const BwdScene& sc, int x0, int y0, BwdSmem& sm, float L0, float L1,
-                                              float L2, float& gl0, float& gl1, float& gl2) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int x = x0 + (tid & (BWD_TILE_W - 1)), y = y0 + tid / BWD_TILE_W;  // a warp covers 16 x 2 pixels
-  const bool inside = x < sc.W && y < sc.H;
-  const size_t o = (size_t)y * sc.W + x;
-  unsigned t = BWD_NONE;
-  if (inside) {
-    const unsigned long long k = __ldg(sc.key + o);
-    // a key naming a triangle outside this scene contributes nothing (it
-    // cannot come from this scene's forward)
-    if (k != KEY_EMPTY && (unsigned)k < (unsigned)sc.T) t = (unsigned)k;
-  }
-  // 1. distinct triangles into the hash table (empty on entry)
-  const unsigned grp = __match_any_sync(FULL_MASK, t);
-  const int leader = __ffs(grp) - 1;
-  int h = 0;
-  if (t != BWD_NONE && lane == leader) {
-    h = (int)((t * 2654435761u) >> (32 - BWD_HASH_BITS));
-    // at most BWD_THREADS keys in BWD_HASH entries: a free or equal entry
-    // is always found
-    for (int probe = 0; probe < BWD_HASH; ++probe) {
-      const unsigned old = atomicCAS(&sm.hkey[h], BWD_NONE, t);
-      if (old == BWD_NONE || old == t) break;
-      h = (h + 1) & (BWD_HASH - 1);
-    }
-  }
-  // the inserts are complete after this barrier; with nothing visible the
-  // table stayed clear and the tile is done
-  if (!__syncthreads_or(t != BWD_NONE)) return;
-  // 2. slots for the occupied entries; one setup per slot
-  for (int e = tid; e < BWD_HASH; e += BWD_THREADS) {
-    const unsigned key = sm.hkey[e];
-    if (key != BWD_NONE) {
-      const int s = atomicAdd(&sm.nslot, 1);
-      sm.hslot[e] = (unsigned short)s;
-      sm.rec[s * BWD_REC + RB_T] = (int)key;
-    }
-  }
-  __syncthreads();
-  const int nslot = sm.nslot;
-  const bool direct = nslot > BWD_DIRECT_SLOTS;
-  for (int s = tid; s < nslot; s += BWD_THREADS) {
-    int* r = sm.rec + s * BWD_REC;
-    const unsigned tri = (unsigned)r[RB_T];
-    const int ia = __ldg(sc.tris + 3 * (size_t)tri), ib = __ldg(sc.tris + 3 * (size_t)tri + 1),
-              ic = __ldg(sc.tris + 3 * (size_t)tri + 2);
-    TriSetup ts;
-    const bool in_range = ia >= 0 && ia < sc.V && ib >= 0 && ib < sc.V && ic >= 0 && ic < sc.V;
-    const bool ok = in_range && setup_triangle(ia, ib, ic, sc.vtx, ts);
-    // a winner the vertex stage rejected was clipped: per-pixel ray weights (2)
-    const bool clipped = !ok && in_range && sc.pos;
-    r[RB_OK] = ok ? 1 : (clipped ? 2 : 0);
-    if (clipped) {
-      ts.v0 = ia; ts.v1 = ib; ts.v2 = ic;
-      r[RB_V] = ia; r[RB_V + 1] = ib; r[RB_V + 2] = ic;
-      if (sc.mode == PIKO_SHADE_LAMBERT) {
-        const int vid[3] = {ia, ib, ic};
+// Flushes the runs of the lanes with fl set (t: their triangle, r: its
+// setup, acc: their sums, cleared here).  Warp-collective.
+__device__ __forceinline__ void bwd_run_flush(const BwdScene& sc, bool fl, unsigned t, const BwdRun& r,
+                                              float (&acc)[BWD_VALS], float (*stage)[33], bool has_c, bool has_n,
+                                              bool has_l, float L0, float L1, float L2, float& gl0, float& gl1,
+                                              float& gl2) {
+  const int lane = threadIdx.x & 31;
+  const unsigned grp = __match_any_sync(FULL_MASK, fl ? t : BWD_NONE);
+  const bool own = fl && __popc(grp) <= 2;
+  if (own) {
+    const int vid[3] = {r.v0, r.v1, r.v2};
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          const float* nn = sc.normal + 3 * (size_t)vid[j];
-          r[RB_VD + j] = __float_as_int(__ldg(nn) * L0 + __ldg(nn + 1) * L1 + __ldg(nn + 2) * L2);
-        }
+    for (int q = 0; q < BWD_VALS; ++q)
+      if (acc[q] != 0.f)
+        bwd_add_term_v(sc, vid[q < 9 ? q / 3 : q - 9], q, acc[q], has_c, has_n, has_l, L0, L1, L2, gl0, gl1, gl2);
+  }
+  unsigned big = __ballot_sync(FULL_MASK, fl && !own);
+  if (big != 0u) {
+#pragma unroll
+    for (int q = 0; q < BWD_VALS; ++q) stage[q][lane] = acc[q];
+    __syncwarp();
+    // every round removes at least the round's leader lane
+    for (int round = 0; big != 0u && round < 32; ++round) {
+      const int ld = __ffs(big) - 1;
+      const unsigned gm = __shfl_sync(FULL_MASK, grp, ld);
+      const int u0 = __shfl_sync(FULL_MASK, r.v0, ld), u1 = __shfl_sync(FULL_MASK, r.v1, ld),
+                u2 = __shfl_sync(FULL_MASK, r.v2, ld);
+      big &= ~gm;
+      if (lane < BWD_VALS) {
+        float sum = 0.f;
+        for (unsigned m = gm; m; m &= m - 1) sum += stage[lane][__ffs(m) - 1];
+        const int j = lane < 9 ? lane / 3 : lane - 9;
+        if (sum != 0.f)
+          bwd_add_term_v(sc, j == 0 ? u0 : (j == 1 ? u1 : u2), lane, sum, has_c, has_n, has_l, L0, L1, L2, gl0, gl1,
+                         gl2);
       }
     }
-    if (ok) {
-      r[0] = ts.X0; r[1] = ts.Y0; r[2] = ts.X1; r[3] = ts.Y1; r[4] = ts.X2; r[5] = ts.Y2;
-      r[RB_V] = ts.v0; r[RB_V + 1] = ts.v1; r[RB_V + 2] = ts.v2;
-      r[RB_ALO] = (int)(unsigned)(ts.A & 0xFFFFFFFFll);
-      r[RB_AHI] = (int)(ts.A >> 32);
-      r[RB_T] = __float_as_int(__frcp_rn(f32_from_i64(ts.A)));
-      if (sc.mode == PIKO_SHADE_LAMBERT) {
-        const int vid[3] = {ts.v0, ts.v1, ts.v2};
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          const float* nn = sc.normal + 3 * (size_t)vid[j];
-          r[RB_VD + j] = __float_as_int(__ldg(nn) * L0 + __ldg(nn + 1) * L1 + __ldg(nn + 2) * L2);
-        }
-      }
-    }
-    if (!direct) {
-      float* a = sm.acc + s * BWD_VALS;
-#pragma unroll
-      for (int q = 0; q < BWD_VALS; ++q) a[q] = 0.f;
-    }
+    __syncwarp();  // the staging area is rewritten by the next flush
   }
-  const int hl = __shfl_sync(FULL_MASK, h, leader);
-  const int slot = t != BWD_NONE ? (int)sm.hslot[hl] : -1;
-  __syncthreads();
-  // 3. per-pixel terms
-  float v[BWD_VALS];
+  if (fl) {
 #pragma unroll
-  for (int q = 0; q < BWD_VALS; ++q) v[q] = 0.f;
-  bool hit = false;
-  const int* r = sm.rec + (slot >= 0 ? slot : 0) * BWD_REC;
-  if (slot >= 0 && r[RB_OK]) {
-    hit = true;
-    const int X0 = r[0], Y0 = r[1], X1 = r[2], Y1 = r[3], X2 = r[4], Y2 = r[5];
-    const long long A = (long long)(((unsigned long long)(unsigned)r[RB_AHI] << 32) | (unsigned)r[RB_ALO]);
-    const int vid[3] = {r[RB_V], r[RB_V + 1], r[RB_V + 2]};
-    const float rA = __int_as_float(r[RB_T]);
-    float b[3];
-    if (r[RB_OK] == 2) {
-      clip_ray_weights(sc.pos, sc.mvp, sc.W, sc.H, vid, x, y, b[0], b[1], b[2]);
-    } else if (A < (1LL << 31)) {
-      // the pixel is covered: its edge functions lie in [0, A], exact in wrapping 32-bit arithmetic
-      const int Px = 256 * x + 128, Py = 256 * y + 128;
-      const int w1 = edge_fn_wrap32(X2, Y2, X0, Y0, Px, Py), w2 = edge_fn_wrap32(X0, Y0, X1, Y1, Px, Py);
-      const int w0 = (int)A - w1 - w2;  // the three edge functions sum to A
-      b[0] = (float)w0 * rA; b[1] = (float)w1 * rA; b[2] = (float)w2 * rA;
-    } else {
-      const long long Px = 256LL * x + 128, Py = 256LL * y + 128;
-      const long long w1 = (long long)(X0 - X2) * (Py - Y2) - (long long)(Y0 - Y2) * (Px - X2);
-      const long long w2 = (long long)(X1 - X0) * (Py - Y0) - (long long)(Y1 - Y0) * (Px - X0);
-      const long long w0 = A - w1 - w2;
-      b[0] = f32_from_i64(w0) * rA; b[1] = f32_from_i64(w1) * rA; b[2] = f32_from_i64(w2) * rA;
-    }
-    if (PERSP && r[RB_OK] == 1)
-      perspective_bary(b[0], b[1], b[2], __ldg(sc.invw + vid[0]), __ldg(sc.invw + vid[1]), __ldg(sc.invw + vid[2]));
-    const float4 g = __ldg(sc.dl + o);
-    if (sc.mode == PIKO_SHADE_GOURAUD) {
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        v[3 * j] = g.x * b[j]; v[3 * j + 1] = g.y * b[j]; v[3 * j + 2] = g.z * b[j];
-      }
-    } else {
-      float a0 = 0.80f, a1 = 0.75f, a2 = 0.65f;  // material of Listing 1 without colours
-      if (sc.color) {
-        a0 = a1 = a2 = 0.f;
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          const float* c = sc.color + 3 * (size_t)vid[j];
-          a0 += b[j] * __ldg(c); a1 += b[j] * __ldg(c + 1); a2 += b[j] * __ldg(c + 2);
-        }
-      }
-      // n . L = sum_j b_j (n_j . L), by linearity
-      const float d = b[0] * __int_as_float(r[RB_VD]) + b[1] * __int_as_float(r[RB_VD + 1]) +
-                      b[2] * __int_as_float(r[RB_VD + 2]);
-      const bool active = sc.unclamped || d > 0.f;
-      const float sh = sc.unclamped ? d : fmaxf(d, 0.f);
-      const float G = active ? (g.x * a0 + g.y * a1 + g.z * a2) : 0.f;
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        if (sc.color) {
-          v[3 * j] = g.x * sh * b[j]; v[3 * j + 1] = g.y * sh * b[j]; v[3 * j + 2] = g.z * sh * b[j];
-        }
-        v[9 + j] = G * b[j];
-      }
-    }
+    for (int q = 0; q < BWD_VALS; ++q) acc[q] = 0.f;
   }
+}
+
+// One tile with its top-left pixel (x0, y0), taken by one warp (all 32 lanes
+// call it with the same arguments); stage is the warp's own staging area.
+// The tile's share of dL/dL is added at its end.  A triangle that starts a
+// run is set up by the lowest lane of the warp that holds it and broadcast to
+// the lanes that need it; a lane whose run goes on keeps its setup.
+// CLIP: near/far clipping may be on (sc.pos set).
+template <bool PERSP = false, bool CLIP = false>
+__device__ __forceinline__ void backward_warp_tile(const BwdScene& sc, int x0, int y0, float (*stage)[33], float L0,
+                                                   float L1, float L2) {
+  const int lane = threadIdx.x & 31;
   const bool has_c = sc.dcolor != nullptr && (sc.mode == PIKO_SHADE_GOURAUD || sc.color != nullptr);
   const bool has_n = sc.dnormal != nullptr && sc.mode == PIKO_SHADE_LAMBERT;
   const bool has_l = sc.dlight != nullptr && sc.mode == PIKO_SHADE_LAMBERT;
-  // 4. Lanes of a group of at most two add their own terms (to the slot's
-  // accumulators, or straight to the gradients in direct tiles).  Larger
-  // groups are summed term by term first: lane q adds term q over the group.
-  const unsigned gsize = hit ? (unsigned)__popc(grp) : 0u;
-  if (__reduce_max_sync(FULL_MASK, gsize) <= 2u) {
-    if (hit) {
-      if (direct) {
+  float gl0 = 0.f, gl1 = 0.f, gl2 = 0.f;
+  float acc[BWD_VALS];
 #pragma unroll
-        for (int q = 0; q < BWD_VALS; ++q)
-          if (v[q] != 0.f) bwd_add_term(sc, r, q, v[q], has_c, has_n, has_l, L0, L1, L2, gl0, gl1, gl2);
-      } else {
-        float* a = sm.acc + slot * BWD_VALS;
-#pragma unroll
-        for (int q = 0; q < BWD_VALS; ++q) atomicAdd(a + q, v[q]);
-      }
+  for (int q = 0; q < BWD_VALS; ++q) acc[q] = 0.f;
+  BwdRun r = {0, 0, 0, 0, 0, 0, 0, 0, 0.f, 0.f, 0.f, 0.f, 0, 0, 0, 0};
+  unsigned cur = BWD_NONE;
+  const int x = x0 + (lane & 15);
+  for (int pass = 0; pass < BWD_TILE_H / 2; ++pass) {
+    const int y = y0 + 2 * pass + (lane >> 4);
+    const bool inside = x < sc.W && y < sc.H;
+    const size_t o = (size_t)y * sc.W + x;
+    unsigned t = BWD_NONE;
+    if (inside) {
+      const unsigned long long k = __ldg(sc.key + o);
+      // a key naming a triangle outside this scene contributes nothing (it
+      // cannot come from this scene's forward)
+      if (k != KEY_EMPTY && (unsigned)k < (unsigned)sc.T) t = (unsigned)k;
     }
-  } else {
-#pragma unroll
-    for (int q = 0; q < BWD_VALS; ++q) sm.stage[warp][q][lane] = v[q];
-    __syncwarp();
-    unsigned todo = __ballot_sync(FULL_MASK, hit);
-    // every round removes at least the round's leader lane
-    for (int round = 0; todo != 0u && round < 32; ++round) {
-      const int ld = __ffs(todo) - 1;
-      const unsigned gm = __shfl_sync(FULL_MASK, grp, ld);
-      const int gs = __shfl_sync(FULL_MASK, slot, ld);
-      todo &= ~gm;
-      if (lane < BWD_VALS) {
-        float sum = 0.f;
-        for (unsigned m = gm; m; m &= m - 1) sum += sm.stage[warp][lane][__ffs(m) - 1];
-        if (direct) {
-          if (sum != 0.f)
-            bwd_add_term(sc, sm.rec + gs * BWD_REC, lane, sum, has_c, has_n, has_l, L0, L1, L2, gl0, gl1, gl2);
-        } else {
-          atomicAdd(sm.acc + gs * BWD_VALS + lane, sum);
-        }
-      }
+    const bool change = t != cur;
+    const bool ends = change && r.kind != 0;
+    if (__any_sync(FULL_MASK, ends))
+      bwd_run_flush(sc, ends, cur, r, acc, stage, has_c, has_n, has_l, L0, L1, L2, gl0, gl1, gl2);
+    const bool need = change && t != BWD_NONE;
+    if (__any_sync(FULL_MASK, need)) {
+      const int leader = __ffs(__match_any_sync(FULL_MASK, t)) - 1;
+      // a leader whose run goes on already holds the setup
+      if (need && lane == leader) bwd_run_setup<CLIP>(sc, t, L0, L1, L2, r);
+      const BwdRun s = bwd_run_shfl(r, leader);
+      if (need) r = s;
+    }
+    cur = t;
+    if (t == BWD_NONE) r.kind = 0;
+    if (r.kind != 0) bwd_run_terms<PERSP, CLIP>(sc, r, x, y, __ldg(sc.dl + o), acc);
+  }
+  const bool ends = r.kind != 0;
+  if (__any_sync(FULL_MASK, ends))
+    bwd_run_flush(sc, ends, cur, r, acc, stage, has_c, has_n, has_l, L0, L1, L2, gl0, gl1, gl2);
+  if (has_l) {
+    for (int o = 16; o > 0; o >>= 1) {
+      gl0 += __shfl_xor_sync(FULL_MASK, gl0, o);
+      gl1 += __shfl_xor_sync(FULL_MASK, gl1, o);
+      gl2 += __shfl_xor_sync(FULL_MASK, gl2, o);
+    }
+    if (lane == 0) {
+      if (gl0 != 0.f) atomicAdd(sc.dlight, gl0);
+      if (gl1 != 0.f) atomicAdd(sc.dlight + 1, gl1);
+      if (gl2 != 0.f) atomicAdd(sc.dlight + 2, gl2);
     }
   }
-  __syncthreads();
-  // 5. one set of gradient atomics per (slot, term); the hash table (no
-  // longer read) is cleared for the next tile meanwhile
-  if (!direct) {
-    for (int idx = tid; idx < nslot * BWD_VALS; idx += BWD_THREADS) {
-      const int s = idx / BWD_VALS, q = idx - s * BWD_VALS;
-      const int* rs = sm.rec + s * BWD_REC;
-      const float val = sm.acc[idx];
-      if (rs[RB_OK] && val != 0.f) bwd_add_term(sc, rs, q, val, has_c, has_n, has_l, L0, L1, L2, gl0, gl1, gl2);
-    }
-  }
-  bwd_clear(sm);
-  __syncthreads();
 }
 
 }  // namespace piko

@@ -263,17 +263,21 @@ __device__ __forceinline__ void backward_warp_tile(const BwdScene& sc, int x0, i
   BwdRun r = {0, 0, 0, 0, 0, 0, 0, 0, 0.f, 0.f, 0.f, 0.f, 0, 0, 0, 0};
   unsigned cur = BWD_NONE;
   const int x = x0 + (lane & 15);
+  // the triangle word (low half) of the next pass's key is loaded a pass
+  // ahead; an empty key's word is all ones
+  const unsigned* kw = reinterpret_cast<const unsigned*>(sc.key);
+  unsigned knext = x < sc.W && y0 + (lane >> 4) < sc.H ? __ldg(kw + 2 * ((size_t)(y0 + (lane >> 4)) * sc.W + x))
+                                                       : BWD_NONE;
   for (int pass = 0; pass < BWD_TILE_H / 2; ++pass) {
     const int y = y0 + 2 * pass + (lane >> 4);
-    const bool inside = x < sc.W && y < sc.H;
     const size_t o = (size_t)y * sc.W + x;
-    unsigned t = BWD_NONE;
-    if (inside) {
-      const unsigned long long k = __ldg(sc.key + o);
-      // a key naming a triangle outside this scene contributes nothing (it
-      // cannot come from this scene's forward)
-      if (k != KEY_EMPTY && (unsigned)k < (unsigned)sc.T) t = (unsigned)k;
-    }
+    // a key naming a triangle outside this scene contributes nothing (it
+    // cannot come from this scene's forward)
+    const unsigned t = knext < (unsigned)sc.T ? knext : BWD_NONE;
+    if (pass + 1 < BWD_TILE_H / 2)
+      knext = x < sc.W && y + 2 < sc.H ? __ldg(kw + 2 * (o + 2 * (size_t)sc.W)) : BWD_NONE;
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (t != BWD_NONE) g = __ldg(sc.dl + o);  // issued before the flush and setup it does not need
     const bool change = t != cur;
     const bool ends = change && r.kind != 0;
     if (__any_sync(FULL_MASK, ends))
@@ -288,7 +292,7 @@ __device__ __forceinline__ void backward_warp_tile(const BwdScene& sc, int x0, i
     }
     cur = t;
     if (t == BWD_NONE) r.kind = 0;
-    if (r.kind != 0) bwd_run_terms<PERSP, CLIP>(sc, r, x, y, __ldg(sc.dl + o), acc);
+    if (r.kind != 0) bwd_run_terms<PERSP, CLIP>(sc, r, x, y, g, acc);
   }
   const bool ends = r.kind != 0;
   if (__any_sync(FULL_MASK, ends))

@@ -82,7 +82,10 @@ extern "C" {
 
 /* ---- options for piko_raster_set_option ------------------------------- */
 #define PIKO_OPT_THREADS_PER_TILE 1 /* CTA size of the Process stage: 64, 128, 256 or 512
-                                       (the threads-per-bin knob of Listing 1 / Sec. 6)   */
+                                       (the threads-per-bin knob of Listing 1 / Sec. 6);
+                                       default 64 for bins of at most 64 pixels, 128 up to
+                                       256 pixels, 256 above, and 512 when the frame has
+                                       fewer bins than twice the GPU's SMs                  */
 #define PIKO_OPT_UNCLAMPED 2        /* 1: Lambert without the max(0, .) clamp,
                                        rgb = albedo * (n . L); default 0 (clamped)         */
 #define PIKO_OPT_CHECK_CAPACITY 3   /* 1 (default): forward reads the bin-list size back

@@ -138,13 +138,13 @@ piko_raster* piko_raster_create(int width, int height, int bin_w, int bin_h, int
   h->g.nbx = (width + bin_w - 1) / bin_w;
   h->g.nby = (height + bin_h - 1) / bin_h;
   h->nbins = h->g.nbx * h->g.nby;
-  h->threads = default_process_threads(bin_w * bin_h);
   if (cudaGetDevice(&h->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
     cudaGetLastError();
     delete h;
     return nullptr;
   }
+  h->threads = default_process_threads(bin_w * bin_h, h->nbins, h->num_sms);
   bool ok = cudaMalloc(&h->bin_count, sizeof(unsigned) * 2 * h->nbins) == cudaSuccess &&
             cudaMalloc(&h->bin_off, sizeof(unsigned) * (h->nbins + 1)) == cudaSuccess &&
             cudaMalloc(&h->cursor, sizeof(unsigned) * h->nbins) == cudaSuccess &&

@@ -402,8 +402,14 @@ cudaError_t process_occupancy(const ProcessParams& p, int threads, int* blocks_p
 // side; larger boxes, and larger triangles, a whole warp per triangle.
 constexpr int DEFAULT_SMALL_PX = 4096;
 
-// Default CTA size of the Process stage for a tile of bin_px pixels.
-inline int default_process_threads(int bin_px) { return bin_px <= 64 ? 64 : (bin_px <= 256 ? 128 : 256); }
+// Default CTA size of the Process stage for a tile of bin_px pixels in a
+// frame of nbins tiles on num_sms SMs.  A frame with fewer tiles than twice
+// the SMs (one CTA per tile cannot fill the GPU) takes 512 threads, so that
+// a tile's queued large triangles spread over 16 warps instead of 4.
+inline int default_process_threads(int bin_px, int nbins, int num_sms) {
+  if (nbins < 2 * num_sms) return 512;
+  return bin_px <= 64 ? 64 : (bin_px <= 256 ? 128 : 256);
+}
 
 // The two other pipeline mappings (piko_altpipe.cu): the fused one without
 // tiling and the unfused five-stage one.  Stages run in this order:

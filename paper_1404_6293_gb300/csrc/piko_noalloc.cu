@@ -235,7 +235,7 @@ extern "C" int piko_raster_forward_noalloc(const piko_scene* s, piko_framebuffer
   p.gnorm_out = reinterpret_cast<uint2*>(fb->gbuf_normal);
   p.galb_out = reinterpret_cast<uint2*>(fb->gbuf_albedo);
   p.st = status;
-  const int threads = default_process_threads(bin_w * bin_h);
+  const int threads = default_process_threads(bin_w * bin_h, nbins, num_sms);
   int grid = nbins;
   if (schedule != PIKO_SCHED_HARDWARE) {
     int per_sm = 0;

@@ -634,32 +634,39 @@ def run_ours(args):
 
 
 def measure_e2e(args, ctx, r, ds, fb, scene, world, dist, barrier) -> dict:
-    """The same metric through Rasterizer.render_from_host: pinned host ->
-    device copies of every input, the forward pass, device -> host copies of
-    key and RGBA, all inside the events."""
+    """The same metric through the C ABI with host buffers
+    (piko_raster_forward_host via Rasterizer.forward_host): every frame the
+    library copies the scene's pinned host arrays to the device, runs the
+    forward pass and copies key and RGBA into pinned host arrays, all inside
+    the events."""
     import torch
 
     from paper_1404_6293_gb300 import _lib as L
-    from paper_1404_6293_gb300.raster import DeviceScene, Framebuffer, Rasterizer
+    from paper_1404_6293_gb300.raster import DeviceScene, Framebuffer, HostScene, Rasterizer
     T = scene.num_triangles
     stream = ctx.stream
     K = args.steps
-    names = [n for n in ("pos", "tris", "normal", "color", "mvp", "light_dir") if getattr(ds, n) is not None]
-    host_in = {n: getattr(ds, n).cpu().pin_memory() for n in names}
-    key_h = torch.empty_like(fb.key, device="cpu").pin_memory()
-    rgba_h = torch.empty_like(fb.rgba, device="cpu").pin_memory()
+    hs = HostScene.from_host(scene)  # pinned; read-only, shared by every lane
+    names = [n for n in ("pos", "tris", "normal", "color", "mvp", "light_dir") if getattr(hs, n) is not None]
+    host_in = {n: getattr(hs, n) for n in names}
+
+    def host_fb():
+        return Framebuffer(torch.empty_like(fb.key, device="cpu").pin_memory(),
+                           torch.empty_like(fb.rgba, device="cpu").pin_memory())
+
+    fb_h = host_fb()
     h2d = sum(t.numel() * t.element_size() for t in host_in.values())
-    d2h = key_h.numel() * 8 + rgba_h.numel() * 4
+    d2h = fb_h.key.numel() * 8 + fb_h.rgba.numel() * 4
     Ke = min(K, args.e2e_steps)
     pairs = [(ctx.event(), ctx.event()) for _ in range(Ke)]
     for _ in range(3):
-        r.render_from_host(host_in, ds, fb, key_h, rgba_h)
+        r.forward_host(hs, fb_h, stream)
     barrier()
     # one frame at a time (L2 flushed between frames, outside the events)
     for k in range(Ke):
         ctx.flush.zero_()
         pairs[k][0].record(stream)
-        r.render_from_host(host_in, ds, fb, key_h, rgba_h)
+        r.forward_host(hs, fb_h, stream)
         pairs[k][1].record(stream)
     barrier()
     seq_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in pairs) / Ke, dist, "cuda")
@@ -667,7 +674,7 @@ def measure_e2e(args, ctx, r, ds, fb, scene, world, dist, barrier) -> dict:
     # host-to-device copy runs while frame k renders and copies back; every
     # frame still copies all its inputs in and its key and RGBA out
     nl = max(2, args.e2e_lanes)
-    lanes = [(r, ds, fb, key_h, rgba_h)]
+    lanes = [(r, fb_h, ds, fb)]
     for _ in range(nl - 1):
         rr = Rasterizer(scene.width, scene.height, args.bins, args.bins, args.schedule)
         if args.threads:
@@ -676,17 +683,19 @@ def measure_e2e(args, ctx, r, ds, fb, scene, world, dist, barrier) -> dict:
             rr.set_option(L.PIKO_OPT_PERSPECTIVE, 1)
         if args.small_px:
             rr.set_option(L.PIKO_OPT_SMALL_TRI_PIXELS, args.small_px)
-        d = DeviceScene.from_host(scene)
-        f = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode)
-        rr.forward(d, f)
+        f_h = host_fb()
+        rr.forward_host(hs, f_h, stream)
+        torch.cuda.synchronize()
         if rr.status()[0] != 0:
             raise RuntimeError("status error sizing an end-to-end handle")
         rr.set_option(L.PIKO_OPT_CHECK_CAPACITY, 0)
-        lanes.append((rr, d, f, torch.empty_like(key_h).pin_memory(), torch.empty_like(rgba_h).pin_memory()))
+        # device tensors of the same shapes for the copies-only leg below
+        lanes.append((rr, f_h, DeviceScene.from_host(scene), Framebuffer.allocate(scene.width, scene.height,
+                                                                                   scene.shade_mode)))
     side = [torch.cuda.Stream() for _ in range(nl)]
     for k in range(3 * nl):
-        rr, d, f, kh, rh = lanes[k % nl]
-        rr.render_from_host(host_in, d, f, kh, rh, stream=side[k % nl])
+        rr, f_h = lanes[k % nl][:2]
+        rr.forward_host(hs, f_h, side[k % nl])
     barrier()
     ctx.flush.zero_()
     e0, e1 = ctx.event(), ctx.event()
@@ -694,8 +703,8 @@ def measure_e2e(args, ctx, r, ds, fb, scene, world, dist, barrier) -> dict:
     for sd in side:
         sd.wait_stream(stream)
     for k in range(Ke):
-        rr, d, f, kh, rh = lanes[k % nl]
-        rr.render_from_host(host_in, d, f, kh, rh, stream=side[k % nl])
+        rr, f_h = lanes[k % nl][:2]
+        rr.forward_host(hs, f_h, side[k % nl])
     for sd in side:
         stream.wait_stream(sd)
     e1.record(stream)
@@ -709,12 +718,12 @@ def measure_e2e(args, ctx, r, ds, fb, scene, world, dist, barrier) -> dict:
     for sd in side:
         sd.wait_stream(stream)
     for k in range(Ke):
-        rr, d, f, kh, rh = lanes[k % nl]
+        _, f_h, d, f = lanes[k % nl]
         with torch.cuda.stream(side[k % nl]):
             for n, t in host_in.items():
                 getattr(d, n).copy_(t, non_blocking=True)
-            kh.copy_(f.key, non_blocking=True)
-            rh.copy_(f.rgba, non_blocking=True)
+            f_h.key.copy_(f.key, non_blocking=True)
+            f_h.rgba.copy_(f.rgba, non_blocking=True)
     for sd in side:
         stream.wait_stream(sd)
     c1.record(stream)
@@ -727,9 +736,9 @@ def measure_e2e(args, ctx, r, ds, fb, scene, world, dist, barrier) -> dict:
     link = (h2d + d2h) / (c_ms * 1e6)
     return {"value": job_throughput(T, world, e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": e_ms, "steps": Ke,
-            "how": "Rasterizer.render_from_host per frame: pinned host -> device copies of every input, "
-                   f"forward, device -> host copies of key and RGBA; frames rotate over {nl} handles and "
-                   f"{nl} streams so copies overlap the other frames' work",
+            "how": "piko_raster_forward_host (the C ABI with host buffers) per frame: the library copies "
+                   "every input from pinned host memory, runs the forward pass and copies key and RGBA back; "
+                   f"frames rotate over {nl} handles and {nl} streams so copies overlap the other frames' work",
             "sequential": {"value": job_throughput(T, world, seq_ms), "ms_per_step": seq_ms,
                            "how": "one frame at a time on one stream, L2 flushed between frames"},
             "copies_only": {"ms_per_step": c_ms, "gb_s": link, "frac_of_e2e_time": c_ms / e_ms,

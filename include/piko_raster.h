@@ -187,6 +187,25 @@ void piko_raster_destroy(piko_raster *h);
 int piko_raster_forward(piko_raster *h, const piko_scene *scene, piko_framebuffer *fb,
                         void *cuda_stream);
 
+/* The forward pass of a scene held in HOST memory into a framebuffer in host
+ * memory (the paper's problem statement end to end: a triangle list with
+ * per-vertex attributes in, a framebuffer out, Sec. 7.1).  scene and fb are
+ * as for piko_raster_forward except that every array pointer (pos, tris,
+ * color, normal, mvp, light_dir; key, rgba, gbuf_normal, gbuf_albedo) is
+ * host memory, with no alignment requirement; page-locked memory
+ * (cudaHostAlloc, or pinned tensors) makes the copies asynchronous.  The
+ * handle copies the arrays into device buffers it owns (allocated on first
+ * use and grown when a larger scene or framebuffer comes, which
+ * synchronizes the device), runs piko_raster_forward on them and copies
+ * fb's requested outputs back, all enqueued on cuda_stream in that order;
+ * the caller must not touch the host arrays until the stream has passed
+ * this call.  Errors: PIKO_ERR_INVALID_ARG (size differs from the handle's,
+ * negative counts, a NULL required pointer; nothing enqueued), PIKO_ERR_OOM
+ * (a device buffer could not grow; nothing enqueued), the codes of
+ * piko_raster_forward, and PIKO_ERR_CUDA for a failed copy. */
+int piko_raster_forward_host(piko_raster *h, const piko_scene *scene, piko_framebuffer *fb,
+                             void *cuda_stream);
+
 /* Gradients of a loss through shading with visibility held fixed by a
  * previous forward's fwd->key (the coverage stays exact integer
  * arithmetic).  dl_drgba [H][W][4] is dLoss/d(rgba) (alpha ignored).

@@ -76,6 +76,7 @@ def _declare(lib):
     lib.piko_raster_destroy.argtypes = [P]
     lib.piko_raster_destroy.restype = None
     lib.piko_raster_forward.argtypes = [P, C.POINTER(PikoScene), C.POINTER(PikoFramebuffer), P]
+    lib.piko_raster_forward_host.argtypes = [P, C.POINTER(PikoScene), C.POINTER(PikoFramebuffer), P]
     lib.piko_raster_backward.argtypes = [P, C.POINTER(PikoScene), C.POINTER(PikoFramebuffer), P, P, P, P, P]
     lib.piko_raster_deferred_light.argtypes = [P, C.POINTER(PikoFramebuffer), P, i32, P, P]
     lib.piko_raster_reserve.argtypes = [P, i64, i64, i64]
@@ -86,7 +87,7 @@ def _declare(lib):
     lib.piko_raster_version.argtypes = []
     lib.piko_raster_set_stage_events.argtypes = [P, C.POINTER(C.c_void_p), i32]
     lib.piko_raster_stats.argtypes = [P, C.POINTER(C.c_int64)]
-    for name in ("piko_raster_forward", "piko_raster_backward", "piko_raster_deferred_light",
+    for name in ("piko_raster_forward", "piko_raster_forward_host", "piko_raster_backward", "piko_raster_deferred_light",
                  "piko_raster_reserve", "piko_raster_set_option", "piko_raster_status",
                  "piko_raster_version", "piko_raster_set_stage_events", "piko_raster_stats"):
         getattr(lib, name).restype = i32

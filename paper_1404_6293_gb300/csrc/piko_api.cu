@@ -73,6 +73,18 @@ struct piko_raster {
   unsigned* clip_orig = nullptr;
   long long ccap_tris = 0, ccap_orig = 0;
   unsigned* h_clips = nullptr;  // pinned: sub-triangle count read back
+  // device copies of a scene and framebuffer held in host memory (piko_raster_forward_host)
+  float4* hs_pos = nullptr;
+  int* hs_tris = nullptr;
+  float* hs_color = nullptr;
+  float* hs_normal = nullptr;
+  float* hs_small = nullptr;  // mvp [16] then light [3]
+  unsigned long long* hs_key = nullptr;
+  float4* hs_rgba = nullptr;
+  uint2* hs_gn = nullptr;
+  uint2* hs_ga = nullptr;
+  long long hcap_pos = 0, hcap_tris = 0, hcap_color = 0, hcap_normal = 0, hcap_small = 0, hcap_key = 0,
+            hcap_rgba = 0, hcap_gn = 0, hcap_ga = 0;
   DevStatus* status = nullptr;
   unsigned long long* h_needed = nullptr;  // pinned
   long long last_entries = 0;              // bin entries of the last frame read back (0: none yet)
@@ -182,6 +194,15 @@ void piko_raster_destroy(piko_raster* h) {
   cudaFree(h->frag_rgba);
   cudaFree(h->clip_tris);
   cudaFree(h->clip_orig);
+  cudaFree(h->hs_pos);
+  cudaFree(h->hs_tris);
+  cudaFree(h->hs_color);
+  cudaFree(h->hs_normal);
+  cudaFree(h->hs_small);
+  cudaFree(h->hs_key);
+  cudaFree(h->hs_rgba);
+  cudaFree(h->hs_gn);
+  cudaFree(h->hs_ga);
   cudaFree(h->status);
   batch_state_free(h->batch);
   if (h->h_needed) cudaFreeHost(h->h_needed);
@@ -517,6 +538,73 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
   cudaError_t e = launch_process(p, h->threads, grid, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "process launch");
   if (ev) cudaEventRecord(h->stage_ev[5], st);
+  return PIKO_OK;
+}
+
+int piko_raster_forward_host(piko_raster* h, const piko_scene* s, piko_framebuffer* fb, void* cuda_stream) {
+  if (!h || !s || !fb) return PIKO_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  if (s->width != h->W || s->height != h->H) return fail(h, PIKO_ERR_INVALID_ARG, "scene size differs from the handle's");
+  if (s->num_vertices < 0 || s->num_triangles < 0) return fail(h, PIKO_ERR_INVALID_ARG, "negative counts");
+  if ((s->num_vertices > 0 && !s->pos) || (s->num_triangles > 0 && !s->tris) || !fb->key)
+    return fail(h, PIKO_ERR_INVALID_ARG, "NULL required pointer");
+  const long long V = s->num_vertices, T = s->num_triangles, P = (long long)h->W * h->H;
+  const bool gbuf = s->shade_mode == PIKO_SHADE_GBUFFER;
+  // device buffers (grown on first use; a growth synchronizes the device)
+  int r = PIKO_OK;
+  if (r == PIKO_OK) r = grow(h, &h->hs_pos, &h->hcap_pos, V, "host-scene positions");
+  if (r == PIKO_OK) r = grow(h, &h->hs_tris, &h->hcap_tris, 3 * T, "host-scene triangles");
+  if (r == PIKO_OK && s->color) r = grow(h, &h->hs_color, &h->hcap_color, 3 * V, "host-scene colours");
+  if (r == PIKO_OK && s->normal) r = grow(h, &h->hs_normal, &h->hcap_normal, 3 * V, "host-scene normals");
+  if (r == PIKO_OK) r = grow(h, &h->hs_small, &h->hcap_small, 20, "host-scene matrix and light");
+  if (r == PIKO_OK) r = grow(h, &h->hs_key, &h->hcap_key, P, "host-framebuffer keys");
+  if (r == PIKO_OK && fb->rgba && !gbuf) r = grow(h, &h->hs_rgba, &h->hcap_rgba, P, "host-framebuffer colour");
+  if (r == PIKO_OK && gbuf && fb->gbuf_normal) r = grow(h, &h->hs_gn, &h->hcap_gn, P, "host G-buffer normals");
+  if (r == PIKO_OK && gbuf && fb->gbuf_albedo) r = grow(h, &h->hs_ga, &h->hcap_ga, P, "host G-buffer albedo");
+  if (r != PIKO_OK) return r;
+  piko_scene ds = *s;
+  piko_framebuffer dfb = {};
+  struct Copy {
+    void* dst;
+    const void* src;
+    size_t bytes;
+  };
+  const Copy in[] = {
+      {h->hs_pos, s->pos, (size_t)V * 16},
+      {h->hs_tris, s->tris, (size_t)T * 12},
+      {h->hs_color, s->color, s->color ? (size_t)V * 12 : 0},
+      {h->hs_normal, s->normal, s->normal ? (size_t)V * 12 : 0},
+      {h->hs_small, s->mvp, s->mvp ? (size_t)64 : 0},
+      {h->hs_small + 16, s->light_dir, s->light_dir ? (size_t)12 : 0},
+  };
+  for (const Copy& c : in) {
+    if (c.bytes == 0) continue;
+    const cudaError_t e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "host-to-device copy");
+  }
+  ds.pos = reinterpret_cast<const float*>(h->hs_pos);
+  ds.tris = h->hs_tris;
+  ds.color = s->color ? h->hs_color : nullptr;
+  ds.normal = s->normal ? h->hs_normal : nullptr;
+  ds.mvp = s->mvp ? h->hs_small : nullptr;
+  ds.light_dir = s->light_dir ? h->hs_small + 16 : nullptr;
+  dfb.key = reinterpret_cast<uint64_t*>(h->hs_key);
+  dfb.rgba = fb->rgba && !gbuf ? reinterpret_cast<float*>(h->hs_rgba) : nullptr;
+  dfb.gbuf_normal = gbuf && fb->gbuf_normal ? h->hs_gn : nullptr;
+  dfb.gbuf_albedo = gbuf && fb->gbuf_albedo ? h->hs_ga : nullptr;
+  r = piko_raster_forward(h, &ds, &dfb, cuda_stream);
+  if (r != PIKO_OK) return r;
+  const Copy out[] = {
+      {fb->key, dfb.key, (size_t)P * 8},
+      {fb->rgba, dfb.rgba, dfb.rgba ? (size_t)P * 16 : 0},
+      {fb->gbuf_normal, dfb.gbuf_normal, dfb.gbuf_normal ? (size_t)P * 8 : 0},
+      {fb->gbuf_albedo, dfb.gbuf_albedo, dfb.gbuf_albedo ? (size_t)P * 8 : 0},
+  };
+  for (const Copy& c : out) {
+    if (c.bytes == 0) continue;
+    const cudaError_t e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "device-to-host copy");
+  }
   return PIKO_OK;
 }
 

@@ -88,6 +88,56 @@ class DeviceScene:
 
 
 @dataclass
+class HostScene:
+    """A scene in host memory (CPU tensors, pinned for asynchronous copies),
+    for Rasterizer.forward_host: the library copies it to the device."""
+
+    width: int
+    height: int
+    pos: torch.Tensor                      # float32 [V,4]
+    tris: torch.Tensor                     # int32 [T,3]
+    color: Optional[torch.Tensor] = None   # float32 [V,3]
+    normal: Optional[torch.Tensor] = None  # float32 [V,3]
+    mvp: Optional[torch.Tensor] = None     # float32 [16]
+    light_dir: Optional[torch.Tensor] = None  # float32 [3]
+    shade_mode: int = L.PIKO_SHADE_GOURAUD
+
+    @staticmethod
+    def from_host(scene, pin=True, mvp=None) -> "HostScene":
+        """Wraps a host scene (numpy arrays, see scenes.Scene) in CPU tensors."""
+        def t(a, dt):
+            if a is None:
+                return None
+            x = torch.from_numpy(np.ascontiguousarray(a, dtype=dt).copy())
+            return x.pin_memory() if pin else x
+
+        m = scene.mvp if mvp is None else mvp
+        return HostScene(scene.width, scene.height, t(scene.pos, np.float32).reshape(-1, 4),
+                         t(scene.tris, np.int32).reshape(-1, 3), t(scene.color, np.float32),
+                         t(scene.normal, np.float32), None if m is None else t(m, np.float32).reshape(16),
+                         t(scene.light_dir, np.float32), int(scene.shade_mode))
+
+    def c_struct(self) -> L.PikoScene:
+        for name in ("pos", "tris", "color", "normal", "mvp", "light_dir"):
+            v = getattr(self, name)
+            if v is not None and (v.is_cuda or not v.is_contiguous()):
+                raise ValueError(f"{name} must be a contiguous CPU tensor")
+        if self.pos.dtype != torch.float32 or self.tris.dtype != torch.int32:
+            raise TypeError("pos must be float32 and tris int32")
+        s = L.PikoScene()
+        s.width, s.height = self.width, self.height
+        s.num_vertices, s.num_triangles = int(self.pos.shape[0]), int(self.tris.shape[0])
+        s.pos, s.tris = self.pos.data_ptr(), self.tris.data_ptr()
+        s.color = None if self.color is None else self.color.data_ptr()
+        s.normal = None if self.normal is None else self.normal.data_ptr()
+        s.mvp = None if self.mvp is None else self.mvp.data_ptr()
+        s.light_dir = None if self.light_dir is None else self.light_dir.data_ptr()
+        s.shade_mode = self.shade_mode
+        s.reserved = 0
+        return s
+
+
+@dataclass
 class Framebuffer:
     key: torch.Tensor                     # int64 [H,W] holding the uint64 keys
     rgba: Optional[torch.Tensor] = None   # float32 [H,W,4]
@@ -191,6 +241,27 @@ class Rasterizer:
             fb = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode, scene.pos.device)
         cs, cf = scene.c_struct(), fb.c_struct()
         self._check(self.lib.piko_raster_forward(self._h, C.byref(cs), C.byref(cf), self._stream(stream)))
+        return fb
+
+    def forward_host(self, scene: HostScene, fb: Optional[Framebuffer] = None, stream=None) -> Framebuffer:
+        """End-to-end frame through the C ABI with host buffers
+        (piko_raster_forward_host): the library copies the scene's host
+        arrays to the device, runs the forward pass and copies the key and
+        colour (or G-buffer) into fb's host tensors, all on ``stream``.  fb
+        defaults to pinned host tensors; the results are valid once the
+        stream has passed the call."""
+        if fb is None:
+            fb = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode, "cpu")
+            for name in ("key", "rgba", "gbuf_normal", "gbuf_albedo"):
+                if getattr(fb, name) is not None:
+                    setattr(fb, name, getattr(fb, name).pin_memory())
+        for name in ("key", "rgba", "gbuf_normal", "gbuf_albedo"):
+            v = getattr(fb, name)
+            if v is not None and (v.is_cuda or not v.is_contiguous()):
+                raise ValueError(f"framebuffer {name} must be a contiguous CPU tensor")
+        cs, cf = scene.c_struct(), fb.c_struct()
+        self._check(self.lib.piko_raster_forward_host(self._h, C.byref(cs), C.byref(cf), self._stream(stream)))
+        self._host_keepalive = (scene, fb)
         return fb
 
     def render_from_host(self, host_inputs: dict, scene: DeviceScene, fb: Framebuffer, key_out: torch.Tensor,

@@ -414,7 +414,10 @@ __device__ void phase_process(const BatchParams& b, ProcessShared& ps, const Til
 #ifndef PIKO_BATCH_MAXNREG
 #define PIKO_BATCH_MAXNREG 64
 #endif
-constexpr int BATCH_THREADS = 128;
+#ifndef PIKO_BATCH_THREADS
+#define PIKO_BATCH_THREADS 128
+#endif
+constexpr int BATCH_THREADS = PIKO_BATCH_THREADS;  // CTA size of the persistent batch kernel
 
 // PERSP: perspective-correct attributes; one instance per setting
 template <bool PERSP>

@@ -212,8 +212,8 @@ constexpr unsigned RECT_SINGLE = 0x8000u;
 // ======================================================================
 // Scan: one CTA per chunk of SCAN_CHUNK bins (scan_chunk in piko_scan.cuh).
 // ======================================================================
-constexpr int SCAN_THREADS = 256;
-constexpr int SCAN_CHUNK = SCAN_THREADS * SCAN_PER;
+constexpr int SCAN_THREADS = FWD_SCAN_THREADS;
+constexpr int SCAN_CHUNK = FWD_SCAN_CHUNK;
 
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan(int nbins, unsigned* __restrict__ cnt,
                                                        unsigned* __restrict__ bin_off, unsigned* __restrict__ cursor,

@@ -20,6 +20,7 @@
 #include <mutex>
 
 #include "piko_internal.cuh"
+#include "piko_scan.cuh"
 
 using namespace piko;
 
@@ -40,7 +41,7 @@ constexpr size_t OFF_COUNT = OFF_CHUNKS + sizeof(unsigned long long) * MAX_CHUNK
 constexpr size_t OFF_OFFS = align256(OFF_COUNT + sizeof(unsigned) * 2 * PIKO_NOALLOC_MAX_BINS);
 constexpr size_t OFF_CURSOR = align256(OFF_OFFS + sizeof(unsigned) * (PIKO_NOALLOC_MAX_BINS + 1));
 constexpr size_t OFF_ENTRIES = align256(OFF_CURSOR + sizeof(unsigned) * PIKO_NOALLOC_MAX_BINS);
-static_assert(PIKO_NOALLOC_MAX_BINS / 2048 + 1 <= MAX_CHUNKS, "scan chunk states (2048 bins each) must fit");
+static_assert(PIKO_NOALLOC_MAX_BINS / FWD_SCAN_CHUNK + 1 <= MAX_CHUNKS, "scan chunk states must fit");
 static_assert(OFF_COUNT % 256 == 0, "counts stay 256-byte aligned");
 constexpr size_t SCRATCH_BYTES = align256(OFF_ENTRIES + sizeof(unsigned) * (size_t)PIKO_NOALLOC_MAX_BIN_ENTRIES);
 

@@ -28,8 +28,8 @@ def test_scan_wait_runs_out_and_reports_timeout():
     torch = _torch()
     from paper_1404_6293_gb300 import _lib as L
     from paper_1404_6293_gb300.raster import DeviceScene, Framebuffer, Rasterizer
-    s = S.random_triangles(1024, 1024, 4000, 12.0, seed=91)  # 64 x 64 = 4096 tiles: two scan chunks
-    r = Rasterizer(s.width, s.height, 16, 16, "dynamic")
+    s = S.random_triangles(1024, 1024, 4000, 12.0, seed=91)  # 128 x 128 = 16384 tiles: eight scan chunks
+    r = Rasterizer(s.width, s.height, 8, 8, "dynamic")
     ds = DeviceScene.from_host(s)
     fb = Framebuffer.allocate(s.width, s.height, s.shade_mode)
     r.forward(ds, fb)

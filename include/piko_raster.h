@@ -200,9 +200,10 @@ int piko_raster_forward(piko_raster *h, const piko_scene *scene, piko_framebuffe
  * fb's requested outputs back, all enqueued on cuda_stream in that order;
  * the caller must not touch the host arrays until the stream has passed
  * this call.  Errors: PIKO_ERR_INVALID_ARG (size differs from the handle's,
- * negative counts, a NULL required pointer; nothing enqueued), PIKO_ERR_OOM
- * (a device buffer could not grow; nothing enqueued), the codes of
- * piko_raster_forward, and PIKO_ERR_CUDA for a failed copy. */
+ * negative counts, a NULL required pointer, a shade mode without the
+ * attributes it needs; nothing enqueued), PIKO_ERR_OOM (a device buffer
+ * could not grow; nothing enqueued), the codes of piko_raster_forward, and
+ * PIKO_ERR_CUDA for a failed copy. */
 int piko_raster_forward_host(piko_raster *h, const piko_scene *scene, piko_framebuffer *fb,
                              void *cuda_stream);
 

@@ -563,6 +563,14 @@ int piko_raster_forward_host(piko_raster* h, const piko_scene* s, piko_framebuff
   if (r == PIKO_OK && gbuf && fb->gbuf_albedo) r = grow(h, &h->hs_ga, &h->hcap_ga, P, "host G-buffer albedo");
   if (r != PIKO_OK) return r;
   piko_scene ds = *s;
+  ds.pos = reinterpret_cast<const float*>(h->hs_pos);
+  ds.tris = h->hs_tris;
+  ds.color = s->color ? h->hs_color : nullptr;
+  ds.normal = s->normal ? h->hs_normal : nullptr;
+  ds.mvp = s->mvp ? h->hs_small : nullptr;
+  ds.light_dir = s->light_dir ? h->hs_small + 16 : nullptr;
+  r = check_scene(h, &ds);  // every argument check before anything is enqueued
+  if (r != PIKO_OK) return r;
   piko_framebuffer dfb = {};
   struct Copy {
     void* dst;
@@ -582,12 +590,6 @@ int piko_raster_forward_host(piko_raster* h, const piko_scene* s, piko_framebuff
     const cudaError_t e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "host-to-device copy");
   }
-  ds.pos = reinterpret_cast<const float*>(h->hs_pos);
-  ds.tris = h->hs_tris;
-  ds.color = s->color ? h->hs_color : nullptr;
-  ds.normal = s->normal ? h->hs_normal : nullptr;
-  ds.mvp = s->mvp ? h->hs_small : nullptr;
-  ds.light_dir = s->light_dir ? h->hs_small + 16 : nullptr;
   dfb.key = reinterpret_cast<uint64_t*>(h->hs_key);
   dfb.rgba = fb->rgba && !gbuf ? reinterpret_cast<float*>(h->hs_rgba) : nullptr;
   dfb.gbuf_normal = gbuf && fb->gbuf_normal ? h->hs_gn : nullptr;

@@ -70,3 +70,22 @@ def test_forward_host_rejects_size_mismatch():
     with pytest.raises(PikoError):
         r.forward_host(HostScene.from_host(s))
     r.close()
+
+
+def test_forward_host_rejects_missing_attributes_and_renders_empty_scene():
+    import torch
+    from paper_1404_6293_gb300.raster import HostScene, PikoError, Rasterizer
+    s = S.random_triangles(64, 48, 20, 6.0, seed=95)
+    r = Rasterizer(64, 48)
+    hs = HostScene.from_host(s)
+    hs.color = None  # Gouraud without colours
+    with pytest.raises(PikoError):
+        r.forward_host(hs)
+    empty = HostScene.from_host(s)
+    empty.tris = empty.tris[:0].contiguous()
+    fb = r.forward_host(empty)
+    torch.cuda.synchronize()
+    assert r.status()[0] == 0
+    assert (fb.key.numpy().view(np.uint64) == np.uint64(0xFFFFFFFFFFFFFFFF)).all()
+    assert (fb.rgba.numpy() == 0).all()
+    r.close()

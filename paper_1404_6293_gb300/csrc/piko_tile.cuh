@@ -86,6 +86,12 @@ __host__ __device__ __forceinline__ int rec_attr_count(int mode, bool has_color)
 
 
 // ---------------------------------------------------------------- raster
+// Large boxes of at least this many pixels in a tile are walked by row spans
+// (raster_warp_spans), smaller ones sample by sample (raster_warp).
+#ifndef PIKO_SPAN_MIN_PX
+#define PIKO_SPAN_MIN_PX 128
+#endif
+
 template <typename I>
 struct Edges {
   I e0, e1, e2;     // edge functions minus the fill-rule bias (covered iff all >= 0)
@@ -268,6 +274,85 @@ __device__ __forceinline__ unsigned raster_warp(const TriSetup& s, unsigned long
     }
     lx += dx; ly += dy;
     if (lx >= bw) { lx -= bw; ++ly; }
+  }
+  return frags;
+}
+
+// Row spans for the large boxes: the covered pixel centres of a row are an
+// interval (each edge's test is a half-plane, monotone along the row), so
+// a lane per row finds its interval's ends exactly by bisection on the
+// edge tests, and the warp then walks only the covered samples, 32 at a
+// time, instead of the whole box.  Every covered sample gets the same
+// depth key as in raster_warp.
+//
+// Narrows [lo, hi] to the columns of row Py (16.8 centre) where edge
+// (ex, ey) through (Xr, Yr) with fill-rule bias b passes (empty: hi < lo).
+__device__ __forceinline__ void clip_span(int ex, int ey, int Xr, int Yr, int b, int Py, int& lo, int& hi) {
+  if (lo > hi) return;
+  const long long wy = (long long)ex * (Py - Yr) - b;
+  // the test at column px: wy - ey (256 px + 128 - Xr) >= 0
+  auto pass = [&](int px) { return wy - (long long)ey * (256 * px + 128 - Xr) >= 0; };
+  if (ey == 0) {
+    if (!pass(lo)) hi = lo - 1;
+    return;
+  }
+  if (ey < 0) {  // the test only turns true along the row: its first passing column
+    if (pass(lo)) return;
+    if (!pass(hi)) { hi = lo - 1; return; }
+    int a = lo, c = hi;  // pass(a) false, pass(c) true; at most 6 halvings for 64 columns
+    while (c - a > 1) {
+      const int m = (a + c) >> 1;
+      if (pass(m)) c = m; else a = m;
+    }
+    lo = c;
+  } else {       // the test only turns false along the row: its last passing column
+    if (pass(hi)) return;
+    if (!pass(lo)) { hi = lo - 1; return; }
+    int a = lo, c = hi;  // pass(a) true, pass(c) false
+    while (c - a > 1) {
+      const int m = (a + c) >> 1;
+      if (pass(m)) a = m; else c = m;
+    }
+    hi = a;
+  }
+}
+
+__device__ __forceinline__ unsigned raster_warp_spans(const TriSetup& s, unsigned long long tag, int px0, int px1,
+                                                      int py0, int py1, int x0, int y0, int bshift_x,
+                                                      unsigned long long* skey, int lane) {
+  const float rA = approx_rcp(f32_from_i64(s.A));
+  const bool mid = s.A < (1LL << 31);  // the same for the whole warp
+  const int b0 = 1 - top_left(s.X2 - s.X1, s.Y2 - s.Y1);
+  const int b1 = 1 - top_left(s.X0 - s.X2, s.Y0 - s.Y2);
+  const int b2 = 1 - top_left(s.X1 - s.X0, s.Y1 - s.Y0);
+  unsigned frags = 0;
+  for (int r0 = py0; r0 <= py1; r0 += 32) {  // rows in groups of 32, a lane each
+    const int py = r0 + lane;
+    int lo = px0, hi = py <= py1 ? px1 : px0 - 1;
+    const int Py = 256 * py + 128;
+    clip_span(s.X2 - s.X1, s.Y2 - s.Y1, s.X1, s.Y1, b0, Py, lo, hi);
+    clip_span(s.X0 - s.X2, s.Y0 - s.Y2, s.X2, s.Y2, b1, Py, lo, hi);
+    clip_span(s.X1 - s.X0, s.Y1 - s.Y0, s.X0, s.Y0, b2, Py, lo, hi);
+    const int cnt = hi >= lo ? hi - lo + 1 : 0;
+    const MultiSpan m = warp_prefix(cnt, lane);
+    for (int k0 = 0; k0 < m.total; k0 += 32) {
+      const int k = k0 + lane;
+      const int owner = pair_owner(m.incl, k < m.total ? k : m.total - 1);
+      const int olo = __shfl_sync(FULL_MASK, lo, owner);
+      const int ofirst = __shfl_sync(FULL_MASK, m.incl - cnt, owner);
+      if (k < m.total) {
+        const int px = olo + (k - ofirst), qy = r0 + owner;
+        const int Px = 256 * px + 128, Qy = 256 * qy + 128;
+        const long long w1 = (long long)(s.X0 - s.X2) * (Qy - s.Y2) - (long long)(s.Y0 - s.Y2) * (Px - s.X2);
+        const long long w2 = (long long)(s.X1 - s.X0) * (Qy - s.Y0) - (long long)(s.Y1 - s.Y0) * (Px - s.X0);
+        const int idx = ((qy - y0) << bshift_x) + (px - x0);
+        if (mid)
+          key_min_mid(skey, idx, (int)w1, (int)w2, s, rA, tag);
+        else
+          key_min_large(skey, idx, w1, w2, s, rA, tag);
+      }
+    }
+    frags += (unsigned)m.total;
   }
   return frags;
 }
@@ -543,8 +628,10 @@ __device__ __forceinline__ void process_tile(const TileScene& p, int tile, unsig
         int px0, px1, py0, py1;
         centre_range(min(s.X0, min(s.X1, s.X2)), max(s.X0, max(s.X1, s.X2)), x0, x1, px0, px1);
         centre_range(min(s.Y0, min(s.Y1, s.Y2)), max(s.Y0, max(s.Y1, s.Y2)), y0, y1, py0, py1);
-        const unsigned f = raster_warp(s, ((unsigned long long)t << p.slot_bits) | slot, px0, px1, py0, py1, x0, y0,
-                                       p.g.bshift_x, skey, lane);
+        const unsigned long long tag = ((unsigned long long)t << p.slot_bits) | slot;
+        const unsigned f = (px1 - px0 + 1) * (py1 - py0 + 1) >= PIKO_SPAN_MIN_PX
+                               ? raster_warp_spans(s, tag, px0, px1, py0, py1, x0, y0, p.g.bshift_x, skey, lane)
+                               : raster_warp(s, tag, px0, px1, py0, py1, x0, y0, p.g.bshift_x, skey, lane);
         if (STATS && lane == 0) st.frags += f;
       }
       big_base += nbig;

@@ -429,7 +429,8 @@ __global__ void __maxnreg__(PIKO_BATCH_MAXNREG) k_batch_forward(BatchParams b) {
   TileSmem sm;
   sm.skey = smem;
   sm.sbig = reinterpret_cast<int*>(smem + b.max_bin_px);
-  sm.srec = sm.sbig + blockDim.x * BIG_REC;
+  sm.sfrag = sm.sbig + blockDim.x;
+  sm.srec = sm.sfrag + (blockDim.x >> 5) * FRAG_WARP_WORDS;
   sm.s_nbig = &s_nbig;
   if (cta_should_stop(b.st)) return;
   if (b.phases & PH_VERTEX) {

@@ -64,11 +64,19 @@ __global__ void __maxnreg__(PIKO_PROCESS_MAXNREG) k_process(const __grid_constan
   TileSmem sm;
   sm.skey = smem;
   sm.sbig = reinterpret_cast<int*>(smem + bin_px);
-  sm.srec = sm.sbig + nt * BIG_REC;
+  sm.sfrag = sm.sbig + nt;
+  sm.srec = sm.sfrag + (nt >> 5) * FRAG_WARP_WORDS;
   sm.s_nbig = &s_nbig;
   const TileScene& sc = pl.sc;
   for (int i = tid; i < bin_px; i += nt) sm.skey[i] = KEY_EMPTY;
   pdl_wait();  // bin lists and status of the scatter pass
+  // the first tile's range is loaded before the status word is tested, so
+  // that the two global round trips overlap (static and hardware schedules)
+  unsigned nbeg = 0u, nend = 0u;
+  if (SCHED != PIKO_SCHED_DYNAMIC && (int)blockIdx.x < p.ntiles) {
+    nbeg = __ldg(p.bin_off + blockIdx.x);
+    nend = __ldg(p.bin_off + blockIdx.x + 1);
+  }
   if (p.st->flags & STATUS_SKIP_MASK) return;
   constexpr bool dynamic = SCHED == PIKO_SCHED_DYNAMIC;
   if (tid == 0) {
@@ -91,7 +99,20 @@ __global__ void __maxnreg__(PIKO_PROCESS_MAXNREG) k_process(const __grid_constan
       if (tid == 0 && tile < p.ntiles) s_tile[(iter + 1) & 1] = (int)atomicAdd(&p.st->queue_head, 1u);
     }
     if (tile >= p.ntiles) break;
-    const unsigned beg = __ldg(p.bin_off + tile), end = __ldg(p.bin_off + tile + 1);
+    unsigned beg, end;
+    if (SCHED == PIKO_SCHED_DYNAMIC) {
+      beg = __ldg(p.bin_off + tile);
+      end = __ldg(p.bin_off + tile + 1);
+    } else {
+      beg = nbeg;
+      end = nend;
+      // the static schedule's next tile is known: its range loads during this one
+      const int next = tile + (int)gridDim.x;
+      if (SCHED == PIKO_SCHED_STATIC && next < p.ntiles) {
+        nbeg = __ldg(p.bin_off + next);
+        nend = __ldg(p.bin_off + next + 1);
+      }
+    }
     process_tile<STATS, PERSP, CLIP>(sc, tile, beg, end, p.bin_tris, sm, big_base, st);
   }
   if (STATS) {  // one atomic per warp: same-address atomics from every thread serialise

@@ -56,14 +56,26 @@ struct TileScene {
 };
 
 // Per-CTA shared memory of the stage.
-// A large triangle queued for the warps: its snapped vertices, depths and
-// area as set up by the thread that met it (so that the warp re-reads
-// nothing from global memory), then its triangle index and record slot.
-constexpr int BIG_REC = 13;  // X0 Y0 X1 Y1 X2 Y2 Z0 Z1 Z2 A_lo A_hi t slot (odd: distinct banks)
+// Each lane owns FST_WORDS staging words per bin entry, stored word-major
+// per warp (word w of lane l at w * 32 + l, so that a lane's words fall in
+// its own bank).  A lane uses them for one of two things:
+//  - a small box: the triangle's depth setup, read by the warp's
+//    fragment_pass (FS_* words);
+//  - a large triangle queued for the warps: its snapped vertices, depths and
+//    area as set up by the lane that met it (so that the warp re-reads
+//    nothing from global memory), then its triangle index and record slot
+//    (BG_* words).
+// After the staging words, each warp has a list of up to FRAG_CAP fragment
+// descriptors.  The queue of large triangles holds the thread index of each.
+constexpr int FST_WORDS = 13;
+constexpr int FRAG_CAP = 128;
+constexpr int FRAG_WARP_WORDS = FST_WORDS * 32 + FRAG_CAP;
+enum { BG_X0 = 0, BG_Y0, BG_X1, BG_Y1, BG_X2, BG_Y2, BG_Z0, BG_Z1, BG_Z2, BG_ALO, BG_AHI, BG_T, BG_SLOT };
 
 struct TileSmem {
   unsigned long long* skey;  // [bin_px], all KEY_EMPTY between tiles
-  int* sbig;                 // [nt][BIG_REC] ring of queued large triangles
+  int* sbig;                 // [nt] ring of the threads whose large triangles are queued
+  int* sfrag;                // [nt / 32][FRAG_WARP_WORDS]
   int* srec;                 // [nslots][rec_stride]
   unsigned* s_nbig;          // grows monotonically
 };
@@ -235,6 +247,115 @@ __device__ __forceinline__ unsigned raster_thread64(const TriSetup& s, unsigned 
                                                  int py0, int py1, int x0, int y0, int bshift_x,
                                                  unsigned long long* skey) {
   return raster_thread_body<long long>(s, tag, px0, px1, py0, py1, x0, y0, bshift_x, skey);
+}
+
+// ------------------------------------------------ compacted small boxes
+// A small box (at most 32 pixels, of a triangle whose bounding box is below
+// 2^15 in 16.8 units, so that the int32 edge walk is exact) is walked by its
+// thread for coverage only, into a mask whose bit j is the box's j-th pixel
+// in row-major order.  The lane stores the triangle's depth setup in the
+// warp's staging area, and fragment_pass then gives the warp's covered
+// samples out to consecutive lanes: the depth quotient, key and shared
+// minimum, most of a tile of tiny triangles' work, run with every lane busy
+// instead of each lane following its own box.
+struct SmallBox {
+  unsigned mask;  // covered pixels of the box
+  int place;      // tile-local index of the box's first pixel | box width << 16
+};
+
+// staging words of a lane (word w of lane l at w * 32 + l)
+enum { FS_E1 = 0, FS_E2, FS_SX1, FS_SY1, FS_SX2, FS_SY2, FS_K1, FS_K2, FS_D1, FS_D2, FS_A, FS_KLO, FS_KHI };
+
+__device__ __forceinline__ void small_box(const TriSetup& s, unsigned long long tag, int px0, int px1, int py0,
+                                          int py1, int x0, int y0, int bshift_x, int* wst, int lane, SmallBox& b) {
+  const Edges<int> e = make_edges<int>(s, px0, py0);
+  const int bw = px1 - px0 + 1, bh = py1 - py0 + 1;
+  // shift each sample's coverage in from the top; the last sample ends at bit n - 1
+  unsigned mask = 0u;
+  int r0 = e.e0, r1 = e.e1, r2 = e.e2;
+  for (int y = 0; y < bh; ++y) {
+    int a0 = r0, a1 = r1, a2 = r2;
+    for (int x = 0; x < bw; ++x) {
+      mask = (mask >> 1) | (~(unsigned)(a0 | a1 | a2) & 0x80000000u);
+      a0 += e.sx0; a1 += e.sx1; a2 += e.sx2;
+    }
+    r0 += e.sy0; r1 += e.sy1; r2 += e.sy2;
+  }
+  b.mask = mask >> (32 - bw * bh);
+  if (b.mask == 0u) return;
+  b.place = (((py0 - y0) << bshift_x) + (px0 - x0)) | (bw << 16);
+  const float rA = approx_rcp(f32_from_i64(s.A));
+  const DepthSetup d = depth_setup(s, rA, tag);
+  int* w = wst + lane;
+  w[FS_E1 * 32] = e.e1 + e.b1;  // exact edge functions at the box's first pixel
+  w[FS_E2 * 32] = e.e2 + e.b2;
+  w[FS_SX1 * 32] = e.sx1; w[FS_SY1 * 32] = e.sy1;
+  w[FS_SX2 * 32] = e.sx2; w[FS_SY2 * 32] = e.sy2;
+  w[FS_K1 * 32] = __float_as_int(d.k1); w[FS_K2 * 32] = __float_as_int(d.k2);
+  w[FS_D1 * 32] = d.d1; w[FS_D2 * 32] = d.d2;
+  w[FS_A * 32] = d.fast ? d.A : -d.A;
+  w[FS_KLO * 32] = (int)(unsigned)d.kbase;
+  w[FS_KHI * 32] = (int)(unsigned)(d.kbase >> 32);
+}
+
+// Depth key of one compacted fragment: descriptor = tile-local pixel index
+// (12 bits) | column in the box << 12 | row << 17 | staging lane << 22.  The
+// same quotient and key as key_min_box.
+__device__ __forceinline__ void fragment_key(const int* wst, unsigned desc, unsigned long long* skey) {
+  const int* w = wst + (desc >> 22);
+  const int rx = (desc >> 12) & 31, ry = (desc >> 17) & 31, idx = desc & 0xFFF;
+  // covered: w1, w2 in [0, A] < 2^30, exact in wrapping 32-bit arithmetic
+  const int w1 = (int)((unsigned)w[FS_E1 * 32] + (unsigned)rx * (unsigned)w[FS_SX1 * 32] +
+                       (unsigned)ry * (unsigned)w[FS_SY1 * 32]);
+  const int w2 = (int)((unsigned)w[FS_E2 * 32] + (unsigned)rx * (unsigned)w[FS_SX2 * 32] +
+                       (unsigned)ry * (unsigned)w[FS_SY2 * 32]);
+  const float k1 = __int_as_float(w[FS_K1 * 32]), k2 = __int_as_float(w[FS_K2 * 32]);
+  const int d1 = w[FS_D1 * 32], d2 = w[FS_D2 * 32], sA = w[FS_A * 32];
+  int q = __float2int_rd(__fmaf_rn((float)w1, k1, (float)w2 * k2));
+  if (sA > 0) {
+    int r = (int)((unsigned)w1 * (unsigned)d1 + (unsigned)w2 * (unsigned)d2 - (unsigned)q * (unsigned)sA);
+    for (int it = 0; r < 0 && it < DIV_FIX_LIMIT; ++it) { --q; r += sA; }
+    for (int it = 0; r >= sA && it < DIV_FIX_LIMIT; ++it) { ++q; r -= sA; }
+  } else {
+    const long long A = -(long long)sA;
+    long long r = (long long)w1 * d1 + (long long)w2 * d2 - (long long)q * A;
+    for (int it = 0; r < 0 && it < DIV_FIX_LIMIT; ++it) { --q; r += A; }
+    for (int it = 0; r >= A && it < DIV_FIX_LIMIT; ++it) { ++q; r -= A; }
+  }
+  // the depth field starts at bit 40: q moves the high word by q << 8
+  const unsigned hi = (unsigned)w[FS_KHI * 32] + ((unsigned)q << 8);
+  const unsigned long long k = ((unsigned long long)hi << 32) | (unsigned)w[FS_KLO * 32];
+  if (k < skey[idx]) atomicMin(skey + idx, k);
+}
+
+// Called by every lane of the warp: hands out the warp's covered samples of
+// small boxes FRAG_CAP at a time.  Returns the warp's fragment count.
+__device__ __forceinline__ unsigned fragment_pass(const SmallBox& b, int bshift_x, int* wst, unsigned long long* skey,
+                                                  int lane) {
+  if (!__any_sync(FULL_MASK, b.mask != 0u)) return 0u;
+  int* list = wst + FST_WORDS * 32;
+  const int cnt = __popc(b.mask);
+  const MultiSpan m = warp_prefix(cnt, lane);
+  int pos = m.incl - cnt;
+  unsigned mask = b.mask;
+  const int first = b.place & 0xFFFF, bw = b.place >> 16;
+  // 65536 / bw to within 2 ulp, floored, plus one: within [65536 / bw, 65536 / bw + 2),
+  // which makes (j * M) >> 16 = floor(j / bw) for every j < 32
+  const unsigned M = __float2uint_rz(__fdividef(65536.0f, (float)bw)) + 1u;
+  for (int base = 0; base < m.total; base += FRAG_CAP) {
+    while (mask != 0u && pos < base + FRAG_CAP) {
+      const int j = __ffs(mask) - 1;
+      mask &= mask - 1u;
+      const int ry = (int)(((unsigned)j * M) >> 16), rx = j - ry * bw;
+      list[pos - base] = (first + (ry << bshift_x) + rx) | (rx << 12) | (ry << 17) | (lane << 22);
+      ++pos;
+    }
+    __syncwarp();
+    const int n = min(FRAG_CAP, m.total - base);
+    for (int k = lane; k < n; k += 32) fragment_key(wst, (unsigned)list[k], skey);
+    __syncwarp();
+  }
+  return (unsigned)m.total;
 }
 
 // A warp covers a large triangle's box 32 pixels at a time; the ballot of
@@ -567,9 +688,12 @@ __device__ __forceinline__ void process_tile(const TileScene& p, int tile, unsig
   const int x0 = tx << p.g.bshift_x, y0 = ty << p.g.bshift_y;
   const int x1 = min(x0 + bin_w, p.g.W) - 1, y1 = min(y0 + bin_h, p.g.H) - 1;
   unsigned long long* skey = sm.skey;
+  int* wst = sm.sfrag + warp * FRAG_WARP_WORDS;
   for (unsigned c = beg; c < end; c += nt) {
     const unsigned i = c + tid;
     bool pushed = false;
+    SmallBox sb;
+    sb.mask = 0u;
     if (i < end) {
       unsigned t = __ldg(bin_tris + i) - (unsigned)p.tri_base;
       unsigned slot = (i - beg) < (unsigned)p.nslots ? (i - beg) : no_slot;
@@ -595,36 +719,48 @@ __device__ __forceinline__ void process_tile(const TileScene& p, int tile, unsig
         const unsigned long long tag = ((unsigned long long)t << p.slot_bits) | slot;
         if (STATS) st.tests += npx;
         if (npx <= p.small_px) {
-          unsigned f;
-          if (maxX - minX < 32768 && maxY - minY < 32768)
-            f = raster_thread32(s, tag, px0, px1, py0, py1, x0, y0, p.g.bshift_x, skey);
-          else
+          unsigned f = 0u;
+          if (maxX - minX < 32768 && maxY - minY < 32768) {
+            if (npx <= 32)  // coverage only; the warp's fragment_pass takes the depths
+              small_box(s, tag, px0, px1, py0, py1, x0, y0, p.g.bshift_x, wst, lane, sb);
+            else
+              f = raster_thread32(s, tag, px0, px1, py0, py1, x0, y0, p.g.bshift_x, skey);
+          } else {
             f = raster_thread64(s, tag, px0, px1, py0, py1, x0, y0, p.g.bshift_x, skey);
+          }
           if (STATS) st.frags += f;
         } else {
           // the ring counter only ever grows; with nt a power of two the ring
           // index stays consistent across its 2^32 wrap
           const unsigned q = atomicAdd(sm.s_nbig, 1u);
-          int* e = sm.sbig + (q & (nt - 1)) * BIG_REC;
-          e[0] = s.X0; e[1] = s.Y0; e[2] = s.X1; e[3] = s.Y1; e[4] = s.X2; e[5] = s.Y2;
-          e[6] = s.Z0; e[7] = s.Z1; e[8] = s.Z2;
-          e[9] = (int)(unsigned)(s.A & 0xFFFFFFFFll); e[10] = (int)(s.A >> 32);
-          e[11] = (int)t; e[12] = (int)slot;
+          sm.sbig[q & (nt - 1)] = tid;
+          int* e = wst + lane;
+          e[BG_X0 * 32] = s.X0; e[BG_Y0 * 32] = s.Y0; e[BG_X1 * 32] = s.X1; e[BG_Y1 * 32] = s.Y1;
+          e[BG_X2 * 32] = s.X2; e[BG_Y2 * 32] = s.Y2;
+          e[BG_Z0 * 32] = s.Z0; e[BG_Z1 * 32] = s.Z1; e[BG_Z2 * 32] = s.Z2;
+          e[BG_ALO * 32] = (int)(unsigned)(s.A & 0xFFFFFFFFll); e[BG_AHI * 32] = (int)(s.A >> 32);
+          e[BG_T * 32] = (int)t; e[BG_SLOT * 32] = (int)slot;
           pushed = true;
         }
       }
+    }
+    {
+      const unsigned f = fragment_pass(sb, p.g.bshift_x, wst, skey, lane);
+      if (STATS && lane == 0) st.frags += f;
     }
     // every thread gets the same count of queued large triangles
     const unsigned nbig = (unsigned)__syncthreads_count(pushed);
     if (nbig != 0u) {
       for (unsigned q = warp; q < nbig; q += nwarps) {
-        const int* e = sm.sbig + ((big_base + q) & (nt - 1)) * BIG_REC;
+        const int owner = sm.sbig[(big_base + q) & (nt - 1)];
+        const int* e = sm.sfrag + (owner >> 5) * FRAG_WARP_WORDS + (owner & 31);
         TriSetup s;
-        s.X0 = e[0]; s.Y0 = e[1]; s.X1 = e[2]; s.Y1 = e[3]; s.X2 = e[4]; s.Y2 = e[5];
-        s.Z0 = e[6]; s.Z1 = e[7]; s.Z2 = e[8];
-        s.A = (long long)(((unsigned long long)(unsigned)e[10] << 32) | (unsigned)e[9]);
+        s.X0 = e[BG_X0 * 32]; s.Y0 = e[BG_Y0 * 32]; s.X1 = e[BG_X1 * 32]; s.Y1 = e[BG_Y1 * 32];
+        s.X2 = e[BG_X2 * 32]; s.Y2 = e[BG_Y2 * 32];
+        s.Z0 = e[BG_Z0 * 32]; s.Z1 = e[BG_Z1 * 32]; s.Z2 = e[BG_Z2 * 32];
+        s.A = (long long)(((unsigned long long)(unsigned)e[BG_AHI * 32] << 32) | (unsigned)e[BG_ALO * 32]);
         s.v0 = s.v1 = s.v2 = 0;  // not needed to rasterize
-        const unsigned t = (unsigned)e[11], slot = (unsigned)e[12];
+        const unsigned t = (unsigned)e[BG_T * 32], slot = (unsigned)e[BG_SLOT * 32];
         int px0, px1, py0, py1;
         centre_range(min(s.X0, min(s.X1, s.X2)), max(s.X0, max(s.X1, s.X2)), x0, x1, px0, px1);
         centre_range(min(s.Y0, min(s.Y1, s.Y2)), max(s.Y0, max(s.Y1, s.Y2)), y0, y1, py0, py1);
@@ -685,7 +821,8 @@ inline void tile_layout(int num_triangles, int bin_px, int mode, bool has_color,
 }
 
 inline size_t tile_smem_bytes(int bin_px, int threads, int nslots, int rec_stride) {
-  return (size_t)bin_px * 8 + (size_t)threads * BIG_REC * 4 + (size_t)nslots * rec_stride * 4;
+  return (size_t)bin_px * 8 + (size_t)threads * 4 + (size_t)(threads / 32) * FRAG_WARP_WORDS * 4 +
+         (size_t)nslots * rec_stride * 4;
 }
 
 }  // namespace piko

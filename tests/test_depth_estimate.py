@@ -98,3 +98,34 @@ def test_extreme_corners():
     w1, w2, d1, d2, A = (np.array(c, dtype=np.int64) for c in zip(*vals))
     assert (np.abs(d1) + np.abs(d2) < (1 << 22)).all()
     _check(w1, w2, d1, d2, A, 3)
+
+
+# ---------------------------------------------------------------------------
+# Compacted small boxes: a thread walks a box of at most 32 pixels for
+# coverage only, shifting each sample's bit in from the top (mask = mask >> 1
+# | covered << 31), then shifts the mask down by 32 - n; bit j is then the
+# box's j-th pixel in row-major order.  The warp's fragment pass recovers the
+# row of bit j as (j * M) >> 16 with M = floor(fl(65536 / bw)) + 1, the
+# quotient taken with a fast division good to 2 ulp.
+
+
+def test_small_box_mask_bit_order():
+    rng = np.random.default_rng(20261204)
+    for n in range(1, 33):
+        for _ in range(50):
+            cov = rng.random(n) < 0.5
+            mask = 0
+            for c in cov:
+                mask = (mask >> 1) | (0x80000000 if c else 0)
+            mask >>= 32 - n
+            assert [(mask >> j) & 1 for j in range(n)] == [int(c) for c in cov]
+
+
+def test_small_box_row_from_bit():
+    for bw in range(1, 33):
+        q = np.float32(65536.0) / np.float32(bw)
+        for ulps in (-2, -1, 0, 1, 2):
+            M = int(np.floor(np.float64(_ulp_shift(np.array([q], dtype=np.float32), ulps)[0]))) + 1
+            assert 65536 / bw <= M < 65536 / bw + 2
+            for j in range(32):
+                assert (j * M) >> 16 == j // bw, (bw, j, M)

@@ -107,6 +107,49 @@ def test_thread_and_warp_raster_paths_agree(small_px, threads):
     assert_keys_equal(out["key"], ref, f"small_px={small_px} threads={threads}")
 
 
+def _dense_small_boxes(W, H, T, seed):
+    """Right triangles with legs 4.9 x 5.9 px (boxes of at most 5 x 6 pixel
+    centres) at random places and orientations, about seven deep."""
+    rng = np.random.default_rng(seed)
+    cx = rng.uniform(0, W - 5, T)
+    cy = rng.uniform(0, H - 6, T)
+    fx = rng.random(T) < 0.5
+    fy = rng.random(T) < 0.5
+    ax = np.where(fx, cx + 4.9, cx)
+    bx = np.where(fx, cx, cx + 4.9)
+    ay = np.where(fy, cy + 5.9, cy)
+    cy2 = np.where(fy, cy, cy + 5.9)
+    px = np.stack([ax, bx, ax], 1)
+    py = np.stack([ay, ay, cy2], 1)
+    z = rng.integers(0, 1 << 24, (T, 3)) * (2.0 / 16777215.0) - 1.0
+    pos = np.stack([px / W * 2 - 1, 1 - py / H * 2, z, np.ones_like(z)], -1).reshape(3 * T, 4)
+    color = rng.random((3 * T, 3))
+    return S.Scene(W, H, pos.astype(np.float32), np.arange(3 * T, dtype=np.int32).reshape(T, 3),
+                   color=color.astype(np.float32), name=f"dense{T}_{W}x{H}")
+
+
+@pytest.mark.parametrize("bins", [(8, 8), (16, 16), (64, 64), (32, 8)])
+def test_dense_small_boxes_many_fragments_per_warp(bins):
+    """Small boxes seven deep: a warp's boxes hold hundreds of covered
+    samples, so the warp hands them out over several rounds of its fragment
+    list.  Keys bit-exact and colour within 1e-5 under each raster path
+    (boxes by the warp's compacted fragments, by one thread each, by whole
+    warps), with the same fragment count."""
+    from paper_1404_6293_gb300 import _lib as L
+    s = _dense_small_boxes(99, 70, 3000, seed=4242 + bins[0])
+    ref, _ = oracle.raster_bbox(s)
+    rgba_ref = oracle.shade(s, ref)
+    counts = []
+    for small_px in (32, 4096, 0):
+        out = rasterize(s, bins[0], bins[1], "dynamic",
+                        {L.PIKO_OPT_SMALL_TRI_PIXELS: small_px, L.PIKO_OPT_STATS: 1})
+        assert out["status"] == 0
+        assert_keys_equal(out["key"], ref, f"bins {bins} small_px={small_px}")
+        assert np.abs(out["rgba"] - rgba_ref).max() <= RGB_TOL
+        counts.append(out["r"].stats()["fragments"])
+    assert counts[0] == counts[1] == counts[2] > 0
+
+
 def test_lambert_heightfield_small():
     s = S.heightfield(320, 180, 80, 40, seed=5)
     ref, _ = oracle.raster_bbox(s, threads=4)

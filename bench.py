@@ -445,6 +445,34 @@ def time_forward(ctx, r, ds, fb, K, W, stages=True):
     return step_ms, stage_ms
 
 
+def exact_bins_record(ctx, scene, ds, bins, schedule, K, W, threads=0) -> dict:
+    """The same forward with AssignBin's exact overlap test on (a handle of
+    its own): per-step and per-stage times and bin entries, beside the
+    bounding-box binning of the line."""
+    import numpy as np
+    from paper_1404_6293_gb300 import _lib as L
+    from paper_1404_6293_gb300.raster import Framebuffer, Rasterizer
+    rec = {}
+    for exact in (0, 1):
+        r = Rasterizer(scene.width, scene.height, bins, bins, schedule)
+        if threads:
+            r.set_option(L.PIKO_OPT_THREADS_PER_TILE, threads)
+        r.set_option(L.PIKO_OPT_EXACT_BINS, exact)
+        fb = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode)
+        stats, _ = size_and_count(r, ds, fb)
+        step_ms, stage_ms = time_forward(ctx, r, ds, fb, K, W)
+        if r.status()[0] != 0:
+            raise RuntimeError("status error in the exact-bins loop")
+        sm = stage_ms.mean(axis=0)
+        rec["exact" if exact else "bounding_box"] = {
+            "forward_ms": float(np.median(step_ms)), "bin_entries": stats["bin_entries"],
+            "stage_ms": dict(zip(["vertex", "setup_count", "scan", "scatter", "process"], (float(x) for x in sm)))}
+        r.close()
+    rec["how"] = ("PIKO_OPT_EXACT_BINS: entries only in bins the triangle overlaps (separating-axis test of its "
+                  "edges against the bin's pixel centres), against bounding-box bins; same keys")
+    return rec
+
+
 def size_and_count(r, ds, fb):
     """One forward that sizes the bin lists, then one with the work counters:
     (stats, covered pixels).  Leaves the capacity check off and the counters off."""
@@ -541,6 +569,7 @@ def run_ours(args):
         n_trials = len(next(iter(tuner.cache.values()))["trials"])
         tuner.close()
         args.bins, args.schedule, args.threads = knobs["bin"][0], knobs["schedule"], knobs["threads"]
+        args.exact_bins = knobs["exact_bins"]
         cfg.update({"bin": list(knobs["bin"]), "schedule": args.schedule,
                     "knobs": f"autotuned: fastest forward of {n_trials} candidates ({tune_s:.1f} s, untimed)"})
     r = Rasterizer(scene.width, scene.height, args.bins, args.bins, args.schedule)
@@ -553,6 +582,9 @@ def run_ours(args):
     if args.small_px:
         r.set_option(L.PIKO_OPT_SMALL_TRI_PIXELS, args.small_px)
         cfg["small_tri_pixels"] = args.small_px
+    if args.exact_bins:
+        r.set_option(L.PIKO_OPT_EXACT_BINS, 1)
+        cfg["exact_bins"] = 1
     ds = DeviceScene.from_host(scene)
     fb = Framebuffer.allocate(scene.width, scene.height, scene.shade_mode)
     stats, covered = size_and_count(r, ds, fb)
@@ -614,6 +646,8 @@ def run_ours(args):
                       "(tests/test_gpu_full_size.py)"}
     if rank == 0 and world == 1 and not args.no_configs:
         line["bin_sweep"] = bin_sweep(args, ctx, scene, ds)
+        line["exact_bins"] = exact_bins_record(ctx, scene, ds, args.bins, args.schedule, K, args.warmup,
+                                               args.threads)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene, args.cpu_seconds, args.perspective)
     if rank == 0 and world == 1 and not args.no_configs:
@@ -930,6 +964,7 @@ def measure_deferred(args, ctx) -> dict:
            "clocks": clk, "gpu_launches": 6 * K,
            "parity": "keys bit-exact, G-buffer within one binary16 step, light pass <= 1e-5 vs the oracle "
                      "(tests/test_gpu_parity.py, tests/test_gpu_full_size.py)"}
+    rec["exact_bins"] = exact_bins_record(ctx, scene, ds, bins, args.deferred_schedule, K, args.warmup, args.threads)
     if not args.no_cpu_baseline:
         import oracle
         lt_host = lights.cpu().numpy()
@@ -1308,6 +1343,8 @@ def main():
     ap.add_argument("--small-px", type=int, default=0,
                     help="largest box (pixels inside a tile) one thread rasterizes; larger boxes take a warp "
                          "(0: library default)")
+    ap.add_argument("--exact-bins", type=int, default=0, choices=[0, 1],
+                    help="heightfield workload: AssignBin's exact overlap test instead of bounding-box bins")
     ap.add_argument("--deferred-bins", type=int, default=16)
     ap.add_argument("--deferred-schedule", default="hardware", choices=["static", "dynamic", "hardware", "fused", "unfused"])
     ap.add_argument("--batch-scenes", type=int, default=256)

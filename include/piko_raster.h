@@ -118,6 +118,16 @@ extern "C" {
                                        (perspective-correct).  Single-scene calls only
                                        (piko_raster_forward_batch rejects it); the sub-triangle
                                        list grows like the bin lists.  Default 0: culling      */
+#define PIKO_OPT_EXACT_BINS 12      /* 1: AssignBin gives a triangle that spans several bins
+                                       an entry only in the bins it overlaps: none of its
+                                       three edges may fail the fill-rule test at every
+                                       pixel centre of the bin inside its bounding box (the
+                                       separating-axis test of the triangle against that
+                                       rectangle of centres).  Fewer bin entries for large
+                                       and thin triangles, identical output; the count and
+                                       scatter passes do the test.  Single-scene calls;
+                                       piko_raster_forward_batch bins by bounding box.
+                                       Default 0: bounding-box bins (AssignToBoundingBox) */
 #define PIKO_OPT_WAIT_BUDGET 9      /* how long a device-side wait (scan look-back, batch grid
                                        barrier) may spin before it gives up, records
                                        PIKO_ERR_TIMEOUT and lets the frame's later phases

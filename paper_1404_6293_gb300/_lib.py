@@ -40,6 +40,7 @@ PIKO_OPT_PERSPECTIVE = 8
 PIKO_OPT_WAIT_BUDGET = 9
 PIKO_OPT_TEST_WITHHOLD = 10
 PIKO_OPT_CLIP = 11
+PIKO_OPT_EXACT_BINS = 12
 PIKO_NUM_STAGE_EVENTS = 6
 
 ERROR_NAMES = {

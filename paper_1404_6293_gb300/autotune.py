@@ -6,7 +6,9 @@ of tiny uniform triangles; fusing stages trades load balance for locality).
 This tuner searches the same knobs automatically: for a scene it times the
 forward pass under every (bin size, schedule, threads per bin) candidate with
 CUDA events and keeps the fastest; the fused (no tiling) and unfused (one
-kernel per stage) mappings of Sec. 7.2 are two more candidates.  Threads per bin is the third template
+kernel per stage) mappings of Sec. 7.2 are two more candidates, and the best binned candidate is
+timed once more with AssignBin's exact overlap test (PIKO_OPT_EXACT_BINS) instead of bounding-box
+bins, which pays for large and thin triangles.  Threads per bin is the third template
 parameter of the paper's Listing 1 stage; small triangles favour fewer
 threads per bin (more CTAs per SM), large ones more (more warps per tile).  Results are cached by workload features (resolution,
 triangle count, coverage density, shading mode) so that similar scenes share
@@ -65,8 +67,10 @@ def features(scene: DeviceScene) -> str:
 class Autotuner:
     def __init__(self, bins: Iterable[Tuple[int, int]] = DEFAULT_BINS,
                  schedules: Iterable[str] = DEFAULT_SCHEDULES, reps: int = 3, cache_path: Optional[str] = None,
-                 tune_threads: bool = True, other_mappings: Iterable[str] = OTHER_MAPPINGS):
+                 tune_threads: bool = True, other_mappings: Iterable[str] = OTHER_MAPPINGS,
+                 tune_exact: bool = True):
         self.bins = tuple(tuple(b) for b in bins)
+        self.tune_exact = tune_exact
         self.schedules = tuple(schedules)
         self.other_mappings = tuple(other_mappings)
         self.tune_threads = tune_threads
@@ -78,19 +82,23 @@ class Autotuner:
                 self.cache = json.load(f)
         self._handles: Dict[tuple, Rasterizer] = {}
 
-    def _handle(self, W, H, bw, bh, sched, threads=0) -> Rasterizer:
-        k = (W, H, bw, bh, sched, threads)
+    def _handle(self, W, H, bw, bh, sched, threads=0, exact=0) -> Rasterizer:
+        k = (W, H, bw, bh, sched, threads, exact)
         if k not in self._handles:
             r = Rasterizer(W, H, bw, bh, sched)
             if threads:
                 r.set_option(L.PIKO_OPT_THREADS_PER_TILE, threads)
+            if exact:
+                r.set_option(L.PIKO_OPT_EXACT_BINS, 1)
             self._handles[k] = r
         return self._handles[k]
 
-    def time_candidate(self, scene: DeviceScene, bw: int, bh: int, sched: str, threads: int = 0) -> float:
+    def time_candidate(self, scene: DeviceScene, bw: int, bh: int, sched: str, threads: int = 0,
+                       exact: int = 0) -> float:
         """Median forward time in ms of one candidate (after a sizing pass);
-        threads 0 keeps the library's CTA size."""
-        r = self._handle(scene.width, scene.height, bw, bh, sched, threads)
+        threads 0 keeps the library's CTA size; exact 1 bins by the exact
+        overlap test."""
+        r = self._handle(scene.width, scene.height, bw, bh, sched, threads, exact)
         fb = r.forward(scene)  # sizes the bin lists
         r.status()
         times: List[float] = []
@@ -115,6 +123,13 @@ class Autotuner:
                     trials.append({"bin": [bw, bh], "schedule": sched, "threads": th, "ms": ms})
                     if best is None or ms < best["ms"]:
                         best = {"bin": [bw, bh], "schedule": sched, "threads": th, "ms": ms}
+        if self.tune_exact and best is not None:
+            bw, bh = best["bin"]
+            ms = self.time_candidate(scene, bw, bh, best["schedule"], best["threads"], exact=1)
+            trials.append({"bin": [bw, bh], "schedule": best["schedule"], "threads": best["threads"],
+                           "exact_bins": 1, "ms": ms})
+            if ms < best["ms"]:
+                best = dict(best, exact_bins=1, ms=ms)
         bw, bh = self.bins[0] if self.bins else (16, 16)
         for sched in self.other_mappings:
             th = default_threads(bw * bh)
@@ -133,7 +148,8 @@ class Autotuner:
             self.cache[key] = self.tune(scene)
         c = self.cache[key]
         bw, bh = c["bin"]
-        return {"bin": (bw, bh), "schedule": c["schedule"], "threads": c.get("threads", default_threads(bw * bh))}
+        return {"bin": (bw, bh), "schedule": c["schedule"], "threads": c.get("threads", default_threads(bw * bh)),
+                "exact_bins": c.get("exact_bins", 0)}
 
     def choose(self, scene: DeviceScene) -> Tuple[Tuple[int, int], str]:
         k = self.knobs(scene)

@@ -40,6 +40,7 @@ struct piko_raster {
   int stats = 0;
   int batch_launch = 0;  // 0 persistent cooperative, 1 one launch per phase
   int clip = 0;                      // near/far clipping instead of culling (PIKO_OPT_CLIP)
+  int exact_bins = 0;                // exact triangle-vs-bin overlap in AssignBin (PIKO_OPT_EXACT_BINS)
   long long wait_budget = 40000000;  // clock cycles a device-side wait may take (PIKO_OPT_WAIT_BUDGET)
   int withhold = 0;                  // test hooks (PIKO_OPT_TEST_WITHHOLD)
   BatchState* batch = nullptr;
@@ -62,6 +63,10 @@ struct piko_raster {
   unsigned scan_epoch = 0;
   unsigned* bin_tris = nullptr;
   long long ecap = 0;
+  // AssignBin's list of heavy triangles (chunks of (triangle, bin) pairs
+  // spread over whole CTAs), and the count pass's parity
+  uint2* heavy = nullptr;
+  unsigned heavy_epoch = 0;
   // fragment buffers of the unfused pipeline (PIKO_SCHED_UNFUSED)
   unsigned* frag_pix = nullptr;
   unsigned long long* frag_key = nullptr;
@@ -163,6 +168,7 @@ piko_raster* piko_raster_create(int width, int height, int bin_w, int bin_h, int
             cudaMalloc(&h->chunk_state, sizeof(unsigned long long) * scan_chunks(h->nbins)) == cudaSuccess &&
             cudaMemset(h->chunk_state, 0, sizeof(unsigned long long) * scan_chunks(h->nbins)) == cudaSuccess &&
             cudaMalloc(&h->status, sizeof(DevStatus)) == cudaSuccess &&
+            cudaMalloc(&h->heavy, sizeof(uint2) * HEAVY_LIST_CAP) == cudaSuccess &&
             cudaMallocHost(&h->h_needed, sizeof(unsigned long long)) == cudaSuccess &&
             cudaMallocHost(&h->h_frags, sizeof(unsigned)) == cudaSuccess &&
             cudaMallocHost(&h->h_clips, sizeof(unsigned)) == cudaSuccess &&
@@ -189,6 +195,7 @@ void piko_raster_destroy(piko_raster* h) {
   cudaFree(h->cursor);
   cudaFree(h->chunk_state);
   cudaFree(h->bin_tris);
+  cudaFree(h->heavy);
   cudaFree(h->frag_pix);
   cudaFree(h->frag_key);
   cudaFree(h->frag_rgba);
@@ -253,6 +260,10 @@ int piko_raster_set_option(piko_raster* h, int key, int value) {
     case PIKO_OPT_CLIP:
       if (value != 0 && value != 1) return fail(h, PIKO_ERR_INVALID_ARG, "clip must be 0 or 1");
       h->clip = value;
+      return PIKO_OK;
+    case PIKO_OPT_EXACT_BINS:
+      if (value != 0 && value != 1) return fail(h, PIKO_ERR_INVALID_ARG, "exact bins must be 0 or 1");
+      h->exact_bins = value;
       return PIKO_OK;
     case PIKO_OPT_WAIT_BUDGET:
       if (value < 1 || value > 1000000) return fail(h, PIKO_ERR_INVALID_ARG, "wait budget must be 1..1000000 kcycles");
@@ -474,7 +485,7 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
   for (int attempt = 0;; ++attempt) {
     if (h->stats && attempt > 0) cudaMemsetAsync(&h->status->binned, 0, sizeof(unsigned long long), st);
     launch_setup_count(h->g, T, s->tris, V, h->vtx, h->rect, h->bin_count, h->status, h->stats, h->num_sms, st,
-                       clip_tris, clip_cap);
+                       clip_tris, clip_cap, h->exact_bins, h->heavy, HEAVY_LIST_CAP, ++h->heavy_epoch);
     if (ev) cudaEventRecord(h->stage_ev[2], st);
     launch_scan(h->nbins, h->bin_count, h->bin_off, h->cursor, (unsigned long long)h->ecap, h->status,
                 h->chunk_state, ++h->scan_epoch, st, h->wait_budget, h->withhold);
@@ -493,7 +504,8 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
     if (e != cudaSuccess) return cuda_fail(h, e, "status clear");
   }
   launch_scatter(h->g, T, h->rect, h->bin_off, h->cursor, h->bin_tris, (unsigned long long)h->ecap, h->status,
-                 h->num_sms, st, clip_tris, clip_cap);
+                 h->num_sms, st, clip_tris, clip_cap, h->exact_bins ? s->tris : nullptr, V, h->vtx, h->heavy,
+                 HEAVY_LIST_CAP, h->heavy_epoch);
   if (ev) cudaEventRecord(h->stage_ev[4], st);
 
   ProcessParams p;

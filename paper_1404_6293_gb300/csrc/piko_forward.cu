@@ -203,11 +203,125 @@ __device__ __forceinline__ int pair_bin(const RasterGeom& g, int k, int first, i
   return (y0 + yy) * g.nbx + x0 + (local - yy * bw);
 }
 
+// Optional exact overlap test of AssignBin (PIKO_OPT_EXACT_BINS): a
+// triangle spanning several bins gets an entry in bin b only if none of its
+// three edges fails the fill-rule test at every pixel centre of b that lies
+// in the triangle's bounding box (the separating-axis test of the triangle
+// against that rectangle of centres: its own axes are the bounding box's,
+// which the rectangle already lies in).  A dropped bin holds no covered
+// sample of the triangle, so the keys do not change; only bin entries of
+// large or thin triangles go away.
+struct OverlapTri {
+  int X0, Y0, X1, Y1, X2, Y2;  // oriented (A > 0)
+  int px0, px1, py0, py1;      // pixel centres inside the bounding box, clipped to the screen
+};
+
+__device__ __forceinline__ OverlapTri overlap_tri(const RasterGeom& g, int4 p0, int4 p1, int4 p2) {
+  const long long A = (long long)(p1.x - p0.x) * (p2.y - p0.y) - (long long)(p2.x - p0.x) * (p1.y - p0.y);
+  if (A < 0) {
+    const int4 q = p1;
+    p1 = p2;
+    p2 = q;
+  }
+  OverlapTri o;
+  o.X0 = p0.x; o.Y0 = p0.y; o.X1 = p1.x; o.Y1 = p1.y; o.X2 = p2.x; o.Y2 = p2.y;
+  centre_range(min(p0.x, min(p1.x, p2.x)), max(p0.x, max(p1.x, p2.x)), 0, g.W - 1, o.px0, o.px1);
+  centre_range(min(p0.y, min(p1.y, p2.y)), max(p0.y, max(p1.y, p2.y)), 0, g.H - 1, o.py0, o.py1);
+  return o;
+}
+
+// Edge a -> b passes its fill-rule test at some centre of columns [x0, x1] x
+// rows [y0, y1]: the edge function (Xb - Xa)(Py - Ya) - (Yb - Ya)(Px - Xa) is
+// largest at the corner where -dy (Px) and dx (Py) push it up.
+__device__ __forceinline__ bool edge_reaches(int Xa, int Ya, int Xb, int Yb, int x0, int x1, int y0, int y1) {
+  const int dx = Xb - Xa, dy = Yb - Ya;
+  const int Px = 256 * (dy < 0 ? x1 : x0) + 128, Py = 256 * (dx > 0 ? y1 : y0) + 128;
+  return (long long)dx * (Py - Ya) - (long long)dy * (Px - Xa) - (1 - top_left(dx, dy)) >= 0;
+}
+
+__device__ __forceinline__ bool overlaps_bin(const RasterGeom& g, const OverlapTri& o, int bx, int by) {
+  const int x0 = max(bx << g.bshift_x, o.px0), x1 = min(((bx + 1) << g.bshift_x) - 1, o.px1);
+  const int y0 = max(by << g.bshift_y, o.py0), y1 = min(((by + 1) << g.bshift_y) - 1, o.py1);
+  return edge_reaches(o.X1, o.Y1, o.X2, o.Y2, x0, x1, y0, y1) && edge_reaches(o.X2, o.Y2, o.X0, o.Y0, x0, x1, y0, y1) &&
+         edge_reaches(o.X0, o.Y0, o.X1, o.Y1, x0, x1, y0, y1);
+}
+
+// The owner lane's OverlapTri, read by every lane of the warp.
+__device__ __forceinline__ OverlapTri shfl_overlap(const OverlapTri& o, int owner) {
+  OverlapTri r;
+  r.X0 = __shfl_sync(FULL_MASK, o.X0, owner); r.Y0 = __shfl_sync(FULL_MASK, o.Y0, owner);
+  r.X1 = __shfl_sync(FULL_MASK, o.X1, owner); r.Y1 = __shfl_sync(FULL_MASK, o.Y1, owner);
+  r.X2 = __shfl_sync(FULL_MASK, o.X2, owner); r.Y2 = __shfl_sync(FULL_MASK, o.Y2, owner);
+  r.px0 = __shfl_sync(FULL_MASK, o.px0, owner); r.px1 = __shfl_sync(FULL_MASK, o.px1, owner);
+  r.py0 = __shfl_sync(FULL_MASK, o.py0, owner); r.py1 = __shfl_sync(FULL_MASK, o.py1, owner);
+  return r;
+}
+
+// pair_bin's bin coordinates
+__device__ __forceinline__ void pair_xy(int k, int first, int x0, int y0, int bw, int& bx, int& by) {
+  const int local = k - first;
+  const int yy = local / bw;
+  by = y0 + yy;
+  bx = x0 + (local - yy * bw);
+}
+
 // BinRect encoding: culled 0xFFFFFFFF; single bin: lo = x | y << 16 | 0x8000,
 // hi = slot inside the bin's single-bin part; several bins: lo = x0 | y0 << 16,
 // hi = x1 | y1 << 16.  Bin coordinates are below 4096 (width / 8).
 constexpr unsigned RECT_CULLED = 0xFFFFFFFFu;
 constexpr unsigned RECT_SINGLE = 0x8000u;
+
+// Heavy triangles of AssignBin: a triangle spanning at least HEAVY_PAIRS
+// bins (a quarter-screen triangle spans thousands of 16x16 bins).  The count
+// pass walks such a triangle's bins with its whole warp, 32 bins a step,
+// with no per-pair owner search.  The scatter pass's cursor atomics return
+// a position, so a warp walking thousands of them in a row would be a long
+// chain of round trips while the rest of the grid has finished: when the
+// handle gives a heavy list, the count pass lists the triangle there as
+// chunks of HEAVY_CHUNK pairs and marks its rectangle RECT_HEAVY (bit 31 of
+// hi; bin coordinates are below 4096), and the scatter pass's CTAs take the
+// chunks after their own triangles, a pair per thread.  A list that is full leaves the
+// triangle's entries to its warp.
+constexpr int HEAVY_PAIRS = 256;
+constexpr int HEAVY_CHUNK = 256;
+constexpr unsigned RECT_HEAVY = 0x80000000u;
+constexpr unsigned HEAVY_NONE = 0xFFFFFFFFu;  // a chunk slot of a triangle that did not fit
+
+// Read after the grid dependency wait: the count pass that wrote it has
+// completed, so a plain (read-only path) load sees its final value.
+__device__ __forceinline__ unsigned heavy_count(const DevStatus* st, unsigned epoch, unsigned cap) {
+  const unsigned n = __ldg(&st->heavy_n[epoch & 1u]);
+  return n < cap ? n : cap;
+}
+
+// The vertices of triangle t (an input triangle, or clipped sub-triangle t - T).
+__device__ __forceinline__ void tri_points(int T, int t, const int* __restrict__ tris, int V,
+                                           const int4* __restrict__ vtx, const int4* __restrict__ clip_tris,
+                                           int4& p0, int4& p1, int4& p2, bool& ok) {
+  ok = true;
+  if (t < T) {
+    const int3 i = load_tri(tris, T, t);
+    if ((unsigned)i.x >= (unsigned)V || (unsigned)i.y >= (unsigned)V || (unsigned)i.z >= (unsigned)V) {
+      ok = false;
+      p0 = p1 = p2 = make_int4(0, 0, 0, 0);
+      return;
+    }
+    p0 = __ldg(vtx + i.x); p1 = __ldg(vtx + i.y); p2 = __ldg(vtx + i.z);
+  } else {
+    const int4* c = clip_tris + 3 * (size_t)(t - T);
+    p0 = c[0]; p1 = c[1]; p2 = c[2];
+  }
+}
+
+// Bin of pair k of a multi-bin rectangle.
+__device__ __forceinline__ void rect_pair(BinRect r, int k, int& bx, int& by, int& nb) {
+  const int bx0 = r.lo & 0xFFFF, by0 = r.lo >> 16, bx1 = r.hi & 0xFFFF, by1 = (r.hi >> 16) & 0x7FFF;
+  const int bw = bx1 - bx0 + 1;
+  nb = bw * (by1 - by0 + 1);
+  const int yy = k / bw;
+  by = by0 + yy;
+  bx = bx0 + (k - yy * bw);
+}
 
 // ======================================================================
 // Scan: one CTA per chunk of SCAN_CHUNK bins (scan_chunk in piko_scan.cuh).
@@ -261,10 +375,13 @@ __device__ __forceinline__ TriVerts gather_verts(int3 idx, int V, const int4* __
   return v;
 }
 
-// Count-pass work for one batch of 32 triangles (one per lane).
+// Count-pass work for one batch of 32 triangles (one per lane).  EXACT:
+// multi-bin pairs pass the exact overlap test first.
+template <bool EXACT>
 __device__ __forceinline__ void count_batch(const RasterGeom& g, int T, int t, int3 idx, const TriVerts& v,
                                             BinRect* __restrict__ rect, unsigned* __restrict__ cnt, int nbins,
-                                            DevStatus* st, int stats, int lane, unsigned lt_mask) {
+                                            DevStatus* st, int stats, int lane, unsigned lt_mask,
+                                            uint2* __restrict__ heavy, unsigned heavy_cap, unsigned* heavy_n) {
   bool valid = false;
   int bx0 = 0, by0 = 0, bx1 = -1, by1 = -1;
   if (t < T) {
@@ -297,6 +414,36 @@ __device__ __forceinline__ void count_batch(const RasterGeom& g, int T, int t, i
   unsigned slot = 0;
   if (single && lane == leader) slot = atomicAdd(cnt + bin, (unsigned)__popc(grp));
   slot = __shfl_sync(FULL_MASK, slot, leader) + __popc(grp & lt_mask);
+  const int bw = bx1 - bx0 + 1;
+  int nb = (valid && !single) ? bw * (by1 - by0 + 1) : 0;
+  bool listed = false;
+  OverlapTri ot;
+  if (EXACT && __any_sync(FULL_MASK, nb > 0)) ot = overlap_tri(g, v.p0, v.p1, v.p2);
+  // heavy triangles, one at a time: the whole warp walks its bins 32 at a
+  // time (no owner search), each lane stepping 32 bins along the rectangle
+  for (unsigned hv = __ballot_sync(FULL_MASK, nb >= HEAVY_PAIRS); hv != 0u; hv &= hv - 1u) {
+    const int owner = __ffs(hv) - 1;
+    const int hx0 = __shfl_sync(FULL_MASK, bx0, owner), hy0 = __shfl_sync(FULL_MASK, by0, owner);
+    const int hbw = __shfl_sync(FULL_MASK, bw, owner), hnb = __shfl_sync(FULL_MASK, nb, owner);
+    OverlapTri o;
+    if (EXACT) o = shfl_overlap(ot, owner);
+    const int sy = 32 / hbw, sx = 32 - sy * hbw;
+    int lx = lane % hbw, ly = lane / hbw;
+    for (int k = lane; k < hnb; k += 32) {
+      if (!EXACT || overlaps_bin(g, o, hx0 + lx, hy0 + ly)) atomicAdd(cnt + nbins + (hy0 + ly) * g.nbx + hx0 + lx, 1u);
+      lx += sx; ly += sy;
+      if (lx >= hbw) { lx -= hbw; ++ly; }
+    }
+  }
+  const bool heavy_tri = nb >= HEAVY_PAIRS;
+  if (heavy && heavy_tri) {
+    const unsigned nch = (unsigned)((nb + HEAVY_CHUNK - 1) / HEAVY_CHUNK);
+    const unsigned pos = atomicAdd(heavy_n, nch);
+    listed = pos < heavy_cap && nch <= heavy_cap - pos;
+    for (unsigned c = 0; c < nch && pos + c < heavy_cap; ++c)
+      heavy[pos + c] = make_uint2(listed ? (unsigned)t : HEAVY_NONE, c);
+  }
+  if (heavy_tri) nb = 0;  // counted above
   if (t < T) {
     BinRect r;
     if (!valid) {
@@ -304,12 +451,11 @@ __device__ __forceinline__ void count_batch(const RasterGeom& g, int T, int t, i
     } else if (single) {
       r.lo = (unsigned)bx0 | ((unsigned)by0 << 16) | RECT_SINGLE; r.hi = slot;
     } else {
-      r.lo = (unsigned)bx0 | ((unsigned)by0 << 16); r.hi = (unsigned)bx1 | ((unsigned)by1 << 16);
+      r.lo = (unsigned)bx0 | ((unsigned)by0 << 16);
+      r.hi = (unsigned)bx1 | ((unsigned)by1 << 16) | (listed ? RECT_HEAVY : 0u);
     }
     rect[t] = r;
   }
-  const int bw = bx1 - bx0 + 1;
-  const int nb = (valid && !single) ? bw * (by1 - by0 + 1) : 0;
   const MultiSpan m = warp_prefix(nb, lane);
   for (int k0 = 0; k0 < m.total; k0 += 32) {
     const int k = k0 + lane;
@@ -317,19 +463,33 @@ __device__ __forceinline__ void count_batch(const RasterGeom& g, int T, int t, i
     const int ox = __shfl_sync(FULL_MASK, bx0, owner), oy = __shfl_sync(FULL_MASK, by0, owner);
     const int obw = __shfl_sync(FULL_MASK, bw, owner);
     const int first = __shfl_sync(FULL_MASK, m.incl - nb, owner);
-    if (k < m.total) atomicAdd(cnt + nbins + pair_bin(g, k, first, ox, oy, obw), 1u);
+    if (EXACT) {
+      const OverlapTri o = shfl_overlap(ot, owner);
+      int bx, by;
+      pair_xy(k, first, ox, oy, obw, bx, by);
+      if (k < m.total && overlaps_bin(g, o, bx, by)) atomicAdd(cnt + nbins + by * g.nbx + bx, 1u);
+    } else if (k < m.total) {
+      atomicAdd(cnt + nbins + pair_bin(g, k, first, ox, oy, obw), 1u);
+    }
   }
 }
 
+template <bool EXACT>
 __global__ void __launch_bounds__(256) k_setup_count(RasterGeom g, int T, const int* __restrict__ tris, int V,
                                                      const int4* __restrict__ vtx, BinRect* __restrict__ rect,
                                                      unsigned* __restrict__ cnt, int nbins, DevStatus* st,
                                                      int stats, const int4* __restrict__ clip_tris,
-                                                     unsigned clip_cap) {
+                                                     unsigned clip_cap, uint2* __restrict__ heavy,
+                                                     unsigned heavy_cap, unsigned heavy_epoch) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   // the vertex stage does not touch the status word, and everything before
   // it has completed (it is launched without the early-start attribute)
-  if (blockIdx.x == 0 && threadIdx.x == 0) st->scan_ticket = 0u;  // the scan runs after this kernel
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->scan_ticket = 0u;  // the scan runs after this kernel
+    // the other parity's heavy counter is the next count pass's: nothing reads it until then
+    st->heavy_n[(heavy_epoch + 1u) & 1u] = 0u;
+  }
+  unsigned* heavy_n = &st->heavy_n[heavy_epoch & 1u];
   pdl_wait();  // snapped vertices
   pdl_launch_dependents();
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -348,7 +508,7 @@ __global__ void __launch_bounds__(256) k_setup_count(RasterGeom g, int T, const 
       va.p0 = c[0]; va.p1 = c[1]; va.p2 = c[2];
       va.in_range = true;
     }
-    count_batch(g, TT, t, ia, va, rect, cnt, nbins, st, stats, lane, lt_mask);
+    count_batch<EXACT>(g, TT, t, ia, va, rect, cnt, nbins, st, stats, lane, lt_mask, heavy, heavy_cap, heavy_n);
   }
 }
 
@@ -365,15 +525,17 @@ static int resident_per_sm(K kernel, int threads) {
 
 void launch_setup_count(const RasterGeom& g, int T, const int* tris, int V, const int4* vtx, BinRect* rect,
                         unsigned* bin_count, DevStatus* st, int stats, int num_sms, cudaStream_t s,
-                        const int4* clip_tris, unsigned clip_cap) {
-  static const int per_sm = resident_per_sm(k_setup_count, 256);
+                        const int4* clip_tris, unsigned clip_cap, int exact, uint2* heavy, unsigned heavy_cap,
+                        unsigned heavy_epoch) {
+  static const int per_sm = resident_per_sm(k_setup_count<false>, 256);
   const long long TT = (long long)T + (clip_tris ? clip_cap : 0u);
   int warps = (int)((TT + 31) / 32);
   int blocks = (warps + 7) / 8;
   blocks = blocks < num_sms * per_sm ? blocks : num_sms * per_sm;
   if (blocks < 1) blocks = 1;  // with no triangles the kernel still resets the scan ticket
-  launch_pdl(k_setup_count, blocks, 256, 0, s, g, T, tris, V, vtx, rect, bin_count, g.nbx * g.nby, st, stats,
-             clip_tris, clip_cap);
+  launch_pdl(exact ? k_setup_count<true> : k_setup_count<false>, blocks, 256, 0, s, g, T, tris, V, vtx, rect,
+             bin_count, g.nbx * g.nby, st, stats, clip_tris, clip_cap, heavy_cap ? heavy : nullptr, heavy_cap,
+             heavy_epoch);
 }
 
 void launch_scan(int nbins, unsigned* bin_count, unsigned* bin_off, unsigned* cursor, unsigned long long capacity,
@@ -389,17 +551,21 @@ void launch_scan(int nbins, unsigned* bin_count, unsigned* bin_off, unsigned* cu
 // after the bin's single-bin part, spread over the warp.
 // ======================================================================
 // Scatter work for one batch of 32 triangles whose rectangles are loaded.
+// EXACT: multi-bin pairs pass the count pass's overlap test; ot is the
+// lane's triangle (read only for a multi-bin rectangle).
+template <bool EXACT>
 __device__ __forceinline__ void scatter_batch(const RasterGeom& g, int base, BinRect r, unsigned pos_single,
                                               unsigned* __restrict__ cursor, unsigned* __restrict__ bin_tris,
-                                              unsigned long long capacity, int lane) {
+                                              unsigned long long capacity, int lane, const OverlapTri& ot) {
   const bool culled = r.lo == RECT_CULLED;
   const bool single = !culled && (r.lo & RECT_SINGLE);
   // positions are below the scanned total, which is at most the capacity;
   // the bound only guards against inconsistent offsets
   if (single && pos_single < capacity) bin_tris[pos_single] = (unsigned)(base + lane);
-  const int bx0 = r.lo & 0xFFFF, by0 = r.lo >> 16, bx1 = r.hi & 0xFFFF, by1 = r.hi >> 16;
+  const int bx0 = r.lo & 0xFFFF, by0 = r.lo >> 16, bx1 = r.hi & 0xFFFF, by1 = (r.hi >> 16) & 0x7FFF;
   const int bw = bx1 - bx0 + 1;
-  const int nb = (!culled && !single) ? bw * (by1 - by0 + 1) : 0;
+  // a listed heavy triangle's entries are written from the heavy list
+  const int nb = (!culled && !single && !(r.hi & RECT_HEAVY)) ? bw * (by1 - by0 + 1) : 0;
   const MultiSpan m = warp_prefix(nb, lane);
   for (int k0 = 0; k0 < m.total; k0 += 32) {
     const int k = k0 + lane;
@@ -407,11 +573,38 @@ __device__ __forceinline__ void scatter_batch(const RasterGeom& g, int base, Bin
     const int ox = __shfl_sync(FULL_MASK, bx0, owner), oy = __shfl_sync(FULL_MASK, by0, owner);
     const int obw = __shfl_sync(FULL_MASK, bw, owner);
     const int first = __shfl_sync(FULL_MASK, m.incl - nb, owner);
-    if (k < m.total) {
+    bool keep = k < m.total;
+    if (EXACT) {
+      const OverlapTri o = shfl_overlap(ot, owner);
+      int bx, by;
+      pair_xy(k, first, ox, oy, obw, bx, by);
+      keep = keep && overlaps_bin(g, o, bx, by);
+    }
+    if (keep) {
       const unsigned pos = atomicAdd(cursor + pair_bin(g, k, first, ox, oy, obw), 1u);
       if (pos < capacity) bin_tris[pos] = (unsigned)(base + owner);
     }
   }
+}
+
+// The vertices of triangle t for the exact test in the scatter pass (only
+// for a multi-bin rectangle: everything else needs none).
+__device__ __forceinline__ OverlapTri scatter_overlap(const RasterGeom& g, int T, int t, BinRect r,
+                                                      const int* __restrict__ tris, int V,
+                                                      const int4* __restrict__ vtx, const int4* __restrict__ clip_tris) {
+  OverlapTri o = {};
+  if (r.lo == RECT_CULLED || (r.lo & RECT_SINGLE) || (r.hi & RECT_HEAVY)) return o;
+  int4 p0, p1, p2;
+  if (t < T) {
+    const int3 i = load_tri(tris, T, t);
+    // a multi-bin rectangle was only written for indices the count pass found in range
+    if ((unsigned)i.x >= (unsigned)V || (unsigned)i.y >= (unsigned)V || (unsigned)i.z >= (unsigned)V) return o;
+    p0 = __ldg(vtx + i.x); p1 = __ldg(vtx + i.y); p2 = __ldg(vtx + i.z);
+  } else {
+    const int4* c = clip_tris + 3 * (size_t)(t - T);
+    p0 = c[0]; p1 = c[1]; p2 = c[2];
+  }
+  return overlap_tri(g, p0, p1, p2);
 }
 
 // Offset of a single-bin triangle's entry: off[bin] + its slot (0 otherwise).
@@ -421,15 +614,24 @@ __device__ __forceinline__ unsigned single_pos(const RasterGeom& g, BinRect r, c
   return __ldg(bin_off + bin) + r.hi;
 }
 
-__global__ void __launch_bounds__(256) k_scatter(RasterGeom g, int T, const BinRect* __restrict__ rect,
+// eight CTAs of 256 threads per SM (32 registers); the exact test's
+// instance keeps its vertices in registers (four CTAs)
+template <bool EXACT>
+__global__ void __launch_bounds__(256, EXACT ? 4 : 8) k_scatter(RasterGeom g, int T, const BinRect* __restrict__ rect,
                                                  const unsigned* __restrict__ bin_off,
                                                  unsigned* __restrict__ cursor, unsigned* __restrict__ bin_tris,
                                                  unsigned long long capacity, const DevStatus* st,
-                                                 const int4* __restrict__ clip_tris, unsigned clip_cap) {
+                                                 const int4* __restrict__ clip_tris, unsigned clip_cap,
+                                                 const int* __restrict__ tris, int V, const int4* __restrict__ vtx,
+                                                 const uint2* __restrict__ heavy, unsigned heavy_cap,
+                                                 unsigned heavy_epoch) {
   pdl_wait();  // offsets, cursors and the status of the scan
   pdl_launch_dependents();
   if (st->flags & STATUS_SKIP_MASK) return;
+  const int T_in = T;
   T = frame_triangles(T, clip_tris, clip_cap, st);
+  // the heavy list's length is loaded now and used after the per-warp work
+  const unsigned nheavy = heavy ? heavy_count(st, heavy_epoch, heavy_cap) : 0u;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int step = gridDim.x * (blockDim.x >> 5) * 32;
   BinRect none;
@@ -441,22 +643,45 @@ __global__ void __launch_bounds__(256) k_scatter(RasterGeom g, int T, const BinR
     const BinRect ra = base + lane < T ? rect[base + lane] : none;
     const BinRect rb = hasB && baseB + lane < T ? rect[baseB + lane] : none;
     const unsigned pa = single_pos(g, ra, bin_off), pb = single_pos(g, rb, bin_off);
-    scatter_batch(g, base, ra, pa, cursor, bin_tris, capacity, lane);
-    if (hasB) scatter_batch(g, baseB, rb, pb, cursor, bin_tris, capacity, lane);
+    OverlapTri oa = {}, ob = {};
+    if (EXACT) {
+      oa = scatter_overlap(g, T_in, base + lane, ra, tris, V, vtx, clip_tris);
+      ob = scatter_overlap(g, T_in, baseB + lane, rb, tris, V, vtx, clip_tris);
+    }
+    scatter_batch<EXACT>(g, base, ra, pa, cursor, bin_tris, capacity, lane, oa);
+    if (hasB) scatter_batch<EXACT>(g, baseB, rb, pb, cursor, bin_tris, capacity, lane, ob);
+  }
+  // the heavy list's chunks, one per CTA step, a pair per thread
+  for (unsigned e = blockIdx.x; e < nheavy; e += gridDim.x) {
+    const uint2 h = heavy[e];
+    if (h.x == HEAVY_NONE || threadIdx.x >= HEAVY_CHUNK) continue;
+    const int k = (int)h.y * HEAVY_CHUNK + (int)threadIdx.x;
+    int bx, by, nb;
+    rect_pair(rect[h.x], k, bx, by, nb);
+    if (k >= nb) continue;
+    if (EXACT) {
+      int4 p0, p1, p2;
+      bool ok;
+      tri_points(T_in, (int)h.x, tris, V, vtx, clip_tris, p0, p1, p2, ok);
+      if (!ok || !overlaps_bin(g, overlap_tri(g, p0, p1, p2), bx, by)) continue;
+    }
+    const unsigned pos = atomicAdd(cursor + by * g.nbx + bx, 1u);
+    if (pos < capacity) bin_tris[pos] = h.x;
   }
 }
 
 void launch_scatter(const RasterGeom& g, int T, const BinRect* rect, const unsigned* bin_off, unsigned* cursor,
                     unsigned* bin_tris, unsigned long long capacity, DevStatus* st, int num_sms, cudaStream_t s,
-                    const int4* clip_tris, unsigned clip_cap) {
+                    const int4* clip_tris, unsigned clip_cap, const int* tris, int V, const int4* vtx,
+                    const uint2* heavy, unsigned heavy_cap, unsigned heavy_epoch) {
   const long long TT = (long long)T + (clip_tris ? clip_cap : 0u);
   if (TT <= 0) return;
-  static const int per_sm = resident_per_sm(k_scatter, 256);
+  static const int per_sm = resident_per_sm(k_scatter<false>, 256);
   int warps = (int)((TT + 31) / 32);
   int blocks = (warps + 7) / 8;
   blocks = blocks < num_sms * per_sm ? blocks : num_sms * per_sm;
-  launch_pdl(k_scatter, blocks, 256, 0, s, g, T, rect, bin_off, cursor, bin_tris, capacity, st, clip_tris,
-             clip_cap);
+  launch_pdl(tris ? k_scatter<true> : k_scatter<false>, blocks, 256, 0, s, g, T, rect, bin_off, cursor, bin_tris,
+             capacity, st, clip_tris, clip_cap, tris, V, vtx, heavy_cap ? heavy : nullptr, heavy_cap, heavy_epoch);
 }
 
 }  // namespace piko

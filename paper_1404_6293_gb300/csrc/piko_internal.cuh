@@ -57,6 +57,7 @@ struct DevStatus {
   unsigned long long frags;     // covered samples
   unsigned long long shaded;    // covered pixels after the depth test
   unsigned long long binned;    // triangles that reached at least one bin
+  unsigned int heavy_n[2];      // chunks in the heavy-triangle list of AssignBin, by count-pass parity
 };
 
 // Screen and bin geometry of one framebuffer.
@@ -375,9 +376,20 @@ void launch_vertex(int W, int H, int V, const float* pos, const float* mvp, int4
 // can hold; above it PIKO_ERR_OVERFLOW is recorded).
 // With clipping, clip_tris / clip_cap describe the sub-triangle list of the
 // clip pass (triangles T.. of the frame); otherwise NULL / 0.
+// exact: multi-bin triangles get entries only in bins they overlap
+// (PIKO_OPT_EXACT_BINS); the scatter pass then needs tris / V / vtx.
+// Chunks a handle's heavy-triangle list holds (4M (triangle, bin) pairs).
+constexpr unsigned HEAVY_LIST_CAP = 16384;
+
+// heavy (optional, heavy_cap entries): triangles spanning many bins are
+// listed there in chunks of pairs, whose entries launch_scatter writes
+// spread over whole CTAs; heavy_epoch
+// must change between consecutive count passes of a handle (its parity
+// picks the list's counter; the pass clears the other one).
 void launch_setup_count(const RasterGeom& g, int T, const int* tris, int V, const int4* vtx,
                         BinRect* rect, unsigned* bin_count, DevStatus* st, int stats, int num_sms, cudaStream_t s,
-                        const int4* clip_tris = nullptr, unsigned clip_cap = 0);
+                        const int4* clip_tris = nullptr, unsigned clip_cap = 0, int exact = 0,
+                        uint2* heavy = nullptr, unsigned heavy_cap = 0, unsigned heavy_epoch = 0);
 // Near/far clipping of the triangles with a rejected vertex: sub-triangles
 // (3 snapped points each) and their triangle's index appended at
 // st->clip_count (PIKO_ERR_OVERFLOW past cap).
@@ -393,7 +405,9 @@ void launch_scan(int nbins, unsigned* bin_count, unsigned* bin_off, unsigned* cu
 int scan_chunks(int nbins);
 void launch_scatter(const RasterGeom& g, int T, const BinRect* rect, const unsigned* bin_off, unsigned* cursor,
                     unsigned* bin_tris, unsigned long long capacity, DevStatus* st, int num_sms, cudaStream_t s,
-                    const int4* clip_tris = nullptr, unsigned clip_cap = 0);
+                    const int4* clip_tris = nullptr, unsigned clip_cap = 0, const int* tris = nullptr, int V = 0,
+                    const int4* vtx = nullptr, const uint2* heavy = nullptr, unsigned heavy_cap = 0,
+                    unsigned heavy_epoch = 0);
 cudaError_t launch_process(const ProcessParams& p, int threads, int grid, cudaStream_t s);
 cudaError_t process_occupancy(const ProcessParams& p, int threads, int* blocks_per_sm);
 

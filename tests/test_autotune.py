@@ -55,7 +55,7 @@ def test_cached_entry_without_threads_uses_the_default(tmp_path):
     path = tmp_path / "tune.json"
     path.write_text(json.dumps({features(scene): {"bin": [16, 16], "schedule": "hardware", "ms": 1.0}}))
     tuner = Autotuner(cache_path=str(path))
-    assert tuner.knobs(scene) == {"bin": (16, 16), "schedule": "hardware", "threads": 128}
+    assert tuner.knobs(scene) == {"bin": (16, 16), "schedule": "hardware", "threads": 128, "exact_bins": 0}
     path.write_text(json.dumps({features(scene): {"bin": [32, 32], "schedule": "static", "threads": 512,
                                                   "ms": 1.0}}))
     assert Autotuner(cache_path=str(path)).knobs(scene)["threads"] == 512
@@ -82,9 +82,12 @@ def test_tuned_settings_are_valid_and_render_exactly():
     # every candidate was timed: bins x schedules x threads, plus the two other mappings
     trials = next(iter(tuner.cache.values()))["trials"]
     assert {t["schedule"] for t in trials} == set(DEFAULT_SCHEDULES + OTHER_MAPPINGS)
+    # the best binned candidate was also timed with exact bins
+    assert sum(1 for t in trials if t.get("exact_bins")) == 1
     # the tuned knobs render the scene exactly
     r1 = Rasterizer(host[0].width, host[0].height, bw, bh, sched)
     r1.set_option(L.PIKO_OPT_THREADS_PER_TILE, k["threads"])
+    r1.set_option(L.PIKO_OPT_EXACT_BINS, k["exact_bins"])
     fb1 = r1.forward(ds[0])
     torch.cuda.synchronize()
     assert r1.status()[0] == 0

@@ -1331,10 +1331,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--bins", type=int, default=16)
+    ap.add_argument("--bins", type=int, default=32,
+                    help="bin size of the heightfield line (32: the fastest of the bin-size x schedule sweep)")
     ap.add_argument("--schedule", default="hardware", choices=["static", "dynamic", "hardware", "fused", "unfused"],
-                    help="tile schedule of the heightfield line (hardware: one CTA per tile, the fastest "
-                         "of the bin-size x schedule sweep at 16x16)")
+                    help="tile schedule of the heightfield line (hardware: one CTA per tile)")
     ap.add_argument("--threads", type=int, default=0, help="Process CTA size (0: library default)")
     ap.add_argument("--perspective", action="store_true",
                     help="heightfield and sphere workloads: perspective-correct attributes (PIKO_OPT_PERSPECTIVE)")

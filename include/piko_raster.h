@@ -139,7 +139,10 @@ extern "C" {
                                        tiles).  Bit 1: in a persistent batch, CTA 0 does not
                                        arrive at the first grid barrier, so every CTA's wait
                                        runs out.  The frame then reports PIKO_ERR_TIMEOUT
-                                       and writes no output.  Default 0                    */
+                                       and writes no output.  Bit 2: the list of heavy
+                                       triangles (spanning 256 bins or more) counts as full,
+                                       so their bin entries are written by their own warps;
+                                       same output.  Default 0                             */
 
 /* Stage boundaries of one forward pass, for piko_raster_set_stage_events. */
 #define PIKO_NUM_STAGE_EVENTS 6 /* before vertex, after vertex, after setup+count, after scan,

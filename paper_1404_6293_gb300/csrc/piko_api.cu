@@ -5,6 +5,7 @@
 #include <string>
 
 #include "piko_internal.cuh"
+#include "piko_scan.cuh"
 
 using namespace piko;
 
@@ -224,6 +225,10 @@ const char* piko_raster_last_error(const piko_raster* h) {
   return h->err.c_str();
 }
 
+// Chunks the heavy-triangle list may hold: none under test hook bit 2, so
+// that every heavy triangle takes the path of a full list.
+static unsigned heavy_cap(const piko_raster* h) { return (h->withhold & TEST_WITHHOLD_HEAVY) ? 0u : HEAVY_LIST_CAP; }
+
 int piko_raster_set_option(piko_raster* h, int key, int value) {
   if (!h) return PIKO_ERR_INVALID_ARG;
   switch (key) {
@@ -270,7 +275,7 @@ int piko_raster_set_option(piko_raster* h, int key, int value) {
       h->wait_budget = (long long)value * 1000;
       return PIKO_OK;
     case PIKO_OPT_TEST_WITHHOLD:
-      if (value < 0 || value > 3) return fail(h, PIKO_ERR_INVALID_ARG, "withhold must be 0..3");
+      if (value < 0 || value > 7) return fail(h, PIKO_ERR_INVALID_ARG, "withhold must be 0..7");
       h->withhold = value;
       return PIKO_OK;
     case PIKO_OPT_SMALL_TRI_PIXELS:
@@ -485,7 +490,7 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
   for (int attempt = 0;; ++attempt) {
     if (h->stats && attempt > 0) cudaMemsetAsync(&h->status->binned, 0, sizeof(unsigned long long), st);
     launch_setup_count(h->g, T, s->tris, V, h->vtx, h->rect, h->bin_count, h->status, h->stats, h->num_sms, st,
-                       clip_tris, clip_cap, h->exact_bins, h->heavy, HEAVY_LIST_CAP, ++h->heavy_epoch);
+                       clip_tris, clip_cap, h->exact_bins, h->heavy, heavy_cap(h), ++h->heavy_epoch);
     if (ev) cudaEventRecord(h->stage_ev[2], st);
     launch_scan(h->nbins, h->bin_count, h->bin_off, h->cursor, (unsigned long long)h->ecap, h->status,
                 h->chunk_state, ++h->scan_epoch, st, h->wait_budget, h->withhold);
@@ -505,7 +510,7 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
   }
   launch_scatter(h->g, T, h->rect, h->bin_off, h->cursor, h->bin_tris, (unsigned long long)h->ecap, h->status,
                  h->num_sms, st, clip_tris, clip_cap, h->exact_bins ? s->tris : nullptr, V, h->vtx, h->heavy,
-                 HEAVY_LIST_CAP, h->heavy_epoch);
+                 heavy_cap(h), h->heavy_epoch);
   if (ev) cudaEventRecord(h->stage_ev[4], st);
 
   ProcessParams p;

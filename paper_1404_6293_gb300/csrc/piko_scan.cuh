@@ -35,6 +35,7 @@ constexpr long long WAIT_BUDGET_CYCLES = 40000000;  // ~20 ms at 2 GHz
 // test hooks (bits of the `withhold` argument)
 constexpr int TEST_WITHHOLD_SCAN = 1;     // scan chunk 0 does not publish its state
 constexpr int TEST_WITHHOLD_BARRIER = 2;  // batch CTA 0 does not arrive at the first grid barrier
+constexpr int TEST_WITHHOLD_HEAVY = 4;    // the heavy-triangle list of AssignBin counts as full
 
 struct ScanSmem {
   unsigned long long warp_sums[32];

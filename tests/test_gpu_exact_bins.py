@@ -172,3 +172,23 @@ def test_exact_bins_with_near_far_clipping():
         _keys_equal(key0, ref, f"clipping {sched}")
         _keys_equal(key1, ref, f"clipping + exact bins {sched}")
         assert e1 <= e0
+
+
+@pytest.mark.parametrize("exact", [0, 1])
+def test_heavy_triangles_without_the_list(exact):
+    """Triangles spanning 256 bins or more are listed for the scatter pass;
+    with the list treated as full (test hook bit 2) their entries are
+    written by their own warps instead.  Same keys and entry counts either
+    way, and equal to the oracle."""
+    from paper_1404_6293_gb300 import _lib as L
+    s = S.random_triangles(400, 300, 150, 160.0, seed=17)
+    ref, _ = oracle.raster_bbox(s, threads=4)
+    out = []
+    for hook in (0, 4):
+        for sched in ("static", "hardware"):
+            key, _, e = _render(s, (8, 8), sched, exact, {L.PIKO_OPT_TEST_WITHHOLD: hook})
+            _keys_equal(key, ref, f"heavy list hook={hook} {sched} exact={exact}")
+            out.append(e)
+    assert len(set(out)) == 1
+    if exact:
+        assert out[0] == _model_entries(s, 8, 8)

@@ -257,7 +257,7 @@ def workload(args):
     scene = S.heightfield()
     cfg = {"workload": "heightfield 1920x1080, 1000x500 quads (1,000,000 triangles), Lambert",
            "width": scene.width, "height": scene.height, "triangles": scene.num_triangles,
-           "vertices": scene.num_vertices, "bin": [args.bins, args.bins], "schedule": args.schedule,
+           "vertices": scene.num_vertices, "bin": [args.bins, args.bin_h or args.bins], "schedule": args.schedule,
            "l2": "flushed between steps (256 MiB write outside the per-step events)"}
     return scene, cfg
 
@@ -445,7 +445,7 @@ def time_forward(ctx, r, ds, fb, K, W, stages=True):
     return step_ms, stage_ms
 
 
-def exact_bins_record(ctx, scene, ds, bins, schedule, K, W, threads=0) -> dict:
+def exact_bins_record(ctx, scene, ds, bins, schedule, K, W, threads=0, bin_h=0) -> dict:
     """The same forward with AssignBin's exact overlap test on (a handle of
     its own): per-step and per-stage times and bin entries, beside the
     bounding-box binning of the line."""
@@ -454,7 +454,7 @@ def exact_bins_record(ctx, scene, ds, bins, schedule, K, W, threads=0) -> dict:
     from paper_1404_6293_gb300.raster import Framebuffer, Rasterizer
     rec = {}
     for exact in (0, 1):
-        r = Rasterizer(scene.width, scene.height, bins, bins, schedule)
+        r = Rasterizer(scene.width, scene.height, bins, bin_h or bins, schedule)
         if threads:
             r.set_option(L.PIKO_OPT_THREADS_PER_TILE, threads)
         r.set_option(L.PIKO_OPT_EXACT_BINS, exact)
@@ -525,6 +525,8 @@ def headline_traffic(args):
     try:
         with open(PROFILE_TRAFFIC) as f:
             prof = json.load(f)
+        if args.bin_h and args.bin_h != args.bins:
+            return None  # the record is for square bins
         bin_px = args.bins * args.bins
         launch = {"bins": args.bins, "schedule": args.schedule,
                   "threads": args.threads or (64 if bin_px <= 64 else (128 if bin_px <= 256 else 256)),
@@ -569,10 +571,11 @@ def run_ours(args):
         n_trials = len(next(iter(tuner.cache.values()))["trials"])
         tuner.close()
         args.bins, args.schedule, args.threads = knobs["bin"][0], knobs["schedule"], knobs["threads"]
+        args.bin_h = knobs["bin"][1]
         args.exact_bins = knobs["exact_bins"]
         cfg.update({"bin": list(knobs["bin"]), "schedule": args.schedule,
                     "knobs": f"autotuned: fastest forward of {n_trials} candidates ({tune_s:.1f} s, untimed)"})
-    r = Rasterizer(scene.width, scene.height, args.bins, args.bins, args.schedule)
+    r = Rasterizer(scene.width, scene.height, args.bins, args.bin_h or args.bins, args.schedule)
     if args.threads:
         r.set_option(L.PIKO_OPT_THREADS_PER_TILE, args.threads)
         cfg["threads_per_tile"] = args.threads
@@ -647,7 +650,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_configs:
         line["bin_sweep"] = bin_sweep(args, ctx, scene, ds)
         line["exact_bins"] = exact_bins_record(ctx, scene, ds, args.bins, args.schedule, K, args.warmup,
-                                               args.threads)
+                                               args.threads, args.bin_h)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene, args.cpu_seconds, args.perspective)
     if rank == 0 and world == 1 and not args.no_configs:
@@ -710,7 +713,7 @@ def measure_e2e(args, ctx, r, ds, fb, scene, world, dist, barrier) -> dict:
     nl = max(2, args.e2e_lanes)
     lanes = [(r, fb_h, ds, fb)]
     for _ in range(nl - 1):
-        rr = Rasterizer(scene.width, scene.height, args.bins, args.bins, args.schedule)
+        rr = Rasterizer(scene.width, scene.height, args.bins, args.bin_h or args.bins, args.schedule)
         if args.threads:
             rr.set_option(L.PIKO_OPT_THREADS_PER_TILE, args.threads)
         if args.perspective:
@@ -1333,6 +1336,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--bins", type=int, default=32,
                     help="bin size of the heightfield line (32: the fastest of the bin-size x schedule sweep)")
+    ap.add_argument("--bin-h", type=int, default=0, help="bin height of the heightfield line (0: square bins)")
     ap.add_argument("--schedule", default="hardware", choices=["static", "dynamic", "hardware", "fused", "unfused"],
                     help="tile schedule of the heightfield line (hardware: one CTA per tile)")
     ap.add_argument("--threads", type=int, default=0, help="Process CTA size (0: library default)")

@@ -8,9 +8,11 @@
 //
 // Per tile:
 //  1. each thread takes one bin entry, re-derives the triangle from the
-//     snapped vertices, stores what shading needs (edge coordinates, 1/A and
-//     the vertex attributes) in a shared-memory record, and rasterizes it if
-//     its box inside the tile is small; larger ones go to a queue that whole
+//     snapped vertices and stores what shading needs (edge coordinates, 1/A
+//     and the vertex attributes) in a shared-memory record.  A small box
+//     inside the tile is walked by the thread for coverage only, and the
+//     warp then shares out the covered samples of all its small boxes for
+//     their depths (fragment_pass); larger boxes go to a queue that whole
 //     warps rasterize 32 pixels at a time with a coverage ballot;
 //  2. every covered sample does a 64-bit atomic minimum on the tile's key,
 //     key = depth << 40 | triangle << slot_bits | record slot: ordered by

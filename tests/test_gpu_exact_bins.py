@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
+from binning_model import exact_bin_entries
 from paper_1404_6293_gb300 import scenes as S
 
 pytestmark = pytest.mark.gpu
@@ -43,47 +44,7 @@ def _keys_equal(got, ref, what):
 
 
 def _model_entries(scene, bw, bh):
-    """Bin entries of the exact test, counted from the oracle's snapped
-    vertices with Python integers: bounding-box bins of each triangle, then,
-    for a triangle spanning several, only the bins where each edge's largest
-    value over the bin's centres inside the box passes the fill rule."""
-    X, Y, _, ok = oracle.vertex_stage(scene)
-    W, H = scene.width, scene.height
-    total = 0
-    for a, b, c in scene.tris.tolist():
-        if not (ok[a] and ok[b] and ok[c]):
-            continue
-        P = [(int(X[i]), int(Y[i])) for i in (a, b, c)]
-        A = (P[1][0] - P[0][0]) * (P[2][1] - P[0][1]) - (P[2][0] - P[0][0]) * (P[1][1] - P[0][1])
-        if A == 0:
-            continue
-        if A < 0:
-            P[1], P[2] = P[2], P[1]
-        xs, ys = [p[0] for p in P], [p[1] for p in P]
-        px0, px1 = max(-((128 - min(xs)) // 256), 0), min((max(xs) - 128) // 256, W - 1)
-        py0, py1 = max(-((128 - min(ys)) // 256), 0), min((max(ys) - 128) // 256, H - 1)
-        if px0 > px1 or py0 > py1:
-            continue
-        bx0, bx1, by0, by1 = px0 // bw, px1 // bw, py0 // bh, py1 // bh
-        if bx0 == bx1 and by0 == by1:
-            total += 1
-            continue
-        edges = [(P[1], P[2]), (P[2], P[0]), (P[0], P[1])]
-        for by in range(by0, by1 + 1):
-            for bx in range(bx0, bx1 + 1):
-                x0, x1 = max(bx * bw, px0), min(bx * bw + bw - 1, px1)
-                y0, y1 = max(by * bh, py0), min(by * bh + bh - 1, py1)
-                keep = True
-                for (xa, ya), (xb, yb) in edges:
-                    dx, dy = xb - xa, yb - ya
-                    top_left = dy < 0 or (dy == 0 and dx > 0)
-                    px = 256 * (x1 if dy < 0 else x0) + 128
-                    py = 256 * (y1 if dx > 0 else y0) + 128
-                    if dx * (py - ya) - dy * (px - xa) - (0 if top_left else 1) < 0:
-                        keep = False
-                        break
-                total += keep
-    return total
+    return exact_bin_entries(scene, bw, bh)
 
 
 def _thin_scene(W, H, T, seed):

@@ -489,12 +489,22 @@ int piko_raster_forward(piko_raster* h, const piko_scene* s, piko_framebuffer* f
     return forward_other_mapping(h, s, fb, st, ev);
   for (int attempt = 0;; ++attempt) {
     if (h->stats && attempt > 0) cudaMemsetAsync(&h->status->binned, 0, sizeof(unsigned long long), st);
-    launch_setup_count(h->g, T, s->tris, V, h->vtx, h->rect, h->bin_count, h->status, h->stats, h->num_sms, st,
-                       clip_tris, clip_cap, h->exact_bins, h->heavy, heavy_cap(h), ++h->heavy_epoch);
-    if (ev) cudaEventRecord(h->stage_ev[2], st);
-    launch_scan(h->nbins, h->bin_count, h->bin_off, h->cursor, (unsigned long long)h->ecap, h->status,
-                h->chunk_state, ++h->scan_epoch, st, h->wait_budget, h->withhold);
-    if (ev) cudaEventRecord(h->stage_ev[3], st);
+    // a frame of one scan chunk of bins is scanned by the count pass's last
+    // CTA (one launch fewer on the chain); larger frames take the scan kernel
+    // (with stage events on, the count and scan launches stay apart)
+    const unsigned heavy_epoch = ++h->heavy_epoch, scan_epoch = ++h->scan_epoch;
+    const bool fused = !ev && launch_count_and_scan(h->g, T, s->tris, V, h->vtx, h->rect, h->bin_count, h->status,
+                                                    h->stats, h->num_sms, st, clip_tris, clip_cap, h->exact_bins,
+                                                    h->heavy, heavy_cap(h), heavy_epoch, h->bin_off, h->cursor,
+                                                    (unsigned long long)h->ecap, h->chunk_state, scan_epoch);
+    if (!fused) {
+      launch_setup_count(h->g, T, s->tris, V, h->vtx, h->rect, h->bin_count, h->status, h->stats, h->num_sms, st,
+                         clip_tris, clip_cap, h->exact_bins, h->heavy, heavy_cap(h), heavy_epoch);
+      if (ev) cudaEventRecord(h->stage_ev[2], st);
+      launch_scan(h->nbins, h->bin_count, h->bin_off, h->cursor, (unsigned long long)h->ecap, h->status,
+                  h->chunk_state, scan_epoch, st, h->wait_budget, h->withhold);
+      if (ev) cudaEventRecord(h->stage_ev[3], st);
+    }
     if (!h->check_capacity) break;
     cudaError_t e = cudaMemcpyAsync(h->h_needed, &h->status->needed, sizeof(unsigned long long),
                                     cudaMemcpyDeviceToHost, st);

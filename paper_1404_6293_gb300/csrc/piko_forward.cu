@@ -474,13 +474,27 @@ __device__ __forceinline__ void count_batch(const RasterGeom& g, int T, int t, i
   }
 }
 
-template <bool EXACT>
-__global__ void __launch_bounds__(256) k_setup_count(RasterGeom g, int T, const int* __restrict__ tris, int V,
+// Scan of a frame of one scan chunk, fused into the count pass (SCAN): the
+// count pass's last CTA to finish (each CTA counts itself out after a fence
+// that makes its count atomics visible) scans the counts.  No CTA waits for
+// another.
+struct FusedScan {
+  unsigned* bin_off;
+  unsigned* cursor;
+  unsigned long long capacity;
+  unsigned long long* chunk_state;
+  unsigned epoch;
+};
+
+// eight CTAs of 256 threads per SM (32 registers) for the default binning,
+// four (64 registers) with the exact overlap test
+template <bool EXACT, bool SCAN = false>
+__global__ void __launch_bounds__(256, EXACT ? 4 : 8) k_setup_count(RasterGeom g, int T, const int* __restrict__ tris, int V,
                                                      const int4* __restrict__ vtx, BinRect* __restrict__ rect,
                                                      unsigned* __restrict__ cnt, int nbins, DevStatus* st,
                                                      int stats, const int4* __restrict__ clip_tris,
                                                      unsigned clip_cap, uint2* __restrict__ heavy,
-                                                     unsigned heavy_cap, unsigned heavy_epoch) {
+                                                     unsigned heavy_cap, unsigned heavy_epoch, FusedScan fs) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   // the vertex stage does not touch the status word, and everything before
   // it has completed (it is launched without the early-start attribute)
@@ -510,6 +524,20 @@ __global__ void __launch_bounds__(256) k_setup_count(RasterGeom g, int T, const 
     }
     count_batch<EXACT>(g, TT, t, ia, va, rect, cnt, nbins, st, stats, lane, lt_mask, heavy, heavy_cap, heavy_n);
   }
+  if (SCAN) {
+    __shared__ ScanSmem scan_sm;
+    __shared__ int s_last;
+    __threadfence();  // this thread's count atomics, before the CTA counts itself out
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&st->count_done, 1u) == gridDim.x - 1u;
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      if (threadIdx.x == 0) st->count_done = 0u;  // for the next frame
+      scan_chunk(0, 1, nbins, cnt, fs.bin_off, fs.cursor, fs.capacity, st, fs.chunk_state, fs.epoch, scan_sm,
+                 &st->queue_head);
+    }
+  }
 }
 
 // Resident CTAs per SM of a kernel (one wave of a persistent grid).
@@ -535,7 +563,33 @@ void launch_setup_count(const RasterGeom& g, int T, const int* tris, int V, cons
   if (blocks < 1) blocks = 1;  // with no triangles the kernel still resets the scan ticket
   launch_pdl(exact ? k_setup_count<true> : k_setup_count<false>, blocks, 256, 0, s, g, T, tris, V, vtx, rect,
              bin_count, g.nbx * g.nby, st, stats, clip_tris, clip_cap, heavy_cap ? heavy : nullptr, heavy_cap,
-             heavy_epoch);
+             heavy_epoch, FusedScan{});
+}
+
+bool launch_count_and_scan(const RasterGeom& g, int T, const int* tris, int V, const int4* vtx, BinRect* rect,
+                           unsigned* bin_count, DevStatus* st, int stats, int num_sms, cudaStream_t s,
+                           const int4* clip_tris, unsigned clip_cap, int exact, uint2* heavy, unsigned heavy_cap,
+                           unsigned heavy_epoch, unsigned* bin_off, unsigned* cursor, unsigned long long capacity,
+                           unsigned long long* chunk_state, unsigned scan_epoch) {
+  const int nbins = g.nbx * g.nby;
+  // one chunk of the count pass's 256 threads x SCAN_PER bins
+  if (nbins > 256 * SCAN_PER) return false;
+  static const int per_sm = resident_per_sm(k_setup_count<false, true>, 256);
+  const long long TT = (long long)T + (clip_tris ? clip_cap : 0u);
+  int warps = (int)((TT + 31) / 32);
+  int blocks = (warps + 7) / 8;
+  blocks = blocks < num_sms * per_sm ? blocks : num_sms * per_sm;
+  if (blocks < 1) blocks = 1;  // with no triangles the one CTA still scans (all counts zero)
+  FusedScan fs;
+  fs.bin_off = bin_off;
+  fs.cursor = cursor;
+  fs.capacity = capacity;
+  fs.chunk_state = chunk_state;
+  fs.epoch = scan_epoch;
+  launch_pdl(exact ? k_setup_count<true, true> : k_setup_count<false, true>, blocks, 256, 0, s, g, T, tris, V, vtx,
+             rect, bin_count, nbins, st, stats, clip_tris, clip_cap, heavy_cap ? heavy : nullptr, heavy_cap,
+             heavy_epoch, fs);
+  return true;
 }
 
 void launch_scan(int nbins, unsigned* bin_count, unsigned* bin_off, unsigned* cursor, unsigned long long capacity,

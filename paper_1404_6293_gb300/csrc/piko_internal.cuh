@@ -58,6 +58,7 @@ struct DevStatus {
   unsigned long long shaded;    // covered pixels after the depth test
   unsigned long long binned;    // triangles that reached at least one bin
   unsigned int heavy_n[2];      // chunks in the heavy-triangle list of AssignBin, by count-pass parity
+  unsigned int count_done;      // count-pass CTAs finished (its last CTA scans small frames; then 0 again)
 };
 
 // Screen and bin geometry of one framebuffer.
@@ -390,6 +391,15 @@ void launch_setup_count(const RasterGeom& g, int T, const int* tris, int V, cons
                         BinRect* rect, unsigned* bin_count, DevStatus* st, int stats, int num_sms, cudaStream_t s,
                         const int4* clip_tris = nullptr, unsigned clip_cap = 0, int exact = 0,
                         uint2* heavy = nullptr, unsigned heavy_cap = 0, unsigned heavy_epoch = 0);
+// Count pass and scan in one launch for a frame of at most one scan chunk of
+// bins (scan_chunks(nbins) == 1): the count pass's last CTA scans.  Returns
+// false (nothing launched) for larger frames, which take launch_setup_count
+// and launch_scan.
+bool launch_count_and_scan(const RasterGeom& g, int T, const int* tris, int V, const int4* vtx, BinRect* rect,
+                           unsigned* bin_count, DevStatus* st, int stats, int num_sms, cudaStream_t s,
+                           const int4* clip_tris, unsigned clip_cap, int exact, uint2* heavy, unsigned heavy_cap,
+                           unsigned heavy_epoch, unsigned* bin_off, unsigned* cursor, unsigned long long capacity,
+                           unsigned long long* chunk_state, unsigned scan_epoch);
 // Near/far clipping of the triangles with a rejected vertex: sub-triangles
 // (3 snapped points each) and their triangle's index appended at
 // st->clip_count (PIKO_ERR_OVERFLOW past cap).

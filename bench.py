@@ -445,6 +445,14 @@ def time_forward(ctx, r, ds, fb, K, W, stages=True):
     return step_ms, stage_ms
 
 
+def forward_launches(W: int, H: int, bw: int, bh: int) -> int:
+    """The library's kernels per single-scene forward without stage events:
+    vertex, count, scan, scatter, Process; a frame of at most 2,048 bins is
+    scanned by the count pass itself (one launch fewer)."""
+    nbins = ((W + bw - 1) // bw) * ((H + bh - 1) // bh)
+    return 4 if nbins <= 2048 else 5
+
+
 def exact_bins_record(ctx, scene, ds, bins, schedule, K, W, threads=0, bin_h=0) -> dict:
     """The same forward with AssignBin's exact overlap test on (a handle of
     its own): per-step and per-stage times and bin entries, beside the
@@ -644,7 +652,7 @@ def run_ours(args):
             "wall_ms_incl_flush": 1e3 * wall / K,
             "step_ms_min": float(np.min(step_ms)), "step_ms_median": float(np.median(step_ms)),
             "roofline": roof, "clocks": clk, "e2e": e2e,
-            "gpu_launches": 5 * K,
+            "gpu_launches": forward_launches(scene.width, scene.height, args.bins, args.bin_h or args.bins) * K,
             "parity": "depth/ID bit-exact vs the CPU oracle on this workload under every schedule "
                       "(tests/test_gpu_full_size.py)"}
     if rank == 0 and world == 1 and not args.no_configs:
@@ -843,7 +851,8 @@ def measure_random256(args, ctx) -> dict:
            "stage_ms": {n: float(stage_ms[:, i].mean()) for i, n in
                         enumerate(["vertex", "setup_count", "scan", "scatter", "process"])},
            "work": {**stats, "covered_pixels": covered},
-           "roofline": process_roofline(ctx, scene, stats, proc_ms, clk), "clocks": clk, "gpu_launches": 5 * K,
+           "roofline": process_roofline(ctx, scene, stats, proc_ms, clk), "clocks": clk,
+           "gpu_launches": forward_launches(scene.width, scene.height, 16, 16) * K,
            "parity": "keys bit-exact, colour <= 1e-5 vs the oracle (tests/test_gpu_parity.py)"}
     if not args.no_cpu_baseline:
         import oracle
@@ -895,7 +904,7 @@ def measure_reyes(args, ctx) -> dict:
            "roofline": process_roofline(ctx, scene, stats, proc_ms, clk),
            "bins_16x16_hardware": {"ms_per_step": runs[(16, "hardware")][0],
                                    "value": scene.num_triangles / (runs[(16, "hardware")][0] * 1e-3) / 1e6},
-           "clocks": clk, "gpu_launches": 5 * K,
+           "clocks": clk, "gpu_launches": forward_launches(scene.width, scene.height, 32, 32) * K,
            "parity": "keys bit-exact, colour <= 1e-5 vs the oracle at this size (tests/test_gpu_reyes.py)"}
     if not args.no_cpu_baseline:
         rec["cpu_baseline"] = cpu_baseline(scene, args.config_cpu_seconds, single_seconds=2.0)
@@ -1279,7 +1288,7 @@ def measure_batch(args, ctx) -> dict:
                       "oracle": "every scene's keys bit-exact and colour <= 1e-5 vs the oracle "
                                 "(tests/test_gpu_full_size.py)"},
            "clocks": clk, "gpu_launches": (2 if args.batch_launch == "persistent" else 6) * args.steps,
-           "gpu_launches_plain": 7 * n * args.steps}
+           "gpu_launches_plain": sum(forward_launches(s.width, s.height, 16, 16) + 2 for s in host) * args.steps}
     if not args.no_cpu_baseline:
         import oracle
         hc = host_cpu()

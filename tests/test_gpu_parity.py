@@ -107,6 +107,39 @@ def test_thread_and_warp_raster_paths_agree(small_px, threads):
     assert_keys_equal(out["key"], ref, f"small_px={small_px} threads={threads}")
 
 
+@pytest.mark.parametrize("W,H,bins", [(256, 256, 16), (640, 480, 16), (1024, 512, 16), (1024, 528, 16), (200, 120, 8)])
+def test_count_pass_scan_matches_scan_kernel(W, H, bins):
+    """A frame of at most 2,048 bins is scanned by the count pass's last CTA;
+    with stage events on, the forward keeps the count and scan launches
+    apart.  Both give the same keys, colours and bin-entry total as the
+    oracle, frame after frame (the fused pass resets its CTA counter)."""
+    torch = _torch()
+    from paper_1404_6293_gb300 import _lib as L
+    from paper_1404_6293_gb300.raster import DeviceScene, Framebuffer, Rasterizer
+    s = S.random_triangles(W, H, 2000, 20.0, seed=W + H)
+    ref, _ = oracle.raster_bbox(s, threads=4)
+    rgba_ref = oracle.shade(s, ref)
+    r = Rasterizer(W, H, bins, bins, "hardware")
+    r.set_option(L.PIKO_OPT_STATS, 1)
+    ds = DeviceScene.from_host(s)
+    fb = Framebuffer.allocate(W, H, s.shade_mode)
+    entries = []
+    for step in range(4):
+        if step % 2:
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(L.PIKO_NUM_STAGE_EVENTS)]
+            for e in ev:
+                e.record()  # creates the CUDA events
+            r.set_stage_events(ev)
+        fb.key.fill_(0)
+        r.forward(ds, fb)
+        torch.cuda.synchronize()
+        assert r.status()[0] == 0
+        assert_keys_equal(fb.key_numpy(), ref, f"{W}x{H} bins {bins} step {step}")
+        assert np.abs(fb.rgba.cpu().numpy() - rgba_ref).max() <= RGB_TOL
+        entries.append(r.stats()["bin_entries"])
+    assert len(set(entries)) == 1
+
+
 def _dense_small_boxes(W, H, T, seed):
     """Right triangles with legs 4.9 x 5.9 px (boxes of at most 5 x 6 pixel
     centres) at random places and orientations, about seven deep."""

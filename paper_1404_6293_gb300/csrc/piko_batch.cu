@@ -62,7 +62,7 @@ struct BatchParams {
   const int* bin_prefix;
   const int* stat_prefix;  // tiles of static scenes
   const int* dyn_prefix;   // tiles of dynamic scenes
-  const int* btile_prefix;  // 16 x 16 backward tiles
+  const int* btile_prefix;  // backward tiles (BWD_TILE_W x BWD_TILE_H)
   int total_v, total_t, total_bins, total_static, total_dyn, total_btiles;
   int4* vtx;
   float* vdot;
@@ -459,7 +459,7 @@ __global__ void __maxnreg__(PIKO_BATCH_MAXNREG) k_batch_forward(BatchParams b) {
 }
 
 // ------------------------------------------------------------------ backward
-// 16 x 16 tiles of every scene, dealt round robin; each tile's gradients are
+// BWD_TILE_W x BWD_TILE_H tiles of every scene, dealt round robin; each tile's gradients are
 // accumulated as in the single-scene backward.
 struct BatchBwdParams {
   int n;

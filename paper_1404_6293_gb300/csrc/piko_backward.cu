@@ -1,5 +1,5 @@
 // piko_backward.cu -- attribute gradients of one scene through the shading of
-// the forward pass: the tile form (a warp per 16 x 32 tile, piko_bwd_tile.cuh)
+// the forward pass: the tile form (a warp per 16 x 16 tile, piko_bwd_tile.cuh)
 // and a per-pixel form for scenes of tiny triangles.
 #include "piko_bwd_tile.cuh"
 

@@ -62,7 +62,7 @@ struct BatchParams {
   const int* bin_prefix;
   const int* stat_prefix;  // tiles of static scenes
   const int* dyn_prefix;   // tiles of dynamic scenes
-  const int* btile_prefix;  // backward tiles (BWD_TILE_W x BWD_TILE_H)
+  const int* btile_prefix;  // backward tiles (BWD_TILE_W x BATCH_BWD_TILE_H)
   int total_v, total_t, total_bins, total_static, total_dyn, total_btiles;
   int4* vtx;
   float* vdot;
@@ -459,7 +459,7 @@ __global__ void __maxnreg__(PIKO_BATCH_MAXNREG) k_batch_forward(BatchParams b) {
 }
 
 // ------------------------------------------------------------------ backward
-// BWD_TILE_W x BWD_TILE_H tiles of every scene, dealt round robin; each tile's gradients are
+// BWD_TILE_W x BATCH_BWD_TILE_H tiles of every scene, dealt round robin; each tile's gradients are
 // accumulated as in the single-scene backward.
 struct BatchBwdParams {
   int n;
@@ -510,7 +510,8 @@ __global__ void __launch_bounds__(BWD_THREADS, PIKO_BWD_MINB) k_batch_backward(B
     const int lt = i - __ldg(b.btile_prefix + s);
     const int ntx = (c.W + BWD_TILE_W - 1) / BWD_TILE_W;
     const int ty = lt / ntx, tx = lt - ty * ntx;
-    backward_warp_tile<PERSP>(c, tx * BWD_TILE_W, ty * BWD_TILE_H, sm.stage[warp], L0, L1, L2);
+    backward_warp_tile<PERSP, false, BATCH_BWD_TILE_H>(c, tx * BWD_TILE_W, ty * BATCH_BWD_TILE_H, sm.stage[warp],
+                                                        L0, L1, L2);
   }
 }
 constexpr size_t BATCH_BWD_SMEM = sizeof(BatchBwdSmem);
@@ -667,7 +668,8 @@ int batch_prepare(BatchState*& bs, int num_sms, const piko_scene* scenes, int n,
     const int ntiles = x.g.nbx * x.g.nby;
     pv[i] = (int)tv; pt[i] = (int)tt; pb[i] = (int)tb; ps[i] = (int)tsd; pd[i] = (int)tdy; pp[i] = (int)tp;
     tv += x.V; tt += x.T; tb += ntiles;
-    tp += (long long)((s.width + BWD_TILE_W - 1) / BWD_TILE_W) * ((s.height + BWD_TILE_H - 1) / BWD_TILE_H);
+    tp += (long long)((s.width + BWD_TILE_W - 1) / BWD_TILE_W) *
+          ((s.height + BATCH_BWD_TILE_H - 1) / BATCH_BWD_TILE_H);
     if (sched == PIKO_SCHED_STATIC) tsd += ntiles;
     else tdy += ntiles;
     if (bw * bh > max_bin_px) max_bin_px = bw * bh;

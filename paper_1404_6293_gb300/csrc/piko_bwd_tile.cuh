@@ -10,7 +10,7 @@
 //   dL/dn_i += (g . albedo) b_i L   when s > 0 (or unclamped)
 //   dL/dL   += (g . albedo) n
 //
-// A warp takes a 16 x 32 tile of pixels (backward_warp_tile, below) with no
+// A warp takes a 16 x 16 or 16 x 32 tile (backward_warp_tile, below) with no
 // CTA barrier: the warps of a CTA work on separate tiles.  Each lane walks a
 // column of the tile and keeps, for as long as its pixels keep the same
 // winning triangle (a run), that triangle's setup (vertex indices, snapped
@@ -25,14 +25,20 @@
 
 namespace piko {
 
-// 16 x 32 tiles: longer column runs per lane than 16 x 16 (256-scene batch
-// backward 5.03 -> 4.87 ms, sphere views 0.672 -> 0.663 ms; 16 x 64: 4.95 and
-// 0.79 ms)
+// Rows per tile: the batch backward takes 16 x 32 tiles, longer column runs
+// per lane (256-scene batch 5.03 -> 4.87 ms, sphere views 0.672 -> 0.663 ms;
+// 16 x 64: 4.95 and 0.79 ms); a single scene keeps 16 x 16, twice the tiles
+// for its one frame (with 16 x 32 the 256-scene per-scene loop took 31.2 ms
+// against 26.3).
 #ifndef PIKO_BWD_TILE_H
-#define PIKO_BWD_TILE_H 32
+#define PIKO_BWD_TILE_H 16
 #endif
-constexpr int BWD_TILE_W = 16;               // pixels per tile row (a warp pass covers two rows)
-constexpr int BWD_TILE_H = PIKO_BWD_TILE_H;  // rows per tile
+#ifndef PIKO_BATCH_BWD_TILE_H
+#define PIKO_BATCH_BWD_TILE_H 32
+#endif
+constexpr int BWD_TILE_W = 16;                           // pixels per tile row (a warp pass covers two rows)
+constexpr int BWD_TILE_H = PIKO_BWD_TILE_H;              // rows per tile, single scene
+constexpr int BATCH_BWD_TILE_H = PIKO_BATCH_BWD_TILE_H;  // rows per tile, batch
 constexpr int BWD_THREADS = 256;             // CTA size of the backward kernels (8 warps, a tile each)
 // Terms per pixel: q = 3 j + c (c < 3) is g_c s b_j, the colour gradient of
 // vertex j (g_c b_j for Gouraud); q = 9 + j is G b_j with G = g . albedo
@@ -60,7 +66,7 @@ struct BwdScene {
 };
 
 // ---------------------------------------------------------------- warp form
-// One warp takes a BWD_TILE_W x BWD_TILE_H tile in passes of 16 x 2 pixels:
+// One warp takes a BWD_TILE_W x TILE_H tile in passes of 16 x 2 pixels:
 // lane l follows column l mod 16 down the rows of parity l / 16.  A run that
 // ends is flushed (bwd_run_flush): lanes ending runs of the same triangle
 // are summed through the warp's staging area, one lane per term, with one
@@ -252,7 +258,7 @@ __device__ __forceinline__ void bwd_run_flush(const BwdScene& sc, bool fl, unsig
 // run is set up by the lowest lane of the warp that holds it and broadcast to
 // the lanes that need it; a lane whose run goes on keeps its setup.
 // CLIP: near/far clipping may be on (sc.pos set).
-template <bool PERSP = false, bool CLIP = false>
+template <bool PERSP = false, bool CLIP = false, int TILE_H = BWD_TILE_H>
 __device__ __forceinline__ void backward_warp_tile(const BwdScene& sc, int x0, int y0, float (*stage)[33], float L0,
                                                    float L1, float L2) {
   const int lane = threadIdx.x & 31;
@@ -271,13 +277,13 @@ __device__ __forceinline__ void backward_warp_tile(const BwdScene& sc, int x0, i
   const unsigned* kw = reinterpret_cast<const unsigned*>(sc.key);
   unsigned knext = x < sc.W && y0 + (lane >> 4) < sc.H ? __ldg(kw + 2 * ((size_t)(y0 + (lane >> 4)) * sc.W + x))
                                                        : BWD_NONE;
-  for (int pass = 0; pass < BWD_TILE_H / 2; ++pass) {
+  for (int pass = 0; pass < TILE_H / 2; ++pass) {
     const int y = y0 + 2 * pass + (lane >> 4);
     const size_t o = (size_t)y * sc.W + x;
     // a key naming a triangle outside this scene contributes nothing (it
     // cannot come from this scene's forward)
     const unsigned t = knext < (unsigned)sc.T ? knext : BWD_NONE;
-    if (pass + 1 < BWD_TILE_H / 2)
+    if (pass + 1 < TILE_H / 2)
       knext = x < sc.W && y + 2 < sc.H ? __ldg(kw + 2 * (o + 2 * (size_t)sc.W)) : BWD_NONE;
     float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
     if (t != BWD_NONE) g = __ldg(sc.dl + o);  // issued before the flush and setup it does not need
